@@ -1,0 +1,225 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by
+mathematics, independent of the oracle's own code (CPU only).
+
+Each pin is chosen so that a plausible slip in the oracle fails it:
+ - Matern closed forms vs the Bessel expression of Eq. 3 (scipy.special.kv):
+   a wrong sqrt(2 nu) scaling, polynomial term or rho use.
+ - RBF as the nu -> infinity limit of Eq. 3: a wrong RBF length-scale reading.
+ - kNN vs an all-pairs lexsort with tie-heavy integer grids: selection, order,
+   tie rule, self exclusion.
+ - Blocks symmetric, nugget only on the diagonal, SPD with lambda_min >= sigma^2 tau^2.
+ - k = n reduces Eq. 7 to the dense GP mean of Eq. 2 (scipy cho_solve), for
+   several responses: the solve, the cross-covariance, the C layout.
+ - Interpolation identity at z = x_i: S_i[0] = i, the row lookup, no nugget in
+   the cross-covariance.
+ - Leave-one-out block identity: ties the LOOCV objective (Eq. 5) to the
+   precomputed C (Eq. 6).
+ - sigma^2 invariance of the mean and 1/sigma^2 scaling of C.
+ - Long-double re-evaluation bounds the FP64 rounding error.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sl
+from scipy.special import gamma, kv
+
+import oracle
+from paper_2205_10879_gb300 import workloads as wl
+
+
+def matern_bessel(u, nu):
+    """Eq. 3 without sigma^2/nugget: 2^(1-nu)/Gamma(nu) (sqrt(2nu) u)^nu K_nu(sqrt(2nu) u)."""
+    u = np.asarray(u, np.float64)
+    out = np.ones_like(u)
+    nz = u > 0
+    a = np.sqrt(2 * nu) * u[nz]
+    out[nz] = 2 ** (1 - nu) / gamma(nu) * a ** nu * kv(nu, a)
+    return out
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_matern_closed_forms_match_bessel(nu):
+    rho = 0.37
+    u = np.concatenate([[0.0], np.geomspace(1e-6, 30, 400)])
+    D = (u * rho) ** 2
+    got = oracle.phi(oracle.kernel("matern", nu, rho), D)
+    ref = matern_bessel(u, nu)
+    assert got[0] == 1.0
+    np.testing.assert_allclose(got, ref, rtol=2e-12, atol=1e-300)
+
+
+def test_rbf_is_the_matern_limit():
+    rho = 0.8
+    u = np.linspace(0.05, 3.0, 60)
+    D = (u * rho) ** 2
+    rbf = oracle.phi(oracle.kernel("rbf", 0.0, rho), D)
+    errs = []
+    for nu in [5.0, 20.0, 80.0]:
+        errs.append(np.max(np.abs(matern_bessel(u, nu) - rbf)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 5e-3
+    # the alternative reading exp(-d^2/rho^2) is far from the limit
+    assert np.max(np.abs(np.exp(-u ** 2) - matern_bessel(u, 80.0))) > 0.1
+
+
+def _canon_keys(X, Q):
+    # canonical key: left-to-right FP64 sum of squared differences
+    t = Q[:, None, 0] - X[None, :, 0]
+    s = t * t
+    for j in range(1, X.shape[1]):
+        t = Q[:, None, j] - X[None, :, j]
+        s = s + t * t
+    return s
+
+
+def _allpairs_knn(X, kq, self_exclude=True, Q=None):
+    Qm = X if Q is None else Q
+    K = _canon_keys(X, Qm)
+    idx = np.arange(X.shape[0])
+    out = np.zeros((Qm.shape[0], kq), np.int64)
+    for q in range(Qm.shape[0]):
+        keys = K[q].copy()
+        cand = idx
+        if self_exclude:
+            cand = idx[idx != q]
+            keys = keys[idx != q]
+        order = np.lexsort((cand, keys))
+        out[q] = cand[order[:kq]]
+    return out
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5])
+def test_knn_matches_allpairs_sort_on_tie_heavy_grid(d):
+    rng = np.random.default_rng(10 + d)
+    X = rng.integers(0, 4, size=(150, d)).astype(np.float64)  # many exact duplicates and ties
+    for kq in [1, 7, 40]:
+        idx, keys = oracle.self_knn(X, kq)
+        np.testing.assert_array_equal(idx, _allpairs_knn(X, kq))
+        assert np.all(np.diff(keys, axis=1) >= 0)
+        # tie rule: equal keys appear in increasing index order
+        eq = np.diff(keys, axis=1) == 0
+        assert np.all(np.diff(idx, axis=1)[eq] > 0)
+        assert not np.any(idx == np.arange(150)[:, None])
+
+
+def test_knn_random_points_and_test_queries():
+    rng = np.random.default_rng(3)
+    X = rng.random((300, 2))
+    Z = rng.random((50, 2))
+    idx, _ = oracle.self_knn(X, 12)
+    np.testing.assert_array_equal(idx, _allpairs_knn(X, 12))
+    j, _ = oracle.knn(X, Z, 1)
+    np.testing.assert_array_equal(j[:, 0], _allpairs_knn(X, 1, False, Z)[:, 0])
+
+
+@pytest.mark.parametrize("kind,nu", [("matern", 0.5), ("matern", 1.5), ("matern", 2.5), ("rbf", 0)])
+def test_blocks_symmetric_spd_nugget_on_diagonal(kind, nu):
+    rng = np.random.default_rng(4)
+    X = rng.random((80, 2))
+    X[5] = X[9]  # a duplicate pair inside the block
+    kern = oracle.kernel(kind, nu, 0.2, 1.7, 1e-3)
+    S = np.array([5, 9, 3, 40, 41, 77, 12, 0], np.int32)
+    K = oracle.assemble(X, S, kern)
+    np.testing.assert_array_equal(K, K.T)
+    np.testing.assert_allclose(np.diag(K), 1.7 * (1 + 1e-3), rtol=0, atol=0)
+    assert K[0, 1] == pytest.approx(1.7)            # duplicate: no nugget off the diagonal
+    assert np.linalg.eigvalsh(K).min() >= 1.7 * 1e-3 * (1 - 1e-8)
+
+
+def _dense_kernel(A, B, nu, rho, var, kind="matern"):
+    d = np.sqrt(((A[:, None, :] - B[None, :, :]) ** 2).sum(-1))
+    if kind == "rbf":
+        return var * np.exp(-d ** 2 / (2 * rho ** 2))
+    return var * matern_bessel(d / rho, nu)
+
+
+@pytest.mark.parametrize("kind,nu", [("matern", 1.5), ("matern", 0.5), ("rbf", 0.0)])
+def test_k_equals_n_is_the_dense_gp_mean(kind, nu):
+    rng = np.random.default_rng(5)
+    n, r = 60, 3
+    X = rng.random((n, 2))
+    Y = rng.normal(size=(n, r))
+    Z = rng.random((25, 2))
+    rho, var, tau2 = 0.3, 2.0, 1e-3
+    kern = oracle.kernel(kind, nu, rho, var, tau2)
+    nbr, _ = oracle.self_knn(X, n - 1)
+    C, st = oracle.precompute(X, Y, nbr, n, kern)
+    assert not st.any()
+    yh, _ = oracle.predict(X, nbr, C, kern, Z)
+    Kxx = _dense_kernel(X, X, nu, rho, var, kind) + var * tau2 * np.eye(n)
+    Kzx = _dense_kernel(Z, X, nu, rho, var, kind)
+    ref = Kzx @ sl.cho_solve(sl.cho_factor(Kxx, lower=True), Y)
+    np.testing.assert_allclose(yh, ref, rtol=1e-8, atol=1e-8 * np.abs(ref).max())
+
+
+def test_interpolation_identity():
+    W = wl.tiny(n=400, m=10)
+    kern = oracle.kernel("matern", 1.5, 0.1, 1.3, 1e-4)
+    nbr, _ = oracle.self_knn(W.X, 29)
+    C, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern)
+    rows = np.array([0, 17, 123, 399])
+    yh, near = oracle.predict(W.X, nbr, C, kern, W.X[rows])
+    np.testing.assert_array_equal(near, rows)
+    # K(x_i, X_Si) is row 0 of K_Si minus the nugget, so yhat = y_i - sigma^2 tau^2 C_i[0]
+    ref = W.Y[rows, 0] - 1.3 * 1e-4 * C[rows, 0, 0]
+    np.testing.assert_allclose(yh[:, 0], ref, rtol=1e-9, atol=1e-12)
+
+
+def test_loo_identity_links_loocv_to_precompute():
+    W = wl.tiny(n=500, m=10)
+    kern = oracle.kernel("matern", 2.5, 0.15, 1.0, 1e-3)
+    kl = 20
+    nbr, _ = oracle.self_knn(W.X, kl)
+    batch = np.array([3, 50, 77, 200, 499], np.int64)
+    Q, res = oracle.loocv(W.X, W.Y, nbr, kl, batch, kern)
+    C, _ = oracle.precompute(W.X, W.Y, nbr, kl + 1, kern)
+    for q, i in enumerate(batch):
+        S = np.concatenate([[i], nbr[i, :kl]]).astype(np.int32)
+        Kinv00 = np.linalg.inv(oracle.assemble(W.X, S, kern))[0, 0]
+        loo = C[i, 0, 0] / Kinv00
+        assert res[q] == pytest.approx(loo ** 2, rel=1e-7)
+    assert Q == pytest.approx(res.mean(), rel=1e-14)
+
+
+def test_sigma2_invariance():
+    W = wl.tiny(n=300, m=40)
+    nbr, _ = oracle.self_knn(W.X, 19)
+    k1 = oracle.kernel("matern", 1.5, 0.1, 1.0, 1e-3)
+    k7 = oracle.kernel("matern", 1.5, 0.1, 7.0, 1e-3)
+    C1, _ = oracle.precompute(W.X, W.Y, nbr, 20, k1)
+    C7, _ = oracle.precompute(W.X, W.Y, nbr, 20, k7)
+    np.testing.assert_allclose(C7 * 7.0, C1, rtol=1e-9)
+    y1, _ = oracle.predict(W.X, nbr, C1, k1, W.Z)
+    y7, _ = oracle.predict(W.X, nbr, C7, k7, W.Z)
+    np.testing.assert_allclose(y7, y1, rtol=1e-10, atol=1e-13)
+
+
+def test_not_spd_block_is_flagged():
+    X = np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 1.0], [2.0, 0.5]])
+    Y = np.ones((4, 1))
+    nbr, _ = oracle.self_knn(X, 2)
+    kern = oracle.kernel("matern", 1.5, 1.0, 1.0, 0.0)  # no nugget: duplicates make K singular
+    C, st = oracle.precompute(X, Y, nbr, 3, kern)
+    assert st[0] == 1 and st[1] == 1
+    assert np.all(C[0] == 0)
+
+
+def test_long_double_bounds_fp64_rounding():
+    W = wl.tiny()
+    kern = oracle.kernel("matern", 1.5, 0.1, 1.0, 1e-4)
+    nbr, _ = oracle.self_knn(W.X, 29)
+    C, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern)
+    yh, near = oracle.predict(W.X, nbr, C, kern, W.Z)
+    yl = oracle.fit_predict_ld(W.X, W.Y, nbr, 30, kern, W.Z, near)
+    rel = np.linalg.norm(yh - yl) / np.linalg.norm(yl)
+    assert rel < 1e-12, rel
+
+
+def test_accuracy_is_plausible_on_tiny():
+    """The method predicts the smooth tiny response well (sanity, not a pin)."""
+    W = wl.tiny()
+    kern = oracle.kernel("matern", 1.5, 0.1, 1.0, 1e-4)
+    nbr, _ = oracle.self_knn(W.X, 29)
+    C, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern)
+    yh, _ = oracle.predict(W.X, nbr, C, kern, W.Z)
+    rmse = np.sqrt(np.mean((yh - W.Ztrue) ** 2))
+    assert rmse < 0.05
