@@ -1,0 +1,386 @@
+"""FastMuyGPs posterior-mean benchmark on GB300.
+
+One step = the whole hot path over one batch of the spatial 2-D workload
+(n = 150,000 training + m = 50,000 test points uniform in [0,1]^2, 20 random
+Fourier features + N(0, 0.05^2), Matern nu = 1.5, rho = 0.1, tau^2 = 1e-3,
+k = 50): self-kNN table (A1), kernel assembly + Cholesky + solve for every
+training point (A2-A3), nearest-training-point lookup (A4), gather-dot
+prediction (A5) and the LOOCV objective over a batch of b = 10,000 (A6).
+
+value = (n + m) / step time [points/s]; per-phase rates (precompute pts/s,
+predictions/s, kNN queries/s, LOOCV pts/s) and the plain FP64 path's numbers
+are reported beside it.  Inputs are resident in HBM before timing; L2 (129 MB)
+is flushed between timed steps by writing a 512 MB buffer.  e2e repeats the
+step from pinned host buffers with the copies inside the timed region.
+
+--impl reference times the FP64 CPU oracle (OpenMP, all host cores) on a
+bounded sample of the same workload and extrapolates to the same metric.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "predictions/s + precompute pts/s vs FP64 plain at equal RMSE; p50/p99 latency"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--n", type=int, default=150_000)
+    p.add_argument("--m", type=int, default=50_000)
+    p.add_argument("--k", type=int, default=50)
+    p.add_argument("--b", type=int, default=10_000)
+    p.add_argument("--nu", type=float, default=1.5)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(a):
+    return {"workload": "spatial-2d", "n_train": a.n, "m_test": a.m, "d": 2, "k": a.k,
+            "r": 1, "kernel": f"matern nu={a.nu} rho=0.1 tau2=1e-3", "loocv_batch": a.b,
+            "l2": "flushed between steps (512 MB write)"}
+
+
+# ----------------------------------------------------------------- flops --
+def precompute_flops_per_point(k, d, r):
+    """Algorithmic FP operations of one neighbourhood (A2 + A3): k(k-1)/2 kernel
+    entries at 3d (distance) + 6 (scale, sqrt, exp, polynomial; transcendentals
+    counted once), Cholesky k^3/3, two triangular solves 2 k^2 r."""
+    return k * (k - 1) / 2 * (3 * d + 6) + k ** 3 / 3 + 2 * k * k * r
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during timing."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our arm ----
+def run_ours(a):
+    import torch
+    from paper_2205_10879_gb300 import _binding as fb
+    from paper_2205_10879_gb300 import workloads as wl
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    fb.load()
+    W = wl.spatial(n=a.n, m=a.m, k=a.k, nu=a.nu, b=a.b)
+    s = W.kernel
+    gk = fb.make_kernel(s.kind, s.nu, s.length_scale, s.variance, s.nugget)
+    k, kq = W.k, W.k  # one table serves precompute (k-1 columns) and LOOCV (k columns)
+    X = torch.from_numpy(W.X).to(dev)
+    Y = torch.from_numpy(W.Y).to(dev)
+    Z = torch.from_numpy(W.Z).to(dev)
+    batch = torch.from_numpy(W.batch).to(dev)
+    n, m, b = W.n, W.m, W.b if hasattr(W, "b") else len(W.batch)
+    b = len(W.batch)
+
+    def pick_precision():
+        if a.precision == "fp64":
+            return fb.PREC_FP64
+        if a.precision == "mixed":
+            return fb.PREC_MIXED
+        try:  # auto: the mixed form when this build has it
+            nb, _ = fb.fmgp_build_knn(X[:1000].contiguous(), 8)
+            fb.fmgp_precompute(X[:1000].contiguous(), Y[:1000].contiguous(), nb, 9, gk,
+                               fb.PREC_MIXED)
+            return fb.PREC_MIXED
+        except fb.FmgpError:
+            return fb.PREC_FP64
+
+    prec = pick_precision()
+    nbr = torch.empty((n, kq), dtype=torch.int32, device=dev)
+    C = torch.empty(fb.coeff_shape(n, k, 1, prec),
+                    dtype=torch.float64 if prec == fb.PREC_FP64 else torch.float32, device=dev)
+    st = torch.empty(n, dtype=torch.int8, device=dev)
+    yh = torch.empty((m, 1), dtype=torch.float64, device=dev)
+    near = torch.empty(m, dtype=torch.int32, device=dev)
+    resid = torch.empty(b, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p, C_, ev=None):
+        if ev: ev[0].record(stream)
+        fb.fmgp_build_knn(X, kq, nbr_out=nbr)
+        if ev: ev[1].record(stream)
+        fb.fmgp_precompute(X, Y, nbr, k, gk, p, C_out=C_, status_out=st)
+        if ev: ev[2].record(stream)
+        fb.fmgp_predict(X, nbr, C_, k, gk, Z, p, Yhat_out=yh, nearest_out=near)
+        if ev: ev[3].record(stream)
+        Q, _ = fb.fmgp_loocv_objective(X, Y, nbr, k, batch, gk, p, resid_out=resid)
+        if ev: ev[4].record(stream)
+        return Q
+
+    def timed(p, C_, steps, warmup):
+        for _ in range(warmup):
+            step(p, C_)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = fb.kernel_launches()
+        for i in range(steps):
+            flush.zero_()
+            step(p, C_, evs[i])
+        torch.cuda.synchronize()
+        launches = (fb.kernel_launches() - l0) / steps
+        ph = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)]
+                       for i in range(steps)])
+        return ph, launches
+
+    clk = ClockSampler(local)
+    clk.start()
+    ph, launches = timed(prec, C, a.steps, a.warmup)
+    clocks = clk.stop()
+    step_ms = ph.sum(axis=1)
+    ms = float(step_ms.mean())
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    phase_ms = ph.mean(axis=0)
+    yh_main = yh.cpu().numpy().copy()
+    rmse = float(np.sqrt(np.mean((yh_main - W.Ztrue) ** 2)))
+    out = {}
+    # the plain FP64 path on the same workload, for the "vs FP64 plain" comparison
+    fp64 = None
+    if prec != fb.PREC_FP64:
+        C64 = torch.empty((n, k, 1), dtype=torch.float64, device=dev)
+        ph64, _ = timed(fb.PREC_FP64, C64, max(2, a.steps // 2), 1)
+        y64 = yh.cpu().numpy().copy()
+        p64 = ph64.mean(axis=0)
+        fp64 = {"ms_per_step": float(ph64.sum(axis=1).mean()),
+                "precompute_pts_per_s": n / (p64[1] * 1e-3),
+                "predictions_per_s": m / (p64[2] * 1e-3),
+                "rmse": float(np.sqrt(np.mean((y64 - W.Ztrue) ** 2))),
+                "rel_rms_vs_fp64": float(np.linalg.norm(yh_main - y64) / np.linalg.norm(y64))}
+        del C64
+    # roofline of the dominant kernel (the precompute block kernel: one launch per step)
+    fl = precompute_flops_per_point(k, 2, 1) * n
+    pre_s = phase_ms[1] * 1e-3
+    if prec == fb.PREC_FP64:
+        peak = 152 * 4 * 2070e6 / 1e12  # FP64: 2 DFMA/clk/SM
+        roof = {"bound": "alu", "pipe": "fp64", "kernel": "block_f64_kernel"}
+    else:
+        peak = 152 * 256 * 2070e6 / 1e12  # FP32: 128 FFMA/clk/SM
+        roof = {"bound": "alu", "pipe": "fp32", "kernel": "block_mixed_kernel"}
+    achieved = fl / pre_s / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": None, "flops_per_launch": fl,
+                 "peak_source": "derived: 152 SMs x pipe FMA/clk x 2 x 2070 MHz"})
+    # e2e: same step from pinned host buffers, copies inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        hX = torch.from_numpy(W.X).pin_memory()
+        hY = torch.from_numpy(W.Y).pin_memory()
+        hZ = torch.from_numpy(W.Z).pin_memory()
+        hB = torch.from_numpy(W.batch).pin_memory()
+        hOut = torch.empty((m, 1), dtype=torch.float64).pin_memory()
+        dX, dY, dZ, dB = (torch.empty_like(t, device=dev) for t in (hX, hY, hZ, hB))
+
+        def e2e_step():
+            dX.copy_(hX, non_blocking=True)
+            dY.copy_(hY, non_blocking=True)
+            dZ.copy_(hZ, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            fb.fmgp_build_knn(dX, kq, nbr_out=nbr)
+            fb.fmgp_precompute(dX, dY, nbr, k, gk, prec, C_out=C, status_out=st)
+            fb.fmgp_predict(dX, nbr, C, k, gk, dZ, prec, Yhat_out=yh, nearest_out=near)
+            Q, _ = fb.fmgp_loocv_objective(dX, dY, nbr, k, dB, gk, prec, resid_out=resid)
+            hOut.copy_(yh, non_blocking=True)
+            return Q
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e = []
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_e.append(e0.elapsed_time(e1))
+        e_ms = float(np.mean(t_e))
+        e2e = {"value": (n + m) / (e_ms * 1e-3) * ws, "unit": "points/s",
+               "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in (hX, hY, hZ, hB))),
+               "d2h_bytes_per_step": int(hOut.numel() * hOut.element_size() + 8)}
+    line = {
+        "metric": METRIC, "value": (n + m) / (ms * 1e-3) * ws, "unit": "points/s",
+        "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == fb.PREC_FP64 else "f32+df64",
+        "precision": "fp64" if prec == fb.PREC_FP64 else "mixed",
+        "data": "synthetic", "config": workload_config(a),
+        "phases_ms": {"knn": phase_ms[0], "precompute": phase_ms[1], "predict": phase_ms[2],
+                      "loocv": phase_ms[3]},
+        "precompute_pts_per_s": n / (phase_ms[1] * 1e-3),
+        "predictions_per_s": m / (phase_ms[2] * 1e-3),
+        "knn_queries_per_s": n / (phase_ms[0] * 1e-3),
+        "loocv_pts_per_s": b / (phase_ms[3] * 1e-3),
+        "rmse": rmse, "fp64_path": fp64, "roofline": roof, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(W, a, samples=(20000, 20000, 5000))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------- oracle ----
+def oracle_sample(W, a, samples):
+    """Time the FP64 oracle on a bounded sample: kNN + precompute for s1
+    training rows, 1-NN + prediction for s2 test points, LOOCV for s3 batch
+    points; extrapolate each phase to the full workload."""
+    import oracle
+    s1, s2, s3 = samples
+    rng = np.random.default_rng(7)
+    ok = oracle.kernel(W.kernel.kind, W.kernel.nu, W.kernel.length_scale, W.kernel.variance,
+                       W.kernel.nugget)
+    rows = np.sort(rng.choice(W.n, s1, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    nb_rows, _ = oracle.knn(W.X, W.X[rows], W.k, rows)
+    t1 = time.perf_counter()
+    nbr = np.zeros((W.n, W.k), np.int32)
+    nbr[rows] = nb_rows
+    oracle.precompute(W.X, W.Y, nbr, W.k, ok, rows=rows)
+    t2 = time.perf_counter()
+    # prediction: 1-NN scan + gather-dot (coefficients of arbitrary value: cost is the same)
+    tz = rng.choice(W.m, s2, replace=False)
+    near, _ = oracle.knn(W.X, W.Z[tz], 1)
+    C = np.zeros((W.n, W.k, 1))
+    # j* is taken from the sampled rows (whose neighbour table exists); the work is identical
+    oracle.predict_given(W.X, nbr, C, ok, W.Z[tz], rows[np.arange(s2) % s1].astype(np.int32))
+    t3 = time.perf_counter()
+    lb = rows[:s3]
+    oracle.loocv(W.X, W.Y, nbr, W.k, lb, ok)
+    t4 = time.perf_counter()
+    per_knn = (t1 - t0) / s1
+    per_pre = (t2 - t1) / s1
+    per_pred = (t3 - t2) / s2
+    per_loo = (t4 - t3) / s3
+    b = len(W.batch)
+    step_s = W.n * (per_knn + per_pre) + W.m * per_pred + b * per_loo
+    return {"value": (W.n + W.m) / step_s, "unit": "points/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{s1} training rows (kNN + precompute), {s2} test points (1-NN + predict), "
+                      f"{s3} LOOCV points of the same workload; extrapolated per point",
+            "sample_seconds": t4 - t0,
+            "precompute_pts_per_s": 1.0 / per_pre, "predictions_per_s": 1.0 / per_pred,
+            "knn_queries_per_s": 1.0 / per_knn}
+
+
+def run_reference(a):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2205_10879_gb300 import workloads as wl
+    W = wl.spatial(n=a.n, m=a.m, k=a.k, nu=a.nu, b=a.b)
+    res = []
+    for i in range(a.warmup + a.steps):
+        r = oracle_sample(W, a, samples=(5000, 5000, 1000))
+        if i >= a.warmup:
+            res.append(r)
+    v = float(np.mean([r["value"] for r in res]))
+    cpu = dict(res[-1])
+    cpu["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s",
+            "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": (W.n + W.m) / v * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a), "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

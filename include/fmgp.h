@@ -1,0 +1,184 @@
+/*
+ * fmgp.h -- C ABI of the GB300-native FastMuyGPs posterior-mean library
+ * (libfmgp.so).
+ *
+ * Method: "Fast Gaussian Process Posterior Mean Prediction via Local Cross
+ * Validation and Precomputation" (Dunton, Priest, Muyskens).  Notation:
+ * training features X in R^{n x d} with responses Y in R^{n x r} (Sec. 2),
+ * neighbourhood size k, test features Z in R^{m x d}, kernel hyperparameters
+ * theta = [sigma, rho, nu, tau] of the Matern kernel (Eq. 3).
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are DEVICE pointers owned by the caller, row-major
+ *    and contiguous (e.g. X[i*d + j]); the library never frees or retains
+ *    them.  Scalars such as Q_out that are documented as HOST pointers are the
+ *    only exception.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued asynchronously on it unless the entry point says otherwise.
+ *    Internal workspace is taken stream-ordered from the device's default
+ *    memory pool (cudaMallocAsync) and returned on the same stream.
+ *  - Argument errors are detected on the host before anything is launched:
+ *    the call returns FMGP_EINVAL and launches nothing.  fmgp_last_error()
+ *    returns a thread-local message describing the most recent failure.
+ *  - Neighbour ranking: candidates are ordered by the canonical key
+ *    D(a,b) = sum_j (a_j - b_j)^2 evaluated in IEEE FP64, left to right, each
+ *    subtraction, product and sum rounded separately (FP32 inputs are widened
+ *    to FP64 first), then by the candidate's index.  Results are therefore
+ *    unique and deterministic: distance ties go to the lowest index.
+ *  - Indices are int32: n must be below 2^31.
+ */
+#ifndef FMGP_H
+#define FMGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FMGP_OK = 0,
+  FMGP_EINVAL = 1,       /* bad argument; nothing launched */
+  FMGP_ENOMEM = 2,       /* workspace allocation failed; nothing launched */
+  FMGP_ECUDA = 3,        /* a CUDA call failed (message in fmgp_last_error) */
+  FMGP_ENOTSPD = 4,      /* at least one kernel block was not positive definite */
+  FMGP_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+  FMGP_EUNSUPPORTED = 6  /* valid request outside what this build implements */
+} fmgp_status;
+
+typedef enum { FMGP_F32 = 0, FMGP_F64 = 1 } fmgp_dtype;
+
+/*
+ * FMGP_PREC_FP64: every step in IEEE FP64 (the plain reference form).
+ * FMGP_PREC_MIXED: kernel blocks assembled and Cholesky-factored in FP32,
+ *   followed by iterative refinement whose residual Y - K C is formed in
+ *   double-float (pairs of FP32, about 48 significant bits); blocks whose FP32
+ *   factorisation fails or whose refinement does not converge are refactored
+ *   in FP64.  Coefficients are stored as double-float pairs and prediction
+ *   evaluates the cross-covariance in double-float.
+ */
+typedef enum { FMGP_PREC_FP64 = 0, FMGP_PREC_MIXED = 1 } fmgp_precision;
+
+/*
+ * Stationary isotropic kernel k(x,x') = sigma^2 phi(||x - x'||) (Sec. 2).
+ * kind = FMGP_KERNEL_MATERN: Eq. 3 with nu in {0.5, 1.5, 2.5} (closed forms
+ *   of the Bessel expression; nu = 0.5 is the exponential kernel).
+ * kind = FMGP_KERNEL_RBF: the nu -> infinity limit, phi = exp(-d^2 / (2 rho^2)).
+ * The nugget tau^2 is added, times sigma^2, to the diagonal of every training
+ * block K(X_S, X_S) only; it never enters a cross-covariance.
+ */
+enum { FMGP_KERNEL_MATERN = 0, FMGP_KERNEL_RBF = 1 };
+typedef struct {
+  int32_t kind;
+  double nu;            /* Matern smoothness (ignored for RBF) */
+  double length_scale;  /* rho > 0 */
+  double variance;      /* sigma^2 > 0 */
+  double nugget;        /* tau^2 >= 0 */
+} fmgp_kernel;
+
+/* Per-neighbourhood status codes written to status_out. */
+enum {
+  FMGP_BLOCK_OK = 0,
+  FMGP_BLOCK_NOT_SPD = 1,   /* Cholesky met a non-positive pivot; row of C is zero */
+  FMGP_BLOCK_FP64_RETRY = 2, /* MIXED only: solved by the FP64 fallback */
+  FMGP_BLOCK_BAD_INDEX = 3   /* a neighbour index was outside [0, n); row of C is zero */
+};
+
+/*
+ * fmgp_build_knn -- self k-nearest-neighbour table of the training set.
+ * Algorithm 2 "query k-1 nearest neighbors of x_i" and Algorithm 1 "query k
+ * nearest neighbors for all i in B": for every training point i, the kq
+ * nearest training points j != i, ascending by (canonical key, j).  Only the
+ * index i itself is excluded; a duplicate of x_i stored at another index is a
+ * neighbour at distance 0.
+ *   X        n x d, FP64 or FP32 per `dtype`.
+ *   kq       neighbours per row, 1 <= kq <= n-1.  A table with
+ *            kq = max(k-1, k_loocv) serves both fmgp_precompute (k-1 columns)
+ *            and fmgp_loocv_objective (k columns) through nbr_ld = kq.
+ *   nbr_out  n x kq int32 (row-major, leading dimension kq).
+ *   dist_out n x kq FP64 canonical keys (squared distances), or NULL.
+ *   flags    0 (reserved).
+ * Search: a uniform grid over the bounding box for d <= 3; a tiled scan with
+ * an FP32 prefilter and an exact FP64 re-rank for d >= 4.
+ * Returns FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM or FMGP_ECUDA.
+ */
+int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
+                   int32_t* nbr_out, double* dist_out, int32_t flags, void* stream);
+
+/*
+ * fmgp_precompute -- the offline loop of Algorithm 2 (Eq. 6).
+ * For every training point i: S_i = [i, nbr[i][0..k-2]], the k x k block
+ * K_i = K(X_Si, X_Si) (sigma^2 phi off the diagonal, sigma^2 (1 + tau^2) on
+ * it), and C_i = K_i^{-1} Y(X_Si).
+ *   Y        n x r FP64.
+ *   nbr      n x nbr_ld int32 neighbour table (first k-1 columns are used),
+ *            normally the output of fmgp_build_knn; entries must lie in [0, n).
+ *   k        neighbourhood size |S_i|, 1 <= k <= min(n, 128), nbr_ld >= k-1.
+ *   C_out    n x k x r coefficients, C_out[(i*k + a)*r + c] pairs with point
+ *            S_i[a].  FMGP_PREC_FP64: double.  FMGP_PREC_MIXED: double-float
+ *            pairs (float hi, float lo; value = hi + lo), i.e. n*k*r*2 floats.
+ *            Both forms take 8 bytes per coefficient.
+ *   status_out n int8 FMGP_BLOCK_* codes, or NULL.
+ * Returns FMGP_ENOTSPD (after completing every other row) if any block was
+ * not positive definite; the status is read back with a synchronisation of
+ * `stream` in that case only when status_out is NULL.  Otherwise FMGP_OK.
+ * When status_out is given the call stays asynchronous and always returns
+ * FMGP_OK on success; inspect status_out.
+ */
+int fmgp_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                    int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                    const fmgp_kernel* kernel, fmgp_precision precision, void* C_out,
+                    int8_t* status_out, void* stream);
+
+/*
+ * fmgp_predict -- the online loop of Algorithm 2 (Eq. 7).
+ * For every test point z_t: j* = the nearest training point (canonical key,
+ * ties to the lowest index), S = S_{j*} = [j*, nbr[j*][0..k-2]] and
+ * Yhat[t][c] = sum_a sigma^2 phi(||z_t - x_Sa||) C[j*][a][c].  The stored row
+ * C_{j*} is the single row of the nearest training point (the O(k) lookup of
+ * Sec. 3).
+ *   X, nbr, C, k, kernel, precision must be those given to fmgp_precompute.
+ *   Z          m x d test features, same dtype as X; m >= 0 (m = 0 is a no-op).
+ *   Yhat_out   m x r FP64.
+ *   nearest_out m int32 j* per test point, or NULL.
+ * Returns FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM or FMGP_ECUDA.
+ */
+int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
+                 int32_t nbr_ld, const void* C, int32_t k, int32_t r, const fmgp_kernel* kernel,
+                 fmgp_precision precision, const void* Z, int64_t m, double* Yhat_out,
+                 int32_t* nearest_out, void* stream);
+
+/*
+ * fmgp_loocv_objective -- the MuyGPs leave-one-out objective (Algorithm 1,
+ * Eqs. 4-5): for each i in the batch B, N_i = nbr[i][0..k-1] (the k nearest
+ * neighbours of x_i excluding i),
+ * yhat_i = K(x_i, X_Ni) K(X_Ni, X_Ni)^{-1} Y(X_Ni) and
+ * Q = (1/b) sum_{i in B} sum_c (Y[i][c] - yhat_i[c])^2.
+ *   batch      b int64 training indices in [0, n) (device).
+ *   k          1 <= k <= min(n-1, 128), nbr_ld >= k.
+ *   Q_out      HOST pointer to one double.
+ *   resid_out  b FP64 per-point squared residuals (device), or NULL.
+ * The per-point residuals are summed in batch order by one deterministic
+ * reduction.  This call synchronises `stream` to return Q.  Returns
+ * FMGP_ENOTSPD (Q = NaN) if any block failed.
+ */
+int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                         int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                         const int64_t* batch, int64_t b, const fmgp_kernel* kernel,
+                         fmgp_precision precision, double* Q_out, double* resid_out,
+                         void* stream);
+
+/* Thread-local description of the most recent error on this thread ("" if none). */
+const char* fmgp_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* fmgp_version(void);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded
+ * (all threads, all devices); a diagnostic counter for launch accounting. */
+uint64_t fmgp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMGP_H */

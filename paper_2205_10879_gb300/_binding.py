@@ -1,0 +1,184 @@
+"""ctypes binding of libfmgp.so: argument marshalling only.
+
+Every compute step runs in the CUDA library; this module turns torch tensors
+into device pointers and sizes, picks the current torch stream, and turns
+status codes into exceptions.  There is no CPU fallback: without the built
+library every call raises."""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM, FMGP_ECUDA, FMGP_ENOTSPD, FMGP_ETIMEOUT, FMGP_EUNSUPPORTED = range(7)
+F32, F64 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+KERNEL_MATERN, KERNEL_RBF = 0, 1
+BLOCK_OK, BLOCK_NOT_SPD, BLOCK_FP64_RETRY, BLOCK_BAD_INDEX = range(4)
+
+_STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTSPD", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
+
+
+class FmgpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fmgp {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Kernel(ctypes.Structure):
+    """fmgp_kernel: sigma^2 phi(d) with phi Matern (nu in {0.5,1.5,2.5}) or RBF;
+    nugget tau^2 on the diagonal of training blocks."""
+    _fields_ = [("kind", ctypes.c_int32), ("nu", ctypes.c_double),
+                ("length_scale", ctypes.c_double), ("variance", ctypes.c_double),
+                ("nugget", ctypes.c_double)]
+
+
+def make_kernel(kind="matern", nu=1.5, length_scale=0.1, variance=1.0, nugget=1e-4):
+    return Kernel(KERNEL_MATERN if kind == "matern" else KERNEL_RBF, float(nu),
+                  float(length_scale), float(variance), float(nugget))
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.TARGET
+
+
+def load(build_if_missing=True):
+    """Load libfmgp.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.TARGET):
+        raise RuntimeError("libfmgp.so is not built; run paper_2205_10879_gb300.build.build()")
+    lib = ctypes.CDLL(_build.TARGET)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    KP = ctypes.POINTER(Kernel)
+    lib.fmgp_build_knn.argtypes = [P, I32, I64, I32, I32, P, P, I32, P]
+    lib.fmgp_precompute.argtypes = [P, I32, P, I64, I32, I32, P, I32, I32, KP, I32, P, P, P]
+    lib.fmgp_predict.argtypes = [P, I32, I64, I32, P, I32, P, I32, I32, KP, I32, P, I64, P, P, P]
+    lib.fmgp_loocv_objective.argtypes = [P, I32, P, I64, I32, I32, P, I32, I32, P, I64, KP, I32,
+                                         P, P, P]
+    for f in ("fmgp_build_knn", "fmgp_precompute", "fmgp_predict", "fmgp_loocv_objective"):
+        getattr(lib, f).restype = I32
+    lib.fmgp_last_error.restype = ctypes.c_char_p
+    lib.fmgp_version.restype = ctypes.c_char_p
+    lib.fmgp_kernel_launches.restype = ctypes.c_uint64
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != FMGP_OK:
+        raise FmgpError(rc, load().fmgp_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dev(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _dtype_code(X):
+    if X.dtype == torch.float64:
+        return F64
+    if X.dtype == torch.float32:
+        return F32
+    raise TypeError("features must be float32 or float64")
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def fmgp_build_knn(X, kq, nbr_out=None, dist_out=None, with_dist=False, stream=None):
+    """Self kNN table of X (n x d): (nbr n x kq int32, dist n x kq float64 or None)."""
+    _dev(X, "X")
+    n, d = X.shape
+    if nbr_out is None:
+        nbr_out = torch.empty((n, kq), dtype=torch.int32, device=X.device)
+    if with_dist and dist_out is None:
+        dist_out = torch.empty((n, kq), dtype=torch.float64, device=X.device)
+    _check(load().fmgp_build_knn(_ptr(X), _dtype_code(X), n, d, int(kq), _ptr(nbr_out),
+                                 _ptr(dist_out), 0, _stream(stream)))
+    return nbr_out, dist_out
+
+
+def coeff_shape(n, k, r, precision):
+    return (n, k, r) if precision == PREC_FP64 else (n, k, r, 2)
+
+
+def fmgp_precompute(X, Y, nbr, k, kernel, precision=PREC_FP64, C_out=None, status_out=None,
+                    with_status=True, stream=None):
+    """C (n x k x r float64, or n x k x r x 2 float32 double-float pairs when
+    precision is PREC_MIXED) and the per-point status (int8) of Eq. 6."""
+    _dev(X, "X"); _dev(Y, "Y"); _dev(nbr, "nbr")
+    n, d = X.shape
+    r = Y.shape[1]
+    if C_out is None:
+        C_out = torch.empty(coeff_shape(n, k, r, precision),
+                            dtype=torch.float64 if precision == PREC_FP64 else torch.float32,
+                            device=X.device)
+    if with_status and status_out is None:
+        status_out = torch.empty(n, dtype=torch.int8, device=X.device)
+    _check(load().fmgp_precompute(_ptr(X), _dtype_code(X), _ptr(Y), n, d, r, _ptr(nbr),
+                                  nbr.shape[1], int(k), ctypes.byref(kernel), int(precision),
+                                  _ptr(C_out), _ptr(status_out), _stream(stream)))
+    return C_out, status_out
+
+
+def fmgp_predict(X, nbr, C, k, kernel, Z, precision=PREC_FP64, Yhat_out=None, nearest_out=None,
+                 with_nearest=True, stream=None):
+    """Eq. 7 posterior means (m x r float64) and j* (m int32)."""
+    _dev(X, "X"); _dev(nbr, "nbr"); _dev(C, "C"); _dev(Z, "Z")
+    n, d = X.shape
+    r = C.shape[2]
+    m = Z.shape[0]
+    if Yhat_out is None:
+        Yhat_out = torch.empty((m, r), dtype=torch.float64, device=X.device)
+    if with_nearest and nearest_out is None:
+        nearest_out = torch.empty(m, dtype=torch.int32, device=X.device)
+    _check(load().fmgp_predict(_ptr(X), _dtype_code(X), n, d, _ptr(nbr), nbr.shape[1], _ptr(C),
+                               int(k), r, ctypes.byref(kernel), int(precision), _ptr(Z), m,
+                               _ptr(Yhat_out), _ptr(nearest_out), _stream(stream)))
+    return Yhat_out, nearest_out
+
+
+def fmgp_loocv_objective(X, Y, nbr, k, batch, kernel, precision=PREC_FP64, resid_out=None,
+                         stream=None, raise_on_not_spd=True):
+    """Eq. 5 objective Q over the batch (host float) and per-point residuals."""
+    _dev(X, "X"); _dev(Y, "Y"); _dev(nbr, "nbr"); _dev(batch, "batch")
+    n, d = X.shape
+    r = Y.shape[1]
+    b = batch.shape[0]
+    if resid_out is None:
+        resid_out = torch.empty(b, dtype=torch.float64, device=X.device)
+    Q = ctypes.c_double(0.0)
+    rc = load().fmgp_loocv_objective(_ptr(X), _dtype_code(X), _ptr(Y), n, d, r, _ptr(nbr),
+                                     nbr.shape[1], int(k), _ptr(batch), b, ctypes.byref(kernel),
+                                     int(precision), ctypes.byref(Q), _ptr(resid_out),
+                                     _stream(stream))
+    if rc == FMGP_ENOTSPD and not raise_on_not_spd:
+        return float("nan"), resid_out
+    _check(rc)
+    return Q.value, resid_out
+
+
+def version():
+    return load().fmgp_version().decode()
+
+
+def kernel_launches():
+    """Kernels libfmgp has enqueued since it was loaded."""
+    return int(load().fmgp_kernel_launches())

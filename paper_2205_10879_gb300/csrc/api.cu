@@ -1,0 +1,339 @@
+// C-ABI entry points of libfmgp: argument validation on the host, workspace,
+// and the launch sequence of each step.
+#include <stdarg.h>
+#include <stdio.h>
+#include <math.h>
+#include <atomic>
+#include <mutex>
+#include "block.cuh"
+#include "knn.cuh"
+#include "predict.cuh"
+
+namespace fmgp {
+
+static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  return FMGP_ECUDA;
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+static void keep_pool_memory() {
+  static std::once_flag once[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return;
+  std::call_once(once[dev], [dev]() {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  });
+}
+
+void* Workspace::alloc(size_t bytes) {
+  if (count_ >= 32) {
+    set_error("workspace: too many allocations");
+    return nullptr;
+  }
+  keep_pool_memory();
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes > 0 ? bytes : 16, stream_);
+  if (e != cudaSuccess) {
+    set_error("workspace: cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    cudaGetLastError();
+    return nullptr;
+  }
+  ptrs_[count_++] = p;
+  return p;
+}
+
+Workspace::~Workspace() {
+  for (int i = 0; i < count_; ++i) cudaFreeAsync(ptrs_[i], stream_);
+}
+
+// ------------------------------------------------------------ validation --
+static bool kernel_ok(const fmgp_kernel* k) {
+  if (!k) { set_error("kernel is NULL"); return false; }
+  if (k->kind != FMGP_KERNEL_MATERN && k->kind != FMGP_KERNEL_RBF) {
+    set_error("kernel kind %d unknown", k->kind);
+    return false;
+  }
+  if (k->kind == FMGP_KERNEL_MATERN && !(k->nu == 0.5 || k->nu == 1.5 || k->nu == 2.5)) {
+    set_error("Matern nu = %g unsupported (0.5, 1.5 or 2.5)", k->nu);
+    return false;
+  }
+  if (!(k->length_scale > 0.0) || !isfinite(k->length_scale)) {
+    set_error("length_scale must be positive and finite");
+    return false;
+  }
+  if (!(k->variance > 0.0) || !isfinite(k->variance)) {
+    set_error("variance must be positive and finite");
+    return false;
+  }
+  if (!(k->nugget >= 0.0) || !isfinite(k->nugget)) {
+    set_error("nugget must be non-negative and finite");
+    return false;
+  }
+  return true;
+}
+
+static bool dtype_ok(fmgp_dtype t) {
+  if (t != FMGP_F32 && t != FMGP_F64) { set_error("dtype %d unknown", (int)t); return false; }
+  return true;
+}
+
+static bool prec_ok(fmgp_precision p) {
+  if (p != FMGP_PREC_FP64 && p != FMGP_PREC_MIXED) {
+    set_error("precision %d unknown", (int)p);
+    return false;
+  }
+  return true;
+}
+
+#define FMGP_REQUIRE(cond, ...)       \
+  do {                                \
+    if (!(cond)) {                    \
+      ::fmgp::set_error(__VA_ARGS__); \
+      return FMGP_EINVAL;             \
+    }                                 \
+  } while (0)
+
+static int pick_warps(const BlockLayout& l, int requested) {
+  const size_t budget = 200 * 1024;
+  int w = (int)(budget / l.bytes_per_warp);
+  if (w > 8) w = 8;
+  if (requested > 0 && requested < w) w = requested;
+  return w;
+}
+
+TuneParams& tune_params() {
+  static TuneParams tp;
+  return tp;
+}
+
+// Deterministic single-CTA sum of the LOOCV residuals: thread t adds
+// entries t, t+1024, ... in order, then a fixed tree.
+__global__ void __launch_bounds__(1024) loocv_reduce(const double* resid, int64_t b, double* out) {
+  __shared__ double part[1024];
+  double s = 0.0;
+  for (int64_t q = threadIdx.x; q < b; q += 1024) s += resid[q];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = part[0] / (double)b;
+}
+
+}  // namespace fmgp
+
+using namespace fmgp;
+
+extern "C" {
+
+const char* fmgp_last_error(void) { return g_err; }
+const char* fmgp_version(void) { return "0.1.0"; }
+uint64_t fmgp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
+                   int32_t* nbr_out, double* dist_out, int32_t flags, void* stream) {
+  g_err[0] = 0;
+  if (!dtype_ok(dtype)) return FMGP_EINVAL;
+  FMGP_REQUIRE(X && nbr_out, "X and nbr_out must be non-NULL");
+  FMGP_REQUIRE(n >= 2 && n < INT32_MAX, "n = %lld out of range [2, 2^31)", (long long)n);
+  FMGP_REQUIRE(d >= 1, "d = %d must be >= 1", d);
+  FMGP_REQUIRE(kq >= 1 && kq <= n - 1 && kq <= kMaxK, "kq = %d must be in [1, min(n-1, %d)]",
+               kq, kMaxK);
+  FMGP_REQUIRE(flags == 0, "flags must be 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  return knn_self(X, dtype, n, d, kq, nbr_out, dist_out, tune_params(), ws, s);
+}
+
+static int validate_block_args(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                               int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld,
+                               const fmgp_kernel* kernel, fmgp_precision precision) {
+  if (!dtype_ok(dtype) || !kernel_ok(kernel) || !prec_ok(precision)) return FMGP_EINVAL;
+  FMGP_REQUIRE(X && Y && nbr, "X, Y and nbr must be non-NULL");
+  FMGP_REQUIRE(n >= 1 && n < INT32_MAX, "n = %lld out of range [1, 2^31)", (long long)n);
+  FMGP_REQUIRE(d >= 1, "d = %d must be >= 1", d);
+  FMGP_REQUIRE(r >= 1, "r = %d must be >= 1", r);
+  (void)nbr_ld;
+  return FMGP_OK;
+}
+
+int fmgp_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                    int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                    const fmgp_kernel* kernel, fmgp_precision precision, void* C_out,
+                    int8_t* status_out, void* stream) {
+  g_err[0] = 0;
+  int rc = validate_block_args(X, dtype, Y, n, d, r, k > 1 ? nbr : (const int32_t*)X, nbr_ld,
+                               kernel, precision);
+  if (rc) return rc;
+  FMGP_REQUIRE(C_out, "C_out must be non-NULL");
+  FMGP_REQUIRE(k >= 1 && k <= n && k <= kMaxK, "k = %d must be in [1, min(n, %d)]", k, kMaxK);
+  FMGP_REQUIRE(nbr_ld >= k - 1 && nbr_ld >= 0, "nbr_ld = %d must be >= k-1 = %d", nbr_ld, k - 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  int* fails = ws.get<int>(1);
+  if (!fails) return FMGP_ENOMEM;
+  FMGP_CUDA_TRY(cudaMemsetAsync(fails, 0, sizeof(int), s));
+  BlockArgs a{};
+  a.Y = Y;
+  a.nbr = nbr;
+  a.C = C_out;
+  a.status = status_out;
+  a.fail_count = fails;
+  a.n = n;
+  a.count = n;
+  a.d = d;
+  a.r = r;
+  a.ld = nbr_ld;
+  a.k = k;
+  a.kp = make_kparams(*kernel);
+  const int xb = dtype == FMGP_F64 ? 8 : 4;
+  if (precision == FMGP_PREC_FP64) {
+    a.layout = block_layout(k, d, r, xb, false);
+  } else {
+    a.layout = block_layout(k, d, r, xb, true);
+    a.layout.bytes_per_warp += block_mixed_extra_bytes(k, d, r);
+  }
+  if (a.layout.bytes_per_warp > 220 * 1024) {
+    set_error("neighbourhood k=%d d=%d r=%d needs %zu bytes of shared memory per warp", k, d, r,
+              a.layout.bytes_per_warp);
+    return FMGP_EUNSUPPORTED;
+  }
+  const int warps = pick_warps(a.layout, tune_params().block_warps);
+  rc = precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, false, warps, s)
+                                   : launch_block_mixed(a, X, dtype, false, warps, s);
+  if (rc) return rc;
+  if (!status_out) {
+    int h = 0;
+    FMGP_CUDA_TRY(cudaMemcpyAsync(&h, fails, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FMGP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+      set_error("%d neighbourhood blocks were not positive definite", h);
+      return FMGP_ENOTSPD;
+    }
+  }
+  return FMGP_OK;
+}
+
+int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
+                 int32_t nbr_ld, const void* C, int32_t k, int32_t r, const fmgp_kernel* kernel,
+                 fmgp_precision precision, const void* Z, int64_t m, double* Yhat_out,
+                 int32_t* nearest_out, void* stream) {
+  g_err[0] = 0;
+  if (!dtype_ok(dtype) || !kernel_ok(kernel) || !prec_ok(precision)) return FMGP_EINVAL;
+  FMGP_REQUIRE(m >= 0, "m = %lld must be >= 0", (long long)m);
+  FMGP_REQUIRE(X && C, "X and C must be non-NULL");
+  FMGP_REQUIRE(n >= 1 && n < INT32_MAX, "n = %lld out of range [1, 2^31)", (long long)n);
+  FMGP_REQUIRE(d >= 1 && r >= 1, "d and r must be >= 1");
+  FMGP_REQUIRE(k >= 1 && k <= n && k <= kMaxK, "k = %d must be in [1, min(n, %d)]", k, kMaxK);
+  FMGP_REQUIRE(k == 1 || nbr, "nbr must be non-NULL when k > 1");
+  FMGP_REQUIRE(nbr_ld >= k - 1, "nbr_ld = %d must be >= k-1", nbr_ld);
+  if (m == 0) return FMGP_OK;
+  FMGP_REQUIRE(Z && Yhat_out, "Z and Yhat_out must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  int32_t* near = nearest_out;
+  if (!near) {
+    near = ws.get<int32_t>(m);
+    if (!near) return FMGP_ENOMEM;
+  }
+  int rc = nearest_train(X, dtype, n, d, Z, m, near, tune_params(), ws, s);
+  if (rc) return rc;
+  return gather_dot(X, dtype, n, d, nbr, nbr_ld, C, k, r, make_kparams(*kernel), precision, Z, m,
+                    near, Yhat_out, s);
+}
+
+int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                         int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                         const int64_t* batch, int64_t b, const fmgp_kernel* kernel,
+                         fmgp_precision precision, double* Q_out, double* resid_out,
+                         void* stream) {
+  g_err[0] = 0;
+  int rc = validate_block_args(X, dtype, Y, n, d, r, nbr, nbr_ld, kernel, precision);
+  if (rc) return rc;
+  FMGP_REQUIRE(Q_out && batch, "Q_out and batch must be non-NULL");
+  FMGP_REQUIRE(n >= 2, "LOOCV needs n >= 2");
+  FMGP_REQUIRE(k >= 1 && k <= n - 1 && k <= kMaxK, "k = %d must be in [1, min(n-1, %d)]", k,
+               kMaxK);
+  FMGP_REQUIRE(nbr_ld >= k, "nbr_ld = %d must be >= k = %d", nbr_ld, k);
+  FMGP_REQUIRE(b >= 1, "batch size b = %lld must be >= 1", (long long)b);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  int* fails = ws.get<int>(1);
+  double* qd = ws.get<double>(1);
+  double* resid = resid_out ? resid_out : ws.get<double>(b);
+  if (!fails || !qd || !resid) return FMGP_ENOMEM;
+  FMGP_CUDA_TRY(cudaMemsetAsync(fails, 0, sizeof(int), s));
+  BlockArgs a{};
+  a.Y = Y;
+  a.nbr = nbr;
+  a.batch = batch;
+  a.resid = resid;
+  a.fail_count = fails;
+  a.n = n;
+  a.count = b;
+  a.d = d;
+  a.r = r;
+  a.ld = nbr_ld;
+  a.k = k;
+  a.kp = make_kparams(*kernel);
+  const int xb = dtype == FMGP_F64 ? 8 : 4;
+  if (precision == FMGP_PREC_FP64) {
+    a.layout = block_layout(k, d, r, xb, false);
+  } else {
+    a.layout = block_layout(k, d, r, xb, true);
+    a.layout.bytes_per_warp += block_mixed_extra_bytes(k, d, r);
+  }
+  if (a.layout.bytes_per_warp > 220 * 1024) {
+    set_error("neighbourhood k=%d d=%d r=%d needs %zu bytes of shared memory per warp", k, d, r,
+              a.layout.bytes_per_warp);
+    return FMGP_EUNSUPPORTED;
+  }
+  const int warps = pick_warps(a.layout, tune_params().block_warps);
+  rc = precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, true, warps, s)
+                                   : launch_block_mixed(a, X, dtype, true, warps, s);
+  if (rc) return rc;
+  FMGP_LAUNCH(loocv_reduce<<<1, 1024, 0, s>>>(resid, b, qd));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  int h = 0;
+  FMGP_CUDA_TRY(cudaMemcpyAsync(Q_out, qd, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FMGP_CUDA_TRY(cudaMemcpyAsync(&h, fails, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FMGP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h) {
+    set_error("%d LOOCV blocks were not positive definite", h);
+    return FMGP_ENOTSPD;
+  }
+  return FMGP_OK;
+}
+
+}  // extern "C"

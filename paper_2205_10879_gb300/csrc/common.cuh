@@ -1,0 +1,149 @@
+// Shared device/host helpers of libfmgp (CUDA path only).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <limits.h>
+#include <string>
+#include "../../include/fmgp.h"
+
+namespace fmgp {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxK = 128;  // largest neighbourhood a block kernel handles
+
+// Kernel hyperparameters as the device sees them.  phi(D) is the correlation
+// at squared distance D (Eq. 3; RBF as its nu -> infinity limit).
+struct KParams {
+  int kind;          // FMGP_KERNEL_MATERN / FMGP_KERNEL_RBF
+  int nu2;           // 2*nu for Matern: 1, 3 or 5
+  double inv_rho;    // 1 / rho
+  double half_inv_rho2;  // 1 / (2 rho^2)
+  double var;        // sigma^2
+  double diag;       // sigma^2 (1 + tau^2)
+  float inv_rho_f, half_inv_rho2_f, var_f, diag_f;
+};
+
+inline KParams make_kparams(const fmgp_kernel& k) {
+  KParams p;
+  p.kind = k.kind;
+  p.nu2 = (int)(2.0 * k.nu + 0.5);
+  p.inv_rho = 1.0 / k.length_scale;
+  p.half_inv_rho2 = 0.5 / (k.length_scale * k.length_scale);
+  p.var = k.variance;
+  p.diag = k.variance * (1.0 + k.nugget);
+  p.inv_rho_f = (float)p.inv_rho;
+  p.half_inv_rho2_f = (float)p.half_inv_rho2;
+  p.var_f = (float)p.var;
+  p.diag_f = (float)p.diag;
+  return p;
+}
+
+// Matern closed forms at half-integer nu (Eq. 3 with K_nu for nu = 1/2, 3/2,
+// 5/2) and the RBF limit, in FP64 with CUDA's exp/sqrt.
+__device__ __forceinline__ double phi64(const KParams& p, double D) {
+  if (p.kind == FMGP_KERNEL_RBF) return exp(-D * p.half_inv_rho2);
+  double u = sqrt(D) * p.inv_rho;
+  if (p.nu2 == 1) return exp(-u);
+  if (p.nu2 == 3) {
+    const double s3 = 1.7320508075688772;
+    double a = s3 * u;
+    return (1.0 + a) * exp(-a);
+  }
+  const double s5 = 2.23606797749979;
+  double a = s5 * u;
+  return (1.0 + a + a * a * (1.0 / 3.0)) * exp(-a);
+}
+
+__device__ __forceinline__ float phi32(const KParams& p, float D) {
+  if (p.kind == FMGP_KERNEL_RBF) return __expf(-D * p.half_inv_rho2_f);
+  float u = sqrtf(D) * p.inv_rho_f;
+  if (p.nu2 == 1) return __expf(-u);
+  if (p.nu2 == 3) {
+    float a = 1.7320508f * u;
+    return (1.0f + a) * __expf(-a);
+  }
+  float a = 2.2360680f * u;
+  return (1.0f + a + a * a * (1.0f / 3.0f)) * __expf(-a);
+}
+
+template <typename T> __device__ __forceinline__ double ld64(const T* p) { return (double)(*p); }
+
+// Canonical ranking key (library-wide convention): FP64, left to right, each
+// operation rounded on its own; the first term is t0*t0 (0 + t0*t0 is exact).
+template <typename T>
+__device__ __forceinline__ double canon_key(const double* q, const T* x, int d) {
+  double t = __dsub_rn(q[0], (double)x[0]);
+  double s = __dmul_rn(t, t);
+  for (int j = 1; j < d; ++j) {
+    t = __dsub_rn(q[j], (double)x[j]);
+    s = __dadd_rn(s, __dmul_rn(t, t));
+  }
+  return s;
+}
+
+// (key, index) lexicographic order on the IEEE bit patterns of non-negative
+// doubles (which order like unsigned integers), avoiding FP64 compares.
+__device__ __forceinline__ bool key_less(unsigned long long ka, int ia, unsigned long long kb,
+                                         int ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// Round a non-negative double given by its bits up to a float (>= value),
+// using integer operations only.  Used to compare FP32 lower bounds with FP64
+// keys without FP64 instructions.
+__device__ __forceinline__ float key_bits_to_float_up(unsigned long long b) {
+  if (b >= 0x7ff0000000000000ull) return __int_as_float(0x7f800000);  // inf / nan -> inf
+  int e = (int)(b >> 52);
+  unsigned long long mant = b & 0xfffffffffffffull;
+  int fe = e - 1023 + 127;
+  if (fe >= 255) return __int_as_float(0x7f800000);
+  if (fe <= 0) return 1.1754944e-38f;  // below FLT_MIN: FLT_MIN is an upper bound
+  unsigned int fm = (unsigned int)(mant >> 29);
+  unsigned int bits = ((unsigned int)fe << 23) | fm;
+  return __uint_as_float(bits + 1u);  // next float up (truncation was downward)
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+
+// ------------------------------------------------------------------ host --
+// Every kernel launch of the library goes through FMGP_LAUNCH so that
+// fmgp_kernel_launches() can report how many kernels were enqueued.
+void note_launch();
+#define FMGP_LAUNCH(...)   \
+  do {                     \
+    __VA_ARGS__;           \
+    ::fmgp::note_launch(); \
+  } while (0)
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define FMGP_CUDA_TRY(call)                                  \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
+    if (_e != cudaSuccess) return ::fmgp::cuda_fail(_e, #call); \
+  } while (0)
+
+// Stream-ordered workspace: every allocation is returned on the same stream
+// when the object goes out of scope.
+class Workspace {
+ public:
+  explicit Workspace(cudaStream_t s) : stream_(s) {}
+  ~Workspace();
+  // Returns nullptr (and records the error) on failure.
+  void* alloc(size_t bytes);
+  template <typename T> T* get(size_t count) { return (T*)alloc(count * sizeof(T)); }
+
+ private:
+  cudaStream_t stream_;
+  void* ptrs_[32];
+  int count_ = 0;
+};
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+int num_sms();
+
+}  // namespace fmgp

@@ -1,0 +1,225 @@
+// A1 (self kNN table) and the nearest-training-point search of A4.
+//   d <= 3 : uniform grid, one warp per query, rings of cells in order of
+//            Chebyshev distance with box pruning and an exact stop test.
+//   d >= 4 : tiled scan of all training points; a CTA of 8 warps (8 queries)
+//            stages 32 candidate rows at a time in shared memory as FP32.
+// Both rank on the canonical FP64 key; FP32 is used only for lower bounds.
+#include "knn.cuh"
+#include "topk.cuh"
+
+namespace fmgp {
+namespace {
+
+constexpr float kU = 5.9604645e-8f;  // 2^-24
+
+// ---------------------------------------------------------------- grid ----
+template <int D, int L>
+__global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
+                                                            int32_t* nbr_out, double* dist_out) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= gv.n) return;
+  const GridGeom g = *gv.geom;
+  double q64[D];
+  float qf[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    q64[j] = gv.xs64[w * D + j];
+    qf[j] = gv.xs32[w * D + j];
+  }
+  const int qi = gv.ids[w];
+  const float qs = query_slack<D>(qf);
+  const float margin = g.margin + qs;
+  const float cerr = g.conv_err + (g.conv_err > 0.f ? qs : 0.f);
+  int cq[3] = {0, 0, 0};
+  cell_of<D>(g, qf, cq);
+  WarpTopK<L> top;
+  top.init(kq);
+  for (int r = 0;; ++r) {
+    for_ring_segments<D>(r, cq, g.G, [&](int c0a, int c0b, int c1, int c2) {
+      if (top.full() && box_lower<D>(g, qf, margin, c0a, c0b, c1, c2) > top.t_up) return;
+      const int s0 = gv.cell_start[cell_linear(c0a, c1, c2, g.G, D)];
+      const int e0 = gv.cell_start[cell_linear(c0b, c1, c2, g.G, D) + 1];
+      for (int base = s0; base < e0; base += 32) {
+        const int j = base + lane;
+        unsigned long long ck = ~0ull;
+        int ci = INT_MAX;
+        if (j < e0) {
+          const int id = gv.ids[j];
+          if (id != qi) {
+            float xf[D];
+#pragma unroll
+            for (int t = 0; t < D; ++t) xf[t] = gv.xs32[(int64_t)j * D + t];
+            if (dist_lower_f32<D>(qf, xf, cerr) <= top.t_up) {
+              ck = dbits(canon_key<double>(q64, gv.xs64 + (int64_t)j * D, D));
+              ci = id;
+            }
+          }
+        }
+        top.offer(ck, ci, lane);
+      }
+    });
+    if (top.full() && outside_lower<D>(g, qf, margin, cq, r) > top.t_up) break;
+    if (r >= g.G) break;
+  }
+  top.store(kq, lane, nbr_out + (int64_t)qi * kq, dist_out ? dist_out + (int64_t)qi * kq : nullptr);
+}
+
+// ---------------------------------------------------------- brute force ----
+constexpr int kBfWarps = 8;
+constexpr int kBfTile = 32;
+constexpr int kBfChunk = 256;  // feature columns staged per pass
+
+__global__ void maxabs_kernel(const void* X, int f64, int64_t count, unsigned int* out_bits) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v = f64 ? fabsf((float)((const double*)X)[i]) : fabsf(((const float*)X)[i]);
+    m = fmaxf(m, v);
+  }
+  for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));
+}
+
+// Each warp owns one query; each lane owns one candidate of the staged tile.
+// The FP32 partial distances over feature chunks give a lower bound
+// (relative rounding of d non-negative terms plus the FP64->FP32 conversion
+// slack); only candidates whose bound does not exceed the current k-th key
+// get their canonical FP64 key.
+template <typename T, int L>
+__global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
+    const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int exclude_self,
+    const unsigned int* maxabs_bits, int32_t* idx_out, double* key_out) {
+  extern __shared__ float sm[];
+  const int ld = d | 1;  // odd stride: conflict-free column reads
+  float* tile = sm;                          // kBfTile x ld (chunk of columns)
+  float* qs = sm + kBfTile * ld;             // kBfWarps x ld
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * kBfWarps + wid;
+  const bool qvalid = q < m;
+  const float M = __uint_as_float(*maxabs_bits);
+  const float cerr = (sizeof(T) == 8) ? 2.5f * kU * M : 0.f;
+  const float rel = 1.0f - (2.0f * d + 8.0f) * kU;
+  // stage this CTA's queries (FP32)
+  for (int e = threadIdx.x; e < kBfWarps * d; e += blockDim.x) {
+    const int w = e / d, j = e % d;
+    const int64_t qq = (int64_t)blockIdx.x * kBfWarps + w;
+    qs[w * ld + j] = qq < m ? (float)Q[qq * d + j] : 0.f;
+  }
+  WarpTopK<L> top;
+  top.init(kq);
+  const float* myq = qs + wid * ld;
+  for (int64_t base = 0; base < n; base += kBfTile) {
+    float acc = 0.f;
+    for (int c0 = 0; c0 < d; c0 += kBfChunk) {
+      const int cw = min(kBfChunk, d - c0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kBfTile * cw; e += blockDim.x) {
+        const int rr = e / cw, j = e % cw;
+        const int64_t row = base + rr;
+        tile[rr * ld + j] = row < n ? (float)X[row * d + c0 + j] : 0.f;
+      }
+      __syncthreads();
+      const float* trow = tile + lane * ld;
+      for (int j = 0; j < cw; ++j) {
+        float t = fabsf(myq[c0 + j] - trow[j]) * (1.0f - 2.0f * kU) - cerr;
+        t = fmaxf(t, 0.f);
+        acc = fmaf(t, t, acc);
+      }
+    }
+    const int64_t cand = base + lane;
+    unsigned long long ck = ~0ull;
+    int ci = INT_MAX;
+    if (qvalid && cand < n && !(exclude_self && cand == q) && acc * rel <= top.t_up) {
+      // canonical FP64 key from the original rows
+      const T* xr = X + cand * d;
+      const T* qr = Q + q * d;
+      double t = __dsub_rn((double)qr[0], (double)xr[0]);
+      double s = __dmul_rn(t, t);
+      for (int j = 1; j < d; ++j) {
+        t = __dsub_rn((double)qr[j], (double)xr[j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+      }
+      ck = dbits(s);
+      ci = (int)cand;
+    }
+    top.offer(ck, ci, lane);
+  }
+  if (qvalid) top.store(kq, lane, idx_out + q * kq, key_out ? key_out + q * kq : nullptr);
+}
+
+template <int D>
+int launch_grid_self(const GridView& gv, int kq, int32_t* nbr, double* dist, cudaStream_t s) {
+  const int blocks = ceil_div(gv.n * 32, 256);
+  if (kq <= 32) FMGP_LAUNCH(knn_grid_self_kernel<D, 1><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
+  else if (kq <= 64) FMGP_LAUNCH(knn_grid_self_kernel<D, 2><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
+  else if (kq <= 96) FMGP_LAUNCH(knn_grid_self_kernel<D, 3><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
+  else FMGP_LAUNCH(knn_grid_self_kernel<D, 4><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
+template <typename T, int L>
+int launch_brute_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
+                   const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s) {
+  const int ld = d | 1;
+  const size_t smem = sizeof(float) * (size_t)(kBfTile + kBfWarps) * ld;
+  if (smem > 200 * 1024) {
+    set_error("brute-force kNN: d = %d needs %zu bytes of shared memory", d, smem);
+    return FMGP_EUNSUPPORTED;
+  }
+  auto kern = knn_brute_kernel<T, L>;
+  FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(X, n, d, Q, m, kq, excl, mx, idx, key));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
+template <typename T>
+int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
+                 Workspace& ws, int32_t* idx, double* key, cudaStream_t s) {
+  unsigned int* mx = ws.get<unsigned int>(1);
+  if (!mx) return FMGP_ENOMEM;
+  FMGP_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), s));
+  const int blocks = (int)std::min<int64_t>(ceil_div(n * d, 256), (int64_t)num_sms() * 8);
+  FMGP_LAUNCH(maxabs_kernel<<<blocks, 256, 0, s>>>(X, sizeof(T) == 8, n * d, mx));
+  if (Q != X) {
+    const int qb = (int)std::min<int64_t>(ceil_div(m * d, 256), (int64_t)num_sms() * 8);
+    if (m > 0) FMGP_LAUNCH(maxabs_kernel<<<qb, 256, 0, s>>>(Q, sizeof(T) == 8, m * d, mx));
+  }
+  if (kq <= 32) return launch_brute_t<T, 1>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
+  if (kq <= 64) return launch_brute_t<T, 2>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
+  if (kq <= 96) return launch_brute_t<T, 3>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
+  return launch_brute_t<T, 4>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
+}
+
+}  // namespace
+
+int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t* nbr,
+             double* dist, const TuneParams& tp, Workspace& ws, cudaStream_t stream) {
+  if (d <= kGridMaxD) {
+    GridView gv;
+    int rc = build_grid(X, dtype, n, d, tp.grid_target, ws, stream, &gv);
+    if (rc) return rc;
+    if (d == 1) return launch_grid_self<1>(gv, kq, nbr, dist, stream);
+    if (d == 2) return launch_grid_self<2>(gv, kq, nbr, dist, stream);
+    return launch_grid_self<3>(gv, kq, nbr, dist, stream);
+  }
+  if (dtype == FMGP_F64)
+    return launch_brute<double>((const double*)X, n, d, (const double*)X, n, kq, 1, ws, nbr, dist,
+                                stream);
+  return launch_brute<float>((const float*)X, n, d, (const float*)X, n, kq, 1, ws, nbr, dist,
+                             stream);
+}
+
+int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
+                    int kq, int32_t* idx, double* key, Workspace& ws, cudaStream_t stream) {
+  if (m == 0) return FMGP_OK;
+  if (dtype == FMGP_F64)
+    return launch_brute<double>((const double*)X, n, d, (const double*)Q, m, kq, 0, ws, idx, key,
+                                stream);
+  return launch_brute<float>((const float*)X, n, d, (const float*)Q, m, kq, 0, ws, idx, key,
+                             stream);
+}
+
+}  // namespace fmgp

@@ -1,0 +1,231 @@
+// A2 + A3 (Eq. 6) and A6 (Eqs. 4-5) in FP64: one warp per neighbourhood.
+// The warp stages the neighbourhood's features and responses in shared
+// memory, assembles the lower triangle of K_S there, factors it by a
+// row-per-lane Crout Cholesky, solves L L^T W = Y_S by column sweeps, and
+// either stores W as the row C_i (precompute) or dots it with the
+// cross-covariance of x_i to form the leave-one-out residual (LOOCV).
+#include "block.cuh"
+
+namespace fmgp {
+namespace {
+
+constexpr int kMaxSlots = kMaxK / 32;
+
+__device__ __forceinline__ void pair_of(int p, int& a, int& b) {
+  int x = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
+  while (x * (x - 1) / 2 > p) --x;
+  while ((x + 1) * x / 2 <= p) ++x;
+  a = x;
+  b = p - x * (x - 1) / 2;
+}
+
+template <typename T, bool LOO>
+__global__ void __launch_bounds__(256) block_f64_kernel(BlockArgs args, const T* X) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BlockLayout lay = args.layout;
+  const int wpb = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem + (size_t)wid * lay.bytes_per_warp;
+  double* L = (double*)(base + lay.off_L);
+  double* W = (double*)(base + lay.off_W);
+  double* invd = (double*)(base + lay.off_inv);
+  T* XS = (T*)(base + lay.off_X);
+  int* S = (int*)(base + lay.off_S);
+  volatile int* flag = (int*)(base + lay.off_flag);
+  const int k = args.k, d = args.d, r = args.r, ldl = lay.ldl;
+  const KParams kp = args.kp;
+
+  for (int64_t item = (int64_t)blockIdx.x * wpb + wid; item < args.count;
+       item += (int64_t)gridDim.x * wpb) {
+    int64_t i = LOO ? args.batch[item] : item;
+    // S: precompute S_i = [i, N_i]; LOOCV N_i (self excluded)
+    bool bad = false;
+    if (i < 0 || i >= args.n) { bad = true; i = 0; }
+    for (int a = lane; a < k; a += 32) {
+      int64_t idx = LOO ? (int64_t)args.nbr[i * args.ld + a]
+                        : (a == 0 ? i : (int64_t)args.nbr[i * args.ld + a - 1]);
+      if (idx < 0 || idx >= args.n) { bad = true; idx = 0; }
+      S[a] = (int)idx;
+    }
+    bad = __any_sync(kFull, bad);
+    __syncwarp();
+    for (int e = lane; e < k * d; e += 32) {
+      const int a = e / d, t = e - a * d;
+      XS[e] = X[(int64_t)S[a] * d + t];
+    }
+    for (int e = lane; e < k * r; e += 32) {
+      const int a = e / r, c = e - a * r;
+      W[e] = args.Y[(int64_t)S[a] * r + c];
+    }
+    __syncwarp();
+    // assemble: lower triangle off-diagonal, then the diagonal
+    const int npairs = k * (k - 1) / 2;
+    for (int p = lane; p < npairs; p += 32) {
+      int a, b;
+      pair_of(p, a, b);
+      double D = 0.0;
+      for (int t = 0; t < d; ++t) {
+        const double diff = (double)XS[a * d + t] - (double)XS[b * d + t];
+        D = fma(diff, diff, D);
+      }
+      L[a * ldl + b] = kp.var * phi64(kp, D);
+    }
+    for (int a = lane; a < k; a += 32) L[a * ldl + a] = kp.diag;
+    if (lane == 0) *flag = 0;
+    __syncwarp();
+    // Cholesky, Crout order: step j forms column j of L
+    for (int j = 0; j < k; ++j) {
+      double dots[kMaxSlots];
+#pragma unroll
+      for (int s = 0; s < kMaxSlots; ++s) {
+        const int row = lane + 32 * s;
+        dots[s] = 0.0;
+        if (row >= j && row < k) {
+          double acc = 0.0;
+          const double* lr = L + row * ldl;
+          const double* lj = L + j * ldl;
+          for (int p = 0; p < j; ++p) acc = fma(lr[p], lj[p], acc);
+          dots[s] = acc;
+        }
+      }
+      if (lane == (j & 31)) {
+        double dj = dots[0];
+#pragma unroll
+        for (int s = 1; s < kMaxSlots; ++s)
+          if (s == (j >> 5)) dj = dots[s];
+        const double v = L[j * ldl + j] - dj;
+        if (!(v > 0.0)) {
+          *flag = 1;
+        } else {
+          const double ljj = sqrt(v);
+          L[j * ldl + j] = ljj;
+          invd[j] = 1.0 / ljj;
+        }
+      }
+      __syncwarp();
+      if (*flag) break;
+      const double inv = invd[j];
+#pragma unroll
+      for (int s = 0; s < kMaxSlots; ++s) {
+        const int row = lane + 32 * s;
+        if (row > j && row < k) L[row * ldl + j] = (L[row * ldl + j] - dots[s]) * inv;
+      }
+      __syncwarp();
+    }
+    const bool fail = (*flag != 0) || bad;
+    if (!fail) {
+      // forward sweep: L v = y
+      for (int p = 0; p < k; ++p) {
+        if (lane == (p & 31))
+          for (int c = 0; c < r; ++c) W[p * r + c] *= invd[p];
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < kMaxSlots; ++s) {
+          const int row = lane + 32 * s;
+          if (row > p && row < k) {
+            const double l = L[row * ldl + p];
+            for (int c = 0; c < r; ++c) W[row * r + c] = fma(-l, W[p * r + c], W[row * r + c]);
+          }
+        }
+        __syncwarp();
+      }
+      // back sweep: L^T w = v
+      for (int p = k - 1; p >= 0; --p) {
+        if (lane == (p & 31))
+          for (int c = 0; c < r; ++c) W[p * r + c] *= invd[p];
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < kMaxSlots; ++s) {
+          const int row = lane + 32 * s;
+          if (row < p) {
+            const double l = L[p * ldl + row];
+            for (int c = 0; c < r; ++c) W[row * r + c] = fma(-l, W[p * r + c], W[row * r + c]);
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (!LOO) {
+      double* Ci = (double*)args.C + i * (int64_t)k * r;
+      for (int e = lane; e < k * r; e += 32) Ci[e] = fail ? 0.0 : W[e];
+      if (args.status && lane == 0)
+        args.status[i] = bad ? FMGP_BLOCK_BAD_INDEX : (fail ? FMGP_BLOCK_NOT_SPD : FMGP_BLOCK_OK);
+      if (fail && lane == 0) atomicAdd(args.fail_count, 1);
+    } else {
+      // leave-one-out residual of x_i against its neighbours
+      double kx[kMaxSlots];
+      const T* xi = X + i * d;
+#pragma unroll
+      for (int s = 0; s < kMaxSlots; ++s) {
+        const int a = lane + 32 * s;
+        kx[s] = 0.0;
+        if (!fail && a < k) {
+          double D = 0.0;
+          for (int t = 0; t < d; ++t) {
+            const double diff = (double)xi[t] - (double)XS[a * d + t];
+            D = fma(diff, diff, D);
+          }
+          kx[s] = kp.var * phi64(kp, D);
+        }
+      }
+      double e2 = 0.0;
+      for (int c = 0; c < r; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int s = 0; s < kMaxSlots; ++s) {
+          const int a = lane + 32 * s;
+          if (a < k) acc = fma(kx[s], W[a * r + c], acc);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+        const double e = args.Y[i * r + c] - acc;
+        e2 = fma(e, e, e2);
+      }
+      if (lane == 0) {
+        args.resid[item] = fail ? __longlong_as_double(0x7ff8000000000000ll) : e2;
+        if (fail) atomicAdd(args.fail_count, 1);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+BlockLayout block_layout(int k, int d, int r, int xbytes, bool f32_factor) {
+  BlockLayout l;
+  const int fb = f32_factor ? 4 : 8;
+  l.ldl = (k % 2 == 0) ? k + 1 : k;
+  auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  size_t off = 0;
+  l.off_L = off;    off += up((size_t)k * l.ldl * fb);
+  l.off_W = off;    off += up((size_t)k * r * 8);
+  l.off_inv = off;  off += up((size_t)k * 8);
+  l.off_X = off;    off += up((size_t)k * d * xbytes);
+  l.off_S = off;    off += up((size_t)k * 4);
+  l.off_flag = off; off += 16;
+  l.off_extra = off;
+  l.bytes_per_warp = off;
+  return l;
+}
+
+int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo, int warps,
+                     cudaStream_t stream) {
+  const size_t smem = a.layout.bytes_per_warp * warps;
+  const int sms = num_sms();
+  const int64_t need = (a.count + warps - 1) / warps;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 16));
+  if (dtype == FMGP_F64) {
+    auto kern = loo ? block_f64_kernel<double, true> : block_f64_kernel<double, false>;
+    FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const double*)X));
+  } else {
+    auto kern = loo ? block_f64_kernel<float, true> : block_f64_kernel<float, false>;
+    FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const float*)X));
+  }
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
+}  // namespace fmgp

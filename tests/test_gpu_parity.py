@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  kNN indices and keys bit-exact; FP64 means within
+rel-RMS 1e-10; mixed means within rel-RMS 1e-5."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2205_10879_gb300 import _binding as fb
+from paper_2205_10879_gb300 import workloads as wl
+from gpu_helpers import FP64_TOL, MIXED_TOL, coeffs_to_f64, dev, kern_pair, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_pipeline(W, k, kq, precision, gk):
+    X = dev(W.X)
+    Y = dev(W.Y)
+    Z = dev(W.Z)
+    nbr, dist = fb.fmgp_build_knn(X, kq, with_dist=True)
+    C, st = fb.fmgp_precompute(X, Y, nbr, k, gk, precision)
+    yh, near = fb.fmgp_predict(X, nbr, C, k, gk, Z, precision)
+    torch.cuda.synchronize()
+    return nbr, dist, C, st, yh, near
+
+
+# ------------------------------------------------------------------ kNN --
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_knn_integer_grid_ties_bitexact(cuda, d):
+    rng = np.random.default_rng(100 + d)
+    n = 3000
+    X = rng.integers(0, 12 if d > 1 else 400, size=(n, d)).astype(np.float64)
+    for kq in [1, 9, 33, 70]:
+        nbr, dist = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
+        ref_i, ref_k = oracle.self_knn(X, kq)
+        np.testing.assert_array_equal(nbr.cpu().numpy(), ref_i)
+        np.testing.assert_array_equal(dist.cpu().numpy(), ref_k)
+
+
+def test_knn_tiny_bitexact(cuda):
+    W = wl.tiny()
+    nbr, dist = fb.fmgp_build_knn(dev(W.X), 30, with_dist=True)
+    ref_i, ref_k = oracle.self_knn(W.X, 30)
+    np.testing.assert_array_equal(nbr.cpu().numpy(), ref_i)
+    np.testing.assert_array_equal(dist.cpu().numpy(), ref_k)
+
+
+@pytest.mark.parametrize("kq", [1, 49, 127])
+def test_knn_spatial_sample_bitexact(cuda, kq):
+    W = wl.spatial(n=40_000, m=10)
+    nbr, dist = fb.fmgp_build_knn(dev(W.X), kq, with_dist=True)
+    rows = np.random.default_rng(0).choice(W.n, 300, replace=False)
+    ref_i, ref_k = oracle.knn(W.X, W.X[rows], kq, rows)
+    np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
+    np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
+
+
+@pytest.mark.parametrize("d,dtype", [(4, np.float64), (16, np.float32), (64, np.float64),
+                                     (784, np.float32)])
+def test_knn_bruteforce_bitexact(cuda, d, dtype):
+    rng = np.random.default_rng(200 + d)
+    n = 700
+    X = rng.random((n, d)).astype(dtype)
+    X[rng.random((n, d)) < 0.8] = 0
+    X[10] = X[20]  # exact duplicate
+    for kq in [1, 29]:
+        nbr, dist = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
+        ref_i, ref_k = oracle.self_knn(X.astype(np.float64), kq)
+        np.testing.assert_array_equal(nbr.cpu().numpy(), ref_i)
+        np.testing.assert_array_equal(dist.cpu().numpy(), ref_k)
+
+
+def test_nearest_test_point_bitexact(cuda):
+    W = wl.spatial(n=30_000, m=5_000)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, 4)
+    C = torch.zeros((W.n, 5, 1), dtype=torch.float64, device="cuda")
+    _, gk = kern_pair(W.kernel)
+    # test points outside the training box and exactly on training points too
+    Z = np.concatenate([W.Z, W.X[:50], W.Z[:20] * 1.5 - 0.25])
+    _, near = fb.fmgp_predict(X, nbr, C, 5, gk, dev(Z))
+    ref, _ = oracle.knn(W.X, Z, 1)
+    np.testing.assert_array_equal(near.cpu().numpy(), ref[:, 0])
+
+
+# ------------------------------------------------------- precompute/predict --
+def test_fp64_pipeline_tiny(cuda):
+    W = wl.tiny()
+    ok, gk = kern_pair(W.kernel)
+    nbr, dist, C, st, yh, near = _gpu_pipeline(W, 30, 29, fb.PREC_FP64, gk)
+    ref_nbr, _ = oracle.self_knn(W.X, 29)
+    np.testing.assert_array_equal(nbr.cpu().numpy(), ref_nbr)
+    Cr, str_ = oracle.precompute(W.X, W.Y, ref_nbr, 30, ok)
+    assert not st.cpu().numpy().any() and not str_.any()
+    assert rel_rms(C.cpu().numpy(), Cr) < FP64_TOL
+    yr, nr = oracle.predict(W.X, ref_nbr, Cr, ok, W.Z)
+    np.testing.assert_array_equal(near.cpu().numpy(), nr)
+    assert rel_rms(yh.cpu().numpy(), yr) < FP64_TOL
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5])
+def test_fp64_pipeline_spatial_shrunk(cuda, nu):
+    W = wl.spatial(n=20_000, m=3_000, nu=nu)
+    ok, gk = kern_pair(W.kernel)
+    nbr, dist, C, st, yh, near = _gpu_pipeline(W, 50, 49, fb.PREC_FP64, gk)
+    nb = nbr.cpu().numpy()
+    rows = np.random.default_rng(1).choice(W.n, 400, replace=False)
+    ref_i, _ = oracle.knn(W.X, W.X[rows], 49, rows)
+    np.testing.assert_array_equal(nb[rows], ref_i)
+    Cr, _ = oracle.precompute(W.X, W.Y, nb, 50, ok, rows=rows)
+    assert rel_rms(C.cpu().numpy()[rows], Cr) < FP64_TOL
+    Cfull, _ = oracle.precompute(W.X, W.Y, nb, 50, ok)
+    yr, nr = oracle.predict(W.X, nb, Cfull, ok, W.Z)
+    np.testing.assert_array_equal(near.cpu().numpy(), nr)
+    assert rel_rms(yh.cpu().numpy(), yr) < FP64_TOL
+
+
+def test_fp64_multi_response_highdim_small(cuda):
+    W = wl.highdim(n=1500, m=300, d=784, r=10, k=30)
+    ok, gk = kern_pair(W.kernel)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, 29)
+    nb = nbr.cpu().numpy()
+    ref_i, _ = oracle.self_knn(W.X.astype(np.float64), 29)
+    np.testing.assert_array_equal(nb, ref_i)
+    C, st = fb.fmgp_precompute(X, dev(W.Y), nbr, 30, gk, fb.PREC_FP64)
+    Cr, _ = oracle.precompute(W.X, W.Y, nb, 30, ok)
+    assert rel_rms(C.cpu().numpy(), Cr) < FP64_TOL
+    yh, near = fb.fmgp_predict(X, nbr, C, 30, gk, dev(W.Z), fb.PREC_FP64)
+    yr, nr = oracle.predict(W.X, nb, Cr, ok, W.Z)
+    np.testing.assert_array_equal(near.cpu().numpy(), nr)
+    assert rel_rms(yh.cpu().numpy(), yr) < FP64_TOL
+
+
+@pytest.mark.parametrize("k", [1, 2, 33, 64, 128])
+def test_fp64_precompute_k_range(cuda, k):
+    W = wl.spatial(n=3_000, m=200, nu=1.5)
+    ok, gk = kern_pair(W.kernel)
+    kq = max(k - 1, 1)
+    nbr, _ = fb.fmgp_build_knn(dev(W.X), kq)
+    nb = nbr.cpu().numpy()
+    C, st = fb.fmgp_precompute(dev(W.X), dev(W.Y), nbr, k, gk, fb.PREC_FP64)
+    Cr, _ = oracle.precompute(W.X, W.Y, nb, k, ok)
+    assert rel_rms(C.cpu().numpy(), Cr) < FP64_TOL
+    yh, _ = fb.fmgp_predict(dev(W.X), nbr, C, k, gk, dev(W.Z), fb.PREC_FP64)
+    yr, _ = oracle.predict(W.X, nb, Cr, ok, W.Z)
+    assert rel_rms(yh.cpu().numpy(), yr) < FP64_TOL
+
+
+def test_k_equals_n_small(cuda):
+    rng = np.random.default_rng(7)
+    X = rng.random((40, 2))
+    Y = rng.normal(size=(40, 2))
+    Z = rng.random((13, 2))
+    ok, gk = oracle.kernel("matern", 2.5, 0.3, 1.0, 1e-3), fb.make_kernel("matern", 2.5, 0.3, 1.0, 1e-3)
+    nbr, _ = fb.fmgp_build_knn(dev(X), 39)
+    C, _ = fb.fmgp_precompute(dev(X), dev(Y), nbr, 40, gk, fb.PREC_FP64)
+    yh, _ = fb.fmgp_predict(dev(X), nbr, C, 40, gk, dev(Z), fb.PREC_FP64)
+    nb, _ = oracle.self_knn(X, 39)
+    Cr, _ = oracle.precompute(X, Y, nb, 40, ok)
+    yr, _ = oracle.predict(X, nb, Cr, ok, Z)
+    assert rel_rms(yh.cpu().numpy(), yr) < FP64_TOL
+
+
+def test_predict_m_zero_is_noop(cuda):
+    W = wl.tiny(n=200, m=1)
+    _, gk = kern_pair(W.kernel)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, 9)
+    C, _ = fb.fmgp_precompute(X, dev(W.Y), nbr, 10, gk)
+    yh, near = fb.fmgp_predict(X, nbr, C, 10, gk, torch.zeros((0, 2), dtype=torch.float64,
+                                                              device="cuda"))
+    assert yh.shape == (0, 1)
+
+
+def test_not_spd_status_and_bad_index(cuda):
+    X = np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 1.0], [2.0, 0.5], [3.0, 3.0]])
+    Y = np.ones((5, 1))
+    gk = fb.make_kernel("matern", 1.5, 1.0, 1.0, 0.0)
+    nbr, _ = fb.fmgp_build_knn(dev(X), 2)
+    C, st = fb.fmgp_precompute(dev(X), dev(Y), nbr, 3, gk)
+    s = st.cpu().numpy()
+    assert s[0] == fb.BLOCK_NOT_SPD and s[1] == fb.BLOCK_NOT_SPD
+    assert np.all(C.cpu().numpy()[0] == 0)
+    with pytest.raises(fb.FmgpError) as e:
+        fb.fmgp_precompute(dev(X), dev(Y), nbr, 3, gk, with_status=False)
+    assert e.value.code == fb.FMGP_ENOTSPD
+    bad = nbr.clone()
+    bad[3, 0] = 99
+    _, st2 = fb.fmgp_precompute(dev(X), dev(Y), bad, 3, fb.make_kernel("matern", 1.5, 1.0, 1.0, 1e-3))
+    assert st2.cpu().numpy()[3] == fb.BLOCK_BAD_INDEX
+
+
+# --------------------------------------------------------------- LOOCV --
+@pytest.mark.parametrize("precision", [fb.PREC_FP64])
+def test_loocv_tiny(cuda, precision):
+    W = wl.tiny()
+    ok, gk = kern_pair(W.kernel)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, 30)
+    Q, res = fb.fmgp_loocv_objective(X, dev(W.Y), nbr, 30, dev(W.batch), gk, precision)
+    nb, _ = oracle.self_knn(W.X, 30)
+    Qr, resr = oracle.loocv(W.X, W.Y, nb, 30, W.batch, ok)
+    tol = FP64_TOL if precision == fb.PREC_FP64 else MIXED_TOL
+    assert abs(Q - Qr) / abs(Qr) < tol
+    assert rel_rms(res.cpu().numpy(), resr) < tol
