@@ -168,6 +168,34 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
                          fmgp_precision precision, double* Q_out, double* resid_out,
                          void* stream);
 
+/*
+ * fmgp_loocv_objective_noalloc -- fmgp_loocv_objective without any device
+ * allocation.  The paper has no counterpart: this is a deployment variant.
+ * It is meant for callers that cannot allocate device memory while running,
+ * such as an application that gives the library a fixed memory budget at
+ * start-up, or a plugin whose host framework owns the device allocator and
+ * does not let it call cudaMalloc.  Arguments, results and error codes are
+ * those of fmgp_loocv_objective, with these differences:
+ *  - Scratch (per-point residuals, the objective, a failure counter) lives in
+ *    one file-scope device array of about 512 KB that every device loading
+ *    the library keeps until the process exits.  Nothing is allocated or
+ *    freed, by this library or by any library it calls.
+ *  - b may be at most 65536; a larger batch returns FMGP_EINVAL.
+ *  - Only FMGP_PREC_FP64 is accepted (FMGP_EUNSUPPORTED otherwise).
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the previous call's contents
+ *    (the call clears its failure counter itself).  Calls that overlap on the
+ *    GPU, from several streams or threads, race on it: serialise them.
+ * When resid_out is non-NULL the residuals are written there instead of the
+ * internal array.  Synchronises `stream` to return Q.
+ */
+int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                                 int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld,
+                                 int32_t k, const int64_t* batch, int64_t b,
+                                 const fmgp_kernel* kernel, fmgp_precision precision,
+                                 double* Q_out, double* resid_out, void* stream);
+
 /* Thread-local description of the most recent error on this thread ("" if none). */
 const char* fmgp_last_error(void);
 
