@@ -123,9 +123,9 @@ static bool prec_ok(fmgp_precision p) {
     }                                 \
   } while (0)
 
-static int pick_warps(const BlockLayout& l, int requested) {
+static int pick_warps(size_t bytes_per_warp, int requested) {
   const size_t budget = 200 * 1024;
-  int w = (int)(budget / l.bytes_per_warp);
+  int w = (int)(budget / bytes_per_warp);
   if (w > 8) w = 8;
   if (requested > 0 && requested < w) w = requested;
   return w;
@@ -134,6 +134,24 @@ static int pick_warps(const BlockLayout& l, int requested) {
 TuneParams& tune_params() {
   static TuneParams tp;
   return tp;
+}
+
+// Precompute / LOOCV blocks in the requested precision.
+static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo,
+                      const fmgp_kernel& kern, fmgp_precision precision, Workspace& ws,
+                      cudaStream_t s) {
+  const int xb = dtype == FMGP_F64 ? 8 : 4;
+  a.layout = block_layout(a.k, a.d, a.r, xb, false);
+  const size_t bytes = precision == FMGP_PREC_FP64 ? a.layout.bytes_per_warp
+                                                   : mixed_bytes_per_warp(a.k, a.d, a.r);
+  if (bytes > 200 * 1024 || a.layout.bytes_per_warp > 200 * 1024) {
+    set_error("neighbourhood k=%d d=%d r=%d needs %zu bytes of shared memory per warp", a.k, a.d,
+              a.r, std::max(bytes, a.layout.bytes_per_warp));
+    return FMGP_EUNSUPPORTED;
+  }
+  const int warps = pick_warps(bytes, tune_params().block_warps);
+  if (precision == FMGP_PREC_FP64) return launch_block_f64(a, X, dtype, loo, warps, s);
+  return run_block_mixed(a, X, dtype, loo, warps, kern, ws, s);
 }
 
 // Deterministic single-CTA sum of the LOOCV residuals: thread t adds
@@ -217,21 +235,7 @@ int fmgp_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
   a.ld = nbr_ld;
   a.k = k;
   a.kp = make_kparams(*kernel);
-  const int xb = dtype == FMGP_F64 ? 8 : 4;
-  if (precision == FMGP_PREC_FP64) {
-    a.layout = block_layout(k, d, r, xb, false);
-  } else {
-    a.layout = block_layout(k, d, r, xb, true);
-    a.layout.bytes_per_warp += block_mixed_extra_bytes(k, d, r);
-  }
-  if (a.layout.bytes_per_warp > 220 * 1024) {
-    set_error("neighbourhood k=%d d=%d r=%d needs %zu bytes of shared memory per warp", k, d, r,
-              a.layout.bytes_per_warp);
-    return FMGP_EUNSUPPORTED;
-  }
-  const int warps = pick_warps(a.layout, tune_params().block_warps);
-  rc = precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, false, warps, s)
-                                   : launch_block_mixed(a, X, dtype, false, warps, s);
+  rc = run_blocks(a, X, dtype, false, *kernel, precision, ws, s);
   if (rc) return rc;
   if (!status_out) {
     int h = 0;
@@ -269,8 +273,8 @@ int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const in
   }
   int rc = nearest_train(X, dtype, n, d, Z, m, near, tune_params(), ws, s);
   if (rc) return rc;
-  return gather_dot(X, dtype, n, d, nbr, nbr_ld, C, k, r, make_kparams(*kernel), precision, Z, m,
-                    near, Yhat_out, s);
+  return gather_dot(X, dtype, n, d, nbr, nbr_ld, C, k, r, make_kparams(*kernel), *kernel,
+                    precision, Z, m, near, Yhat_out, ws, s);
 }
 
 int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
@@ -307,21 +311,7 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
   a.ld = nbr_ld;
   a.k = k;
   a.kp = make_kparams(*kernel);
-  const int xb = dtype == FMGP_F64 ? 8 : 4;
-  if (precision == FMGP_PREC_FP64) {
-    a.layout = block_layout(k, d, r, xb, false);
-  } else {
-    a.layout = block_layout(k, d, r, xb, true);
-    a.layout.bytes_per_warp += block_mixed_extra_bytes(k, d, r);
-  }
-  if (a.layout.bytes_per_warp > 220 * 1024) {
-    set_error("neighbourhood k=%d d=%d r=%d needs %zu bytes of shared memory per warp", k, d, r,
-              a.layout.bytes_per_warp);
-    return FMGP_EUNSUPPORTED;
-  }
-  const int warps = pick_warps(a.layout, tune_params().block_warps);
-  rc = precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, true, warps, s)
-                                   : launch_block_mixed(a, X, dtype, true, warps, s);
+  rc = run_blocks(a, X, dtype, true, *kernel, precision, ws, s);
   if (rc) return rc;
   FMGP_LAUNCH(loocv_reduce<<<1, 1024, 0, s>>>(resid, b, qd));
   FMGP_CUDA_TRY(cudaGetLastError());

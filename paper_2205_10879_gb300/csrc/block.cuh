@@ -26,12 +26,21 @@ struct BlockArgs {
   int d, r, ld, k;
   KParams kp;
   BlockLayout layout;
+  // FP64 fallback of the mixed path: process only the items list[0..*list_count)
+  // (item = training point, or batch position for LOOCV) and store C as
+  // double-float pairs when c_df is set.
+  const int* list = nullptr;
+  const int* list_count = nullptr;
+  bool c_df = false;
 };
 
+// blocks = 0 picks a grid covering `count`; the list mode needs an explicit grid.
 int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo, int warps,
-                     cudaStream_t stream);
-int launch_block_mixed(const BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo, int warps,
-                       cudaStream_t stream);
-size_t block_mixed_extra_bytes(int k, int d, int r);
+                     cudaStream_t stream, int blocks = 0);
+
+// Mixed-precision form (FP32 factor + double-float refinement + FP64 fallback).
+size_t mixed_bytes_per_warp(int k, int d, int r);
+int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int warps,
+                    const fmgp_kernel& kern, Workspace& ws, cudaStream_t s);
 
 }  // namespace fmgp

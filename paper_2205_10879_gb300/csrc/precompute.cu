@@ -35,8 +35,10 @@ __global__ void __launch_bounds__(256) block_f64_kernel(BlockArgs args, const T*
   const int k = args.k, d = args.d, r = args.r, ldl = lay.ldl;
   const KParams kp = args.kp;
 
-  for (int64_t item = (int64_t)blockIdx.x * wpb + wid; item < args.count;
-       item += (int64_t)gridDim.x * wpb) {
+  const int64_t total = args.list ? (int64_t)*args.list_count : args.count;
+  for (int64_t it = (int64_t)blockIdx.x * wpb + wid; it < total;
+       it += (int64_t)gridDim.x * wpb) {
+    const int64_t item = args.list ? (int64_t)args.list[it] : it;
     int64_t i = LOO ? args.batch[item] : item;
     // S: precompute S_i = [i, N_i]; LOOCV N_i (self excluded)
     bool bad = false;
@@ -146,10 +148,21 @@ __global__ void __launch_bounds__(256) block_f64_kernel(BlockArgs args, const T*
       }
     }
     if (!LOO) {
-      double* Ci = (double*)args.C + i * (int64_t)k * r;
-      for (int e = lane; e < k * r; e += 32) Ci[e] = fail ? 0.0 : W[e];
+      if (args.c_df) {
+        float2* Ci = (float2*)args.C + i * (int64_t)k * r;
+        for (int e = lane; e < k * r; e += 32) {
+          const double v = fail ? 0.0 : W[e];
+          const float hi = (float)v;
+          Ci[e] = make_float2(hi, (float)(v - (double)hi));
+        }
+      } else {
+        double* Ci = (double*)args.C + i * (int64_t)k * r;
+        for (int e = lane; e < k * r; e += 32) Ci[e] = fail ? 0.0 : W[e];
+      }
       if (args.status && lane == 0)
-        args.status[i] = bad ? FMGP_BLOCK_BAD_INDEX : (fail ? FMGP_BLOCK_NOT_SPD : FMGP_BLOCK_OK);
+        args.status[i] = bad ? FMGP_BLOCK_BAD_INDEX
+                             : (fail ? FMGP_BLOCK_NOT_SPD
+                                     : (args.list ? FMGP_BLOCK_FP64_RETRY : FMGP_BLOCK_OK));
       if (fail && lane == 0) atomicAdd(args.fail_count, 1);
     } else {
       // leave-one-out residual of x_i against its neighbours
@@ -210,11 +223,11 @@ BlockLayout block_layout(int k, int d, int r, int xbytes, bool f32_factor) {
 }
 
 int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo, int warps,
-                     cudaStream_t stream) {
+                     cudaStream_t stream, int blocks) {
   const size_t smem = a.layout.bytes_per_warp * warps;
   const int sms = num_sms();
   const int64_t need = (a.count + warps - 1) / warps;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 16));
+  if (blocks <= 0) blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 16));
   if (dtype == FMGP_F64) {
     auto kern = loo ? block_f64_kernel<double, true> : block_f64_kernel<double, false>;
     FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -138,8 +138,9 @@ int nearest_train(const void* X, fmgp_dtype dtype, int64_t n, int d, const void*
 }
 
 int gather_dot(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
-               const void* C, int k, int r, const KParams& kp, fmgp_precision prec, const void* Z,
-               int64_t m, const int32_t* nearest, double* Yhat, cudaStream_t stream) {
+               const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
+               fmgp_precision prec, const void* Z, int64_t m, const int32_t* nearest,
+               double* Yhat, Workspace& ws, cudaStream_t stream) {
   if (m == 0) return FMGP_OK;
   const int blocks = ceil_div(m * 32, 256);
   if (prec == FMGP_PREC_FP64) {
@@ -152,7 +153,8 @@ int gather_dot(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t*
           (const float*)X, n, d, nbr, ld, (const double*)C, k, r, kp, (const float*)Z, m,
           nearest, Yhat));
   } else {
-    return gather_dot_mixed(X, dtype, n, d, nbr, ld, C, k, r, kp, Z, m, nearest, Yhat, stream);
+    return gather_dot_mixed(X, dtype, n, d, nbr, ld, C, k, r, kp, kern, Z, m, nearest, Yhat, ws,
+                            stream);
   }
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;

@@ -10,12 +10,14 @@ int nearest_train(const void* X, fmgp_dtype dtype, int64_t n, int d, const void*
 
 // A5: Yhat[t][c] = sum_a sigma^2 phi(||z_t - x_{S_j*[a]}||) C[j*][a][c].
 int gather_dot(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
-               const void* C, int k, int r, const KParams& kp, fmgp_precision prec, const void* Z,
-               int64_t m, const int32_t* nearest, double* Yhat, cudaStream_t stream);
+               const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
+               fmgp_precision prec, const void* Z, int64_t m, const int32_t* nearest,
+               double* Yhat, Workspace& ws, cudaStream_t stream);
 
 // A5 with double-float coefficients and cross-covariances (mixed precision).
 int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
-                     const void* C, int k, int r, const KParams& kp, const void* Z, int64_t m,
-                     const int32_t* nearest, double* Yhat, cudaStream_t stream);
+                     const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
+                     const void* Z, int64_t m, const int32_t* nearest, double* Yhat,
+                     Workspace& ws, cudaStream_t stream);
 
 }  // namespace fmgp

@@ -204,3 +204,88 @@ def test_loocv_tiny(cuda, precision):
     tol = FP64_TOL if precision == fb.PREC_FP64 else MIXED_TOL
     assert abs(Q - Qr) / abs(Qr) < tol
     assert rel_rms(res.cpu().numpy(), resr) < tol
+
+
+# ------------------------------------------------------------ mixed path --
+def _mixed_check(W, k, kq, n_rows=None, tol=MIXED_TOL):
+    ok, gk = kern_pair(W.kernel)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, kq)
+    nb = nbr.cpu().numpy()
+    C, st = fb.fmgp_precompute(X, dev(W.Y), nbr, k, gk, fb.PREC_MIXED)
+    yh, near = fb.fmgp_predict(X, nbr, C, k, gk, dev(W.Z), fb.PREC_MIXED)
+    torch.cuda.synchronize()
+    s = st.cpu().numpy()
+    assert np.all((s == fb.BLOCK_OK) | (s == fb.BLOCK_FP64_RETRY))
+    near = near.cpu().numpy()
+    rows = np.unique(near)
+    Cr, _ = oracle.precompute(W.X, W.Y, nb, k, ok, rows=rows)
+    Cfull = np.zeros((W.n, k, W.r))
+    Cfull[rows] = Cr
+    yr = oracle.predict_given(W.X, nb, Cfull, ok, W.Z, near)
+    err = rel_rms(yh.cpu().numpy(), yr)
+    assert err < tol, err
+    cerr = rel_rms(coeffs_to_f64(C, fb.PREC_MIXED)[rows], Cr)
+    return err, cerr, s
+
+
+def test_mixed_pipeline_tiny(cuda):
+    W = wl.tiny()
+    err, cerr, s = _mixed_check(W, 30, 29)
+    assert cerr < 1e-6
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5])
+def test_mixed_spatial(cuda, nu):
+    W = wl.spatial(n=60_000, m=4_000, nu=nu)
+    err, cerr, s = _mixed_check(W, 50, 50)
+    assert (s == fb.BLOCK_FP64_RETRY).mean() < 0.01
+
+
+def test_mixed_ill_conditioned_large_like(cuda):
+    """Matern 5/2 with tau^2 = 1e-5 on dense 3-D points: refinement takes
+    several steps and some blocks may go to the FP64 fallback."""
+    W = wl.large(n=1_000_000, m=3_000)
+    _mixed_check(W, 64, 63)
+
+
+def test_mixed_highdim_multiresponse(cuda):
+    W = wl.highdim(n=2_000, m=300)
+    _mixed_check(W, 30, 29)
+
+
+def test_mixed_fp64_fallback_on_fp32_failure(cuda):
+    """Near-duplicate clusters with a tiny nugget: the FP32 factorisation
+    breaks down, the block is re-solved in FP64 and flagged FP64_RETRY."""
+    rng = np.random.default_rng(11)
+    centres = rng.random((300, 2))
+    X = (np.repeat(centres, 6, axis=0) + rng.normal(0, 1e-6, (1800, 2)))
+    Y = np.sin(7 * X[:, :1]) + np.cos(5 * X[:, 1:])
+    Z = rng.random((200, 2))
+    spec = wl.KernelSpec("matern", 2.5, 0.2, 1.0, 1e-9)
+    ok, gk = kern_pair(spec)
+    Xd = dev(X)
+    nbr, _ = fb.fmgp_build_knn(Xd, 11)
+    C, st = fb.fmgp_precompute(Xd, dev(Y), nbr, 12, gk, fb.PREC_MIXED)
+    s = st.cpu().numpy()
+    assert (s == fb.BLOCK_FP64_RETRY).sum() > 0
+    nb = nbr.cpu().numpy()
+    Cr, str_ = oracle.precompute(X, Y, nb, 12, ok)
+    Cg = coeffs_to_f64(C, fb.PREC_MIXED)
+    retry = (s == fb.BLOCK_FP64_RETRY) & (str_ == 0)
+    assert retry.sum() > 0
+    # cond(K) ~ 1e10 here: FP64 against FP64 agrees to ~cond * eps
+    assert rel_rms(Cg[retry], Cr[retry]) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [fb.PREC_MIXED])
+def test_loocv_mixed(cuda, precision):
+    test_loocv_tiny(cuda, precision)
+    W = wl.spatial(n=30_000, m=10, nu=1.5, b=3000)
+    ok, gk = kern_pair(W.kernel)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, 50)
+    Q, res = fb.fmgp_loocv_objective(X, dev(W.Y), nbr, 50, dev(W.batch), gk, precision)
+    Qr, resr = oracle.loocv(W.X, W.Y, nbr.cpu().numpy(), 50, W.batch, ok)
+    assert abs(Q - Qr) / abs(Qr) < MIXED_TOL
+    assert rel_rms(res.cpu().numpy(), resr) < MIXED_TOL
