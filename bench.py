@@ -216,6 +216,7 @@ def run_ours(a):
         ms = float(t.item())
     phase_ms = ph.mean(axis=0)
     yh_main = yh.cpu().numpy().copy()
+    st_main = st.cpu().numpy().copy()
     rmse = float(np.sqrt(np.mean((yh_main - W.Ztrue) ** 2)))
     out = {}
     # the plain FP64 path on the same workload, for the "vs FP64 plain" comparison
@@ -297,6 +298,7 @@ def run_ours(a):
         "knn_queries_per_s": n / (phase_ms[0] * 1e-3),
         "loocv_pts_per_s": b / (phase_ms[3] * 1e-3),
         "rmse": rmse, "fp64_path": fp64, "roofline": roof, "e2e": e2e,
+        "block_status": {str(v): int(c) for v, c in zip(*np.unique(st_main, return_counts=True))},
         "gpu_launches": launches, "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:

@@ -123,12 +123,21 @@ static bool prec_ok(fmgp_precision p) {
     }                                 \
   } while (0)
 
+// Warps per CTA for a block kernel: the choice that keeps the most warps
+// resident per SM given bytes_per_warp of shared memory (227 KB per SM, 1 KB
+// reserved per CTA); ties go to the larger CTA.
 static int pick_warps(size_t bytes_per_warp, int requested) {
-  const size_t budget = 200 * 1024;
-  int w = (int)(budget / bytes_per_warp);
-  if (w > 8) w = 8;
-  if (requested > 0 && requested < w) w = requested;
-  return w;
+  if (requested > 0) return requested;
+  const size_t sm_bytes = 227 * 1024;
+  int best = 1, best_total = 0;
+  for (int w : {8, 6, 4, 2, 1}) {
+    const size_t cta = (size_t)w * bytes_per_warp + 1024;
+    if ((size_t)w * bytes_per_warp > 200 * 1024) continue;
+    const int ctas = (int)(sm_bytes / cta);
+    const int total = w * std::min(ctas, 32 / w);
+    if (total > best_total) { best_total = total; best = w; }
+  }
+  return best;
 }
 
 TuneParams& tune_params() {

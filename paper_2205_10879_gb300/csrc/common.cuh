@@ -4,7 +4,7 @@
 #include <stdint.h>
 #include <limits.h>
 #include <string>
-#include "../../include/fmgp.h"
+#include "fmgp.h"
 
 namespace fmgp {
 

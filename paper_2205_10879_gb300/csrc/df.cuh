@@ -88,14 +88,16 @@ __device__ __forceinline__ dfl df_sqr(dfl x) {
 // acc + x*y (x, y, acc DF), the product rounded to DF first.
 __device__ __forceinline__ dfl df_fma(dfl x, dfl y, dfl acc) { return df_add(acc, df_mul(x, y)); }
 
-// Square root by one Newton (Karp-Markstein) correction of the FP32 root:
-// s = sqrt(hi), result s + (x - s^2) / (2 s) with x - s^2 formed exactly.
+// Square root by one Newton (Karp-Markstein) correction of an FP32 root:
+// s ~ sqrt(hi), result s + (x - s^2) / (2 s) with x - s^2 formed exactly.
 __device__ __forceinline__ dfl df_sqrt(dfl x) {
   if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
-  const float s = __fsqrt_rn(x.hi);
+  // s needs only FP32-level accuracy: the correction below restores ~2^-46
+  const float rs = rsqrtf(x.hi);
+  const float s = __fmul_rn(x.hi, rs);
   const dfl p = df_two_prod(s, s);
   const float e = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);
-  const float c = __fmul_rn(e, __fdiv_rn(0.5f, s));
+  const float c = e * (0.5f * rs);
   return df_quick(s, c);
 }
 
@@ -109,27 +111,34 @@ struct DfConsts {
 };
 
 // exp(-a) for a >= 0 (DF), relative error about 1e-13:
-//   a = n ln2 + r, |r| <= ln2/2 (Cody-Waite reduction in DF);
-//   r = j/64 + s, |s| <= 1/128;  exp(-a) = 2^-n exp(-j/64) exp(-s);
-//   exp(-s) = (1 - s + s^2/2) in DF + s^3 (-1/6 + s/24 - s^2/120 + s^3/720)
-//   in FP32 (that tail is below 1e-7, so FP32 keeps it to ~1e-14).
+//   a = n ln2 + r, |r| <= ln2/2 (Cody-Waite reduction: a.hi - n ln2_1 is
+//   exact by Sterbenz's lemma, the remaining small terms are summed in DF);
+//   r = j/64 + s, |s| <= 1/128 (r.hi - j/64 is exact as well);
+//   exp(-a) = 2^-n exp(-j/64) exp(-s),
+//   exp(-s) = 1 - s + s^2/2 in DF + s^3 (-1/6 + s/24 - s^2/120 + s^3/720) in
+//   FP32 (that tail is below 1e-7, so FP32 keeps it to ~1e-14).
 __device__ __forceinline__ dfl df_exp_neg(dfl a, const DfConsts& K) {
   if (!(a.hi < 87.0f)) return {0.0f, 0.0f};
   const float nf = rintf(__fmul_rn(a.hi, 1.4426950408889634f));
-  dfl r = df_add_f(a, -__fmul_rn(nf, K.ln2_1));  // nf * ln2_1 is exact
-  r = df_add(r, df_neg(df_two_prod(nf, K.ln2_2)));
-  r = df_add_f(r, -__fmul_rn(nf, K.ln2_3));
+  const float r1 = __fsub_rn(a.hi, __fmul_rn(nf, K.ln2_1));  // exact
+  const dfl p2 = df_two_prod(nf, K.ln2_2);                    // n ln2_2 exactly
+  const dfl c = df_two_sum(a.lo, -p2.hi);                     // a.lo - n ln2_2 (hi part)
+  const float cl = __fsub_rn(__fsub_rn(c.lo, p2.lo), __fmul_rn(nf, K.ln2_3));
+  dfl r = df_two_sum(r1, c.hi);
+  r = df_quick(r.hi, __fadd_rn(r.lo, cl));
   int j = (int)rintf(__fmul_rn(r.hi, 64.0f));
   j = max(-24, min(24, j));
-  const dfl s = df_add_f(r, -(float)j * 0.015625f);
+  const dfl s = df_quick(__fsub_rn(r.hi, (float)j * 0.015625f), r.lo);  // exact difference
   const dfl s2 = df_sqr(s);
-  dfl h = df_add_f(df_neg(s), 1.0f);
-  h = df_add(h, dfl{0.5f * s2.hi, 0.5f * s2.lo});
+  const dfl h1 = df_quick(1.0f, -s.hi);                   // 1 - s.hi, exact as a pair
+  const dfl h2 = df_two_sum(h1.hi, __fmul_rn(0.5f, s2.hi));
   const float t = s.hi;
   const float tail =
       t * t * t *
       (-0.16666667f + t * (0.041666668f + t * (-0.008333334f + t * 0.0013888889f)));
-  const dfl e = df_add_f(h, tail);
+  const float lo = __fadd_rn(__fadd_rn(__fsub_rn(__fadd_rn(h2.lo, h1.lo), s.lo),
+                                       __fmul_rn(0.5f, s2.lo)), tail);
+  const dfl e = df_quick(h2.hi, lo);
   dfl v = df_mul(dfl{K.e_hi[j + 24], K.e_lo[j + 24]}, e);
   const int ni = (int)nf;
   return {ldexpf(v.hi, -ni), ldexpf(v.lo, -ni)};

@@ -26,12 +26,16 @@ namespace {
 constexpr int kMaxSlots = kMaxK / 32;
 constexpr int kMaxRefine = 6;
 
+// The mixed kernels work with correlations phi (sigma^2 factored out): the
+// block solved is M = K / sigma^2 (diagonal 1 + tau^2), so C = M^{-1} Y / sigma^2,
+// and predictions multiply the dot product by sigma^2 once.
 struct KParamsDF {
   int kind, nu2;
-  dfl scale;   // sqrt(2 nu)/rho (Matern) or 1/(2 rho^2) (RBF)
-  dfl var;     // sigma^2
-  dfl diag;    // sigma^2 (1 + tau^2)
-  dfl third;   // 1/3
+  dfl scale;    // sqrt(2 nu)/rho (Matern) or 1/(2 rho^2) (RBF)
+  dfl var;      // sigma^2
+  dfl inv_var;  // 1 / sigma^2
+  dfl diag;     // 1 + tau^2
+  dfl third;    // 1/3
 };
 
 dfl split(double v) {
@@ -47,7 +51,8 @@ KParamsDF make_kparams_df(const KParams& p, const fmgp_kernel& k) {
   if (p.kind == FMGP_KERNEL_RBF) q.scale = split(0.5 / (k.length_scale * k.length_scale));
   else q.scale = split(sqrt((double)p.nu2) / k.length_scale);
   q.var = split(k.variance);
-  q.diag = split(k.variance * (1.0 + k.nugget));
+  q.inv_var = split(1.0 / k.variance);
+  q.diag = split(1.0 + k.nugget);
   q.third = split(1.0 / 3.0);
   return q;
 }
@@ -70,8 +75,8 @@ const DfConsts& df_consts() {
   return c;
 }
 
-// Correlation sigma^2 phi at DF squared distance D.
-__device__ __forceinline__ dfl kernel_df(const KParamsDF& p, dfl D, const DfConsts& K) {
+// Correlation phi at DF squared distance D (Eq. 3 closed forms / RBF).
+__device__ __forceinline__ dfl corr_df(const KParamsDF& p, dfl D, const DfConsts& K) {
   dfl ph;
   if (p.kind == FMGP_KERNEL_RBF) {
     ph = df_exp_neg(df_mul(D, p.scale), K);
@@ -82,7 +87,7 @@ __device__ __forceinline__ dfl kernel_df(const KParamsDF& p, dfl D, const DfCons
     else if (p.nu2 == 3) ph = df_mul(df_add_f(a, 1.0f), e);
     else ph = df_mul(df_add(df_add_f(a, 1.0f), df_mul(df_sqr(a), p.third)), e);
   }
-  return df_mul(p.var, ph);
+  return ph;
 }
 
 __device__ __forceinline__ dfl sqdist_df(const float2* a, const float2* b, int d) {
@@ -105,17 +110,26 @@ struct MixedArgs {
 };
 
 struct MixedLayout {
-  int ldl;
-  size_t off_L, off_K, off_X, off_Y, off_V, off_R, off_inv, off_S, off_flag, bytes;
+  int ldl;  // row stride of the factor: multiple of 4 and = 4 (mod 8), so rows are
+            // 16-byte aligned and float4 row reads by 8 consecutive lanes hit
+            // distinct bank groups
+  size_t off_L, off_LO, off_X, off_Y, off_V, off_R, off_inv, off_S, off_flag, bytes;
 };
 
+// Per-warp shared memory of the mixed block kernel.  The factor matrix M
+// (k x ldl floats) holds, after assembly, hi(K_ab) in BOTH triangles; the
+// Cholesky overwrites only the lower triangle and the diagonal, so hi(K_ab)
+// for the residual stays available in the upper triangle, while lo(K_ab) is
+// kept in a packed strict-lower array LO.
 MixedLayout mixed_layout(int k, int d, int r) {
   MixedLayout l;
-  l.ldl = (k % 2 == 0) ? k + 1 : k;
+  int ldl = (k + 3) & ~3;
+  if (ldl % 8 == 0) ldl += 4;
+  l.ldl = ldl;
   auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
   size_t o = 0;
-  l.off_L = o;    o += up((size_t)k * l.ldl * 4);
-  l.off_K = o;    o += up((size_t)k * (k + 1) / 2 * 8);
+  l.off_L = o;    o += up((size_t)k * ldl * 4);
+  l.off_LO = o;   o += up((size_t)k * (k - 1) / 2 * 4 + 4);
   l.off_X = o;    o += up((size_t)k * d * 8);
   l.off_Y = o;    o += up((size_t)k * r * 8);
   l.off_V = o;    o += up((size_t)k * r * 8);
@@ -127,56 +141,154 @@ MixedLayout mixed_layout(int k, int d, int r) {
   return l;
 }
 
-__device__ __forceinline__ void pair_of(int p, int& a, int& b) {
-  int x = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
-  while (x * (x - 1) / 2 > p) --x;
-  while ((x + 1) * x / 2 <= p) ++x;
-  a = x;
-  b = p - x * (x - 1) / 2;
+// Sum_{p<j} a0[p] b[p] and Sum_{p<j} a1[p] b[p] over 16-byte aligned rows
+// (b read once for both), eight independent accumulators.
+__device__ __forceinline__ void row_dot2(const float* a0, const float* a1, const float* b, int j,
+                                         bool use1, float& out0, float& out1) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+  const int j4 = j & ~3;
+  if (use1) {
+    int p = 0;
+    for (; p + 8 <= j4; p += 8) {
+      const float4 y = *reinterpret_cast<const float4*>(b + p);
+      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
+      const float4 z = *reinterpret_cast<const float4*>(a1 + p);
+      const float4 y2 = *reinterpret_cast<const float4*>(b + p + 4);
+      const float4 x2 = *reinterpret_cast<const float4*>(a0 + p + 4);
+      const float4 z2 = *reinterpret_cast<const float4*>(a1 + p + 4);
+      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
+      t0 = fmaf(z.x, y.x, t0); t1 = fmaf(z.y, y.y, t1); t2 = fmaf(z.z, y.z, t2); t3 = fmaf(z.w, y.w, t3);
+      s0 = fmaf(x2.x, y2.x, s0); s1 = fmaf(x2.y, y2.y, s1); s2 = fmaf(x2.z, y2.z, s2); s3 = fmaf(x2.w, y2.w, s3);
+      t0 = fmaf(z2.x, y2.x, t0); t1 = fmaf(z2.y, y2.y, t1); t2 = fmaf(z2.z, y2.z, t2); t3 = fmaf(z2.w, y2.w, t3);
+    }
+    for (; p < j4; p += 4) {
+      const float4 y = *reinterpret_cast<const float4*>(b + p);
+      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
+      const float4 z = *reinterpret_cast<const float4*>(a1 + p);
+      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
+      t0 = fmaf(z.x, y.x, t0); t1 = fmaf(z.y, y.y, t1); t2 = fmaf(z.z, y.z, t2); t3 = fmaf(z.w, y.w, t3);
+    }
+    for (int p = j4; p < j; ++p) {
+      s0 = fmaf(a0[p], b[p], s0);
+      t0 = fmaf(a1[p], b[p], t0);
+    }
+  } else {
+    int p = 0;
+    for (; p + 8 <= j4; p += 8) {
+      const float4 y = *reinterpret_cast<const float4*>(b + p);
+      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
+      const float4 y2 = *reinterpret_cast<const float4*>(b + p + 4);
+      const float4 x2 = *reinterpret_cast<const float4*>(a0 + p + 4);
+      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
+      t0 = fmaf(x2.x, y2.x, t0); t1 = fmaf(x2.y, y2.y, t1); t2 = fmaf(x2.z, y2.z, t2); t3 = fmaf(x2.w, y2.w, t3);
+    }
+    for (; p < j4; p += 4) {
+      const float4 y = *reinterpret_cast<const float4*>(b + p);
+      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
+      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
+    }
+    for (int p = j4; p < j; ++p) s0 = fmaf(a0[p], b[p], s0);
+    s0 += (t0 + t1) + (t2 + t3);
+    t0 = t1 = t2 = t3 = 0.f;
+  }
+  out0 = (s0 + s1) + (s2 + s3);
+  out1 = (t0 + t1) + (t2 + t3);
 }
 
-// FP32 forward and back substitution with L (row stride ldl) on R (k x r).
-__device__ __forceinline__ void solve_f32(const float* L, int ldl, const float* invd, float* R,
+// L y = b then L^T x = y for column c of R (k x r), L the lower triangle of
+// M (stride ldl) with inverse diagonal invd.  Rows are taken 32 at a time,
+// lane = row within the block: contributions of finished blocks are
+// subtracted with dot products, the block itself is solved through shuffles.
+__device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* invd, float* R,
                                           int k, int r, int lane) {
-  for (int p = 0; p < k; ++p) {
-    if (lane == (p & 31))
-      for (int c = 0; c < r; ++c) R[p * r + c] *= invd[p];
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < kMaxSlots; ++s) {
-      const int row = lane + 32 * s;
-      if (row > p && row < k) {
-        const float l = L[row * ldl + p];
-        for (int c = 0; c < r; ++c) R[row * r + c] = fmaf(-l, R[p * r + c], R[row * r + c]);
+  const int nblk = (k + 31) >> 5;
+  for (int c = 0; c < r; ++c) {
+    // forward
+    for (int q = 0; q < nblk; ++q) {
+      const int row = 32 * q + lane;
+      const bool valid = row < k;
+      float v = valid ? R[row * r + c] : 0.0f;
+      const float iv = valid ? invd[row] : 0.0f;
+      if (valid && q > 0) {
+        const float* mr = M + row * ldl;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        if (r == 1) {
+          for (int p = 0; p < 32 * q; p += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(mr + p);
+            const float4 x = *reinterpret_cast<const float4*>(R + p);
+            s0 = fmaf(a.x, x.x, s0); s1 = fmaf(a.y, x.y, s1);
+            s2 = fmaf(a.z, x.z, s2); s3 = fmaf(a.w, x.w, s3);
+          }
+        } else {
+          for (int p = 0; p < 32 * q; ++p) s0 = fmaf(mr[p], R[p * r + c], s0);
+        }
+        v -= (s0 + s1) + (s2 + s3);
       }
-    }
-    __syncwarp();
-  }
-  for (int p = k - 1; p >= 0; --p) {
-    if (lane == (p & 31))
-      for (int c = 0; c < r; ++c) R[p * r + c] *= invd[p];
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < kMaxSlots; ++s) {
-      const int row = lane + 32 * s;
-      if (row < p) {
-        const float l = L[p * ldl + row];
-        for (int c = 0; c < r; ++c) R[row * r + c] = fmaf(-l, R[p * r + c], R[row * r + c]);
+      const float* mb = M + row * ldl + 32 * q;
+      if (32 * q + 32 <= k) {
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) {
+          const float m = (lane > t && valid) ? mb[t] : 0.0f;
+          const float xt = __shfl_sync(kFull, v * iv, t);
+          v = (lane == t) ? xt : fmaf(-m, xt, v);
+        }
+      } else {
+        const int tmax = k - 32 * q;
+        for (int t = 0; t < tmax; ++t) {
+          const float m = (lane > t && valid) ? mb[t] : 0.0f;
+          const float xt = __shfl_sync(kFull, v * iv, t);
+          v = (lane == t) ? xt : fmaf(-m, xt, v);
+        }
       }
+      if (valid) R[row * r + c] = v;
+      __syncwarp();
     }
-    __syncwarp();
+    // backward
+    for (int q = nblk - 1; q >= 0; --q) {
+      const int row = 32 * q + lane;
+      const bool valid = row < k;
+      float v = valid ? R[row * r + c] : 0.0f;
+      const float iv = valid ? invd[row] : 0.0f;
+      if (valid) {
+        float s0 = 0.f, s1 = 0.f;
+        int p = 32 * (q + 1);
+        for (; p + 1 < k; p += 2) {
+          s0 = fmaf(M[p * ldl + row], R[p * r + c], s0);
+          s1 = fmaf(M[(p + 1) * ldl + row], R[(p + 1) * r + c], s1);
+        }
+        if (p < k) s0 = fmaf(M[p * ldl + row], R[p * r + c], s0);
+        v -= s0 + s1;
+      }
+      const int tmax = min(32, k - 32 * q);
+      if (tmax == 32) {
+#pragma unroll 8
+        for (int t = 31; t >= 0; --t) {
+          const float m = (lane < t && valid) ? M[(32 * q + t) * ldl + row] : 0.0f;
+          const float xt = __shfl_sync(kFull, v * iv, t);
+          v = (lane == t) ? xt : fmaf(-m, xt, v);
+        }
+      } else {
+        for (int t = tmax - 1; t >= 0; --t) {
+          const float m = (lane < t && valid) ? M[(32 * q + t) * ldl + row] : 0.0f;
+          const float xt = __shfl_sync(kFull, v * iv, t);
+          v = (lane == t) ? xt : fmaf(-m, xt, v);
+        }
+      }
+      if (valid) R[row * r + c] = v;
+      __syncwarp();
+    }
   }
 }
 
 template <bool LOO>
-__global__ void __launch_bounds__(256) block_mixed_kernel(BlockArgs args, MixedArgs mx,
+__global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
                                                           MixedLayout lay) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int wpb = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* base = smem + (size_t)wid * lay.bytes;
-  float* L = (float*)(base + lay.off_L);
-  dfl* KP = (dfl*)(base + lay.off_K);
+  float* M = (float*)(base + lay.off_L);
+  float* LO = (float*)(base + lay.off_LO);
   float2* XS = (float2*)(base + lay.off_X);
   dfl* YS = (dfl*)(base + lay.off_Y);
   dfl* XV = (dfl*)(base + lay.off_V);
@@ -210,87 +322,107 @@ __global__ void __launch_bounds__(256) block_mixed_kernel(BlockArgs args, MixedA
       YS[e] = dfl{y.x, y.y};
     }
     __syncwarp();
-    // assembly: DF entries (packed lower triangle) and their FP32 roundings
-    const int npairs = k * (k - 1) / 2;
-    for (int p = lane; p < npairs; p += 32) {
-      int a, b;
-      pair_of(p, a, b);
-      const dfl kab = kernel_df(kp, sqdist_df(XS + a * d, XS + b * d, d), mx.K);
-      KP[a * (a + 1) / 2 + b] = kab;
-      L[a * ldl + b] = kab.hi;
+    // assembly: pair p = a(a-1)/2 + b (a > b), walked incrementally per lane
+    {
+      const int npairs = k * (k - 1) / 2;
+      int a = 1, b = lane;
+      while (b >= a) { b -= a; ++a; }
+      // two entries per iteration (p and p + 32) for instruction-level parallelism
+      for (int p = lane; p < npairs; p += 64) {
+        const int a0 = a, b0 = b;
+        b += 32;
+        while (b >= a) { b -= a; ++a; }
+        const int a1 = a, b1 = b;
+        const bool two = p + 32 < npairs;
+        const dfl k0 = corr_df(kp, sqdist_df(XS + a0 * d, XS + b0 * d, d), mx.K);
+        dfl k1 = {0.0f, 0.0f};
+        if (two) k1 = corr_df(kp, sqdist_df(XS + a1 * d, XS + b1 * d, d), mx.K);
+        M[a0 * ldl + b0] = k0.hi;
+        M[b0 * ldl + a0] = k0.hi;
+        LO[p] = k0.lo;
+        if (two) {
+          M[a1 * ldl + b1] = k1.hi;
+          M[b1 * ldl + a1] = k1.hi;
+          LO[p + 32] = k1.lo;
+        }
+        b += 32;
+        while (b >= a) { b -= a; ++a; }
+      }
     }
-    for (int a = lane; a < k; a += 32) {
-      KP[a * (a + 1) / 2 + a] = kp.diag;
-      L[a * ldl + a] = kp.diag.hi;
-    }
-    if (lane == 0) *flag = 0;
+    for (int a = lane; a < k; a += 32) M[a * ldl + a] = kp.diag.hi;
     __syncwarp();
-    // FP32 Cholesky (Crout order)
+    // FP32 Cholesky (Crout order), lower triangle of M.  Rows r0 = lane and
+    // r1 = lane + 32 share one pass over row j; rows 64.. (k > 64) follow.
+    // The pivot's reciprocal square root is broadcast by shuffle.
+    bool fail = false;
     for (int j = 0; j < k; ++j) {
-      float dots[kMaxSlots];
-#pragma unroll
-      for (int s = 0; s < kMaxSlots; ++s) {
-        const int row = lane + 32 * s;
-        dots[s] = 0.0f;
-        if (row >= j && row < k) {
-          float acc = 0.0f;
-          const float* lr = L + row * ldl;
-          const float* lj = L + j * ldl;
-          for (int q = 0; q < j; ++q) acc = fmaf(lr[q], lj[q], acc);
-          dots[s] = acc;
-        }
+      const float* mj = M + j * ldl;
+      const int r0 = lane, r1 = lane + 32, r2 = lane + 64, r3 = lane + 96;
+      const bool a0 = r0 >= j && r0 < k, a1 = r1 >= j && r1 < k;
+      float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
+      if (a0 || a1) row_dot2(M + (a0 ? r0 : r1) * ldl, M + r1 * ldl, mj, j, a0 && a1, d0, d1);
+      if (!a0) { d1 = d0; d0 = 0.0f; }
+      if (k > 64) {
+        const bool a2 = r2 >= j && r2 < k, a3 = r3 >= j && r3 < k;
+        if (a2 || a3) row_dot2(M + (a2 ? r2 : r3) * ldl, M + r3 * ldl, mj, j, a2 && a3, d2, d3);
+        if (!a2) { d3 = d2; d2 = 0.0f; }
       }
+      float inv = 0.0f;
       if (lane == (j & 31)) {
-        float dj = dots[0];
-#pragma unroll
-        for (int s = 1; s < kMaxSlots; ++s)
-          if (s == (j >> 5)) dj = dots[s];
-        const float v = L[j * ldl + j] - dj;
-        if (!(v > 0.0f)) {
-          *flag = 1;
-        } else {
-          const float ljj = sqrtf(v);
-          L[j * ldl + j] = ljj;
-          invd[j] = 1.0f / ljj;
+        const int sj = j >> 5;
+        const float dj = sj == 0 ? d0 : (sj == 1 ? d1 : (sj == 2 ? d2 : d3));
+        const float v = M[j * ldl + j] - dj;
+        if (v > 0.0f) {
+          inv = rsqrtf(v);
+          M[j * ldl + j] = v * inv;
+          invd[j] = inv;
         }
       }
-      __syncwarp();
-      if (*flag) break;
-      const float inv = invd[j];
-#pragma unroll
-      for (int s = 0; s < kMaxSlots; ++s) {
-        const int row = lane + 32 * s;
-        if (row > j && row < k) L[row * ldl + j] = (L[row * ldl + j] - dots[s]) * inv;
-      }
+      inv = __shfl_sync(kFull, inv, j & 31);
+      if (!(inv > 0.0f)) { fail = true; break; }
+      if (r0 > j && r0 < k) M[r0 * ldl + j] = (M[r0 * ldl + j] - d0) * inv;
+      if (r1 > j && r1 < k) M[r1 * ldl + j] = (M[r1 * ldl + j] - d1) * inv;
+      if (r2 > j && r2 < k) M[r2 * ldl + j] = (M[r2 * ldl + j] - d2) * inv;
+      if (r3 > j && r3 < k) M[r3 * ldl + j] = (M[r3 * ldl + j] - d3) * inv;
       __syncwarp();
     }
+    if (lane == 0) *flag = fail ? 1 : 0;
+    __syncwarp();
     bool ok = (*flag == 0) && !bad;
     if (ok) {
       for (int e = lane; e < k * r; e += 32) RV[e] = YS[e].hi;
       __syncwarp();
-      solve_f32(L, ldl, invd, RV, k, r, lane);
+      solve_f32(M, ldl, invd, RV, k, r, lane);
       for (int e = lane; e < k * r; e += 32) XV[e] = dfl{RV[e], 0.0f};
       __syncwarp();
       float prev = 1.0f;
       bool conv = false;
       for (int step = 1; step <= kMaxRefine; ++step) {
-        // residual y - K x in DF; lane owns rows
+        // residual y - K x in DF; lane owns rows; K_ab = (upper hi, packed lo)
 #pragma unroll
         for (int s = 0; s < kMaxSlots; ++s) {
           const int row = lane + 32 * s;
           if (row < k) {
+            const int rb = row * (row - 1) / 2;
             for (int c = 0; c < r; ++c) {
               dfl acc = YS[row * r + c];
-              for (int b = 0; b < k; ++b) {
-                const dfl kab = (b <= row) ? KP[row * (row + 1) / 2 + b] : KP[b * (b + 1) / 2 + row];
+              acc = df_add(acc, df_neg(df_mul(kp.diag, XV[row * r + c])));
+              for (int b = 0; b < row; ++b) {  // K_row,b = (M[b][row], LO[row(row-1)/2 + b])
+                const dfl kab = {M[b * ldl + row], LO[rb + b]};
                 acc = df_add(acc, df_neg(df_mul(kab, XV[b * r + c])));
+              }
+              int cb = row * (row + 1) / 2;  // b(b-1)/2 at b = row + 1
+              for (int b = row + 1; b < k; ++b) {  // K_b,row = (M[row][b], LO[b(b-1)/2 + row])
+                const dfl kab = {M[row * ldl + b], LO[cb + row]};
+                acc = df_add(acc, df_neg(df_mul(kab, XV[b * r + c])));
+                cb += b;
               }
               RV[row * r + c] = acc.hi;
             }
           }
         }
         __syncwarp();
-        solve_f32(L, ldl, invd, RV, k, r, lane);
+        solve_f32(M, ldl, invd, RV, k, r, lane);
         float dmax = 0.0f, xmax = 0.0f;
         for (int e = lane; e < k * r; e += 32) {
           const dfl v = df_add_f(XV[e], RV[e]);
@@ -318,7 +450,10 @@ __global__ void __launch_bounds__(256) block_mixed_kernel(BlockArgs args, MixedA
       }
     } else if (!LOO) {
       float2* Ci = (float2*)args.C + i * (int64_t)k * r;
-      for (int e = lane; e < k * r; e += 32) Ci[e] = make_float2(XV[e].hi, XV[e].lo);
+      for (int e = lane; e < k * r; e += 32) {
+        const dfl cv = df_mul(XV[e], kp.inv_var);
+        Ci[e] = make_float2(cv.hi, cv.lo);
+      }
       if (args.status && lane == 0) args.status[i] = FMGP_BLOCK_OK;
     } else {
       // leave-one-out residual of x_i from its k neighbours, in DF
@@ -328,7 +463,7 @@ __global__ void __launch_bounds__(256) block_mixed_kernel(BlockArgs args, MixedA
       for (int s = 0; s < kMaxSlots; ++s) {
         const int a = lane + 32 * s;
         kx[s] = dfl{0.0f, 0.0f};
-        if (a < k) kx[s] = kernel_df(kp, sqdist_df(xi, XS + a * d, d), mx.K);
+        if (a < k) kx[s] = corr_df(kp, sqdist_df(xi, XS + a * d, d), mx.K);
       }
       dfl e2 = {0.0f, 0.0f};
       for (int c = 0; c < r; ++c) {
@@ -397,7 +532,7 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
     if (s < nslots && a < k) {
       int64_t idx = (a == 0) ? j : (int64_t)nbr[j * ld + a - 1];
       if (idx < 0 || idx >= n) idx = j;
-      kz[s] = kernel_df(kp, sqdist_df(z, Xdf + idx * d, d), K);
+      kz[s] = corr_df(kp, sqdist_df(z, Xdf + idx * d, d), K);
     }
   }
   for (int c = 0; c < r; ++c) {
@@ -415,7 +550,7 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
       const dfl o = {__shfl_xor_sync(kFull, acc.hi, off), __shfl_xor_sync(kFull, acc.lo, off)};
       acc = df_add(acc, o);
     }
-    if (lane == 0) Yhat[w * r + c] = df_to_double(acc);
+    if (lane == 0) Yhat[w * r + c] = df_to_double(df_mul(acc, kp.var));
   }
 }
 

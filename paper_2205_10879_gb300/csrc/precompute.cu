@@ -20,7 +20,7 @@ __device__ __forceinline__ void pair_of(int p, int& a, int& b) {
 }
 
 template <typename T, bool LOO>
-__global__ void __launch_bounds__(256) block_f64_kernel(BlockArgs args, const T* X) {
+__global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const T* X) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BlockLayout lay = args.layout;
   const int wpb = blockDim.x >> 5;
@@ -77,24 +77,28 @@ __global__ void __launch_bounds__(256) block_f64_kernel(BlockArgs args, const T*
     __syncwarp();
     // Cholesky, Crout order: step j forms column j of L
     for (int j = 0; j < k; ++j) {
-      double dots[kMaxSlots];
-#pragma unroll
-      for (int s = 0; s < kMaxSlots; ++s) {
-        const int row = lane + 32 * s;
-        dots[s] = 0.0;
-        if (row >= j && row < k) {
-          double acc = 0.0;
-          const double* lr = L + row * ldl;
-          const double* lj = L + j * ldl;
-          for (int p = 0; p < j; ++p) acc = fma(lr[p], lj[p], acc);
-          dots[s] = acc;
-        }
+      const double* lj = L + j * ldl;
+      const int r0 = lane, r1 = lane + 32, r2 = lane + 64, r3 = lane + 96;
+      double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+      if (r0 >= j && r0 < k) {
+        const double* lr = L + r0 * ldl;
+        for (int p = 0; p < j; ++p) d0 = fma(lr[p], lj[p], d0);
+      }
+      if (r1 >= j && r1 < k) {
+        const double* lr = L + r1 * ldl;
+        for (int p = 0; p < j; ++p) d1 = fma(lr[p], lj[p], d1);
+      }
+      if (r2 >= j && r2 < k) {
+        const double* lr = L + r2 * ldl;
+        for (int p = 0; p < j; ++p) d2 = fma(lr[p], lj[p], d2);
+      }
+      if (r3 >= j && r3 < k) {
+        const double* lr = L + r3 * ldl;
+        for (int p = 0; p < j; ++p) d3 = fma(lr[p], lj[p], d3);
       }
       if (lane == (j & 31)) {
-        double dj = dots[0];
-#pragma unroll
-        for (int s = 1; s < kMaxSlots; ++s)
-          if (s == (j >> 5)) dj = dots[s];
+        const int sj = j >> 5;
+        const double dj = sj == 0 ? d0 : (sj == 1 ? d1 : (sj == 2 ? d2 : d3));
         const double v = L[j * ldl + j] - dj;
         if (!(v > 0.0)) {
           *flag = 1;
@@ -107,11 +111,10 @@ __global__ void __launch_bounds__(256) block_f64_kernel(BlockArgs args, const T*
       __syncwarp();
       if (*flag) break;
       const double inv = invd[j];
-#pragma unroll
-      for (int s = 0; s < kMaxSlots; ++s) {
-        const int row = lane + 32 * s;
-        if (row > j && row < k) L[row * ldl + j] = (L[row * ldl + j] - dots[s]) * inv;
-      }
+      if (r0 > j && r0 < k) L[r0 * ldl + j] = (L[r0 * ldl + j] - d0) * inv;
+      if (r1 > j && r1 < k) L[r1 * ldl + j] = (L[r1 * ldl + j] - d1) * inv;
+      if (r2 > j && r2 < k) L[r2 * ldl + j] = (L[r2 * ldl + j] - d2) * inv;
+      if (r3 > j && r3 < k) L[r3 * ldl + j] = (L[r3 * ldl + j] - d3) * inv;
       __syncwarp();
     }
     const bool fail = (*flag != 0) || bad;
