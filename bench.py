@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serving-requests", type=int, default=300)
     p.add_argument("--n", type=int, default=150_000)
     p.add_argument("--m", type=int, default=50_000)
     p.add_argument("--k", type=int, default=50)
@@ -301,12 +303,52 @@ def run_ours(a):
         "block_status": {str(v): int(c) for v, c in zip(*np.unique(st_main, return_counts=True))},
         "gpu_launches": launches, "clocks": clocks,
     }
+    if not a.no_serving:
+        line["serving"] = serving_bench(a, dev)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(W, a, samples=(20000, 20000, 5000))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------- serving ----
+def serving_bench(a, dev):
+    """Eight resident models (n log-uniform in [1e4, 2e6], d in {2,3,16,64},
+    k in {16,32,64,128}, Matern/RBF, mixed precision; n capped at 200,000 for
+    d >= 16, whose kNN table is built by exhaustive scan), one continuous-
+    batching server (4 streams), Poisson request streams of log-uniform 1..65,536
+    points at 50% and 90% of the measured saturation rate: p50/p99 latency
+    (submission to results in host memory) and predictions/s."""
+    from paper_2205_10879_gb300 import _binding as fb
+    from paper_2205_10879_gb300 import serving, workloads as wl
+    specs = wl.serving_models()
+    models = []
+    t0 = time.perf_counter()
+    for s in specs:
+        X, Y = s["X"], s["Y"]
+        if X.shape[1] >= 16 and X.shape[0] > 200_000:
+            X, Y = X[:200_000], Y[:200_000]
+        models.append(serving.fit_model(X, Y, s["k"], s["kernel"], fb.PREC_MIXED))
+    fit_s = time.perf_counter() - t0
+    srv = fb.FmgpServer(models, device_budget_bytes=4 << 30, host_staging_bytes=2 << 30,
+                        streams=4)
+    # saturation: a burst of requests all at once
+    lat, pts, wall = serving.run_poisson(srv, models, 0.0, max(40, a.serving_requests // 4), 11)
+    sat = serving.latency_summary(lat, pts, wall)
+    req_rate = sat["requests"] / sat["wall_s"]
+    out = {"models": [{"n": int(m.n), "d": int(m.d), "k": int(m.k)} for m in models],
+           "fit_seconds": fit_s, "saturation": sat}
+    for frac in (0.5, 0.9):
+        lat, pts, wall = serving.run_poisson(srv, models, frac * req_rate, a.serving_requests,
+                                             12 + int(frac * 10))
+        out[f"load_{int(frac * 100)}"] = serving.latency_summary(lat, pts, wall)
+    out["server"] = srv.stats()
+    srv.close()
+    for m in models:
+        m.close()
+    return out
 
 
 # ------------------------------------------------------------- oracle ----

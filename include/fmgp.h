@@ -168,6 +168,96 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
                          fmgp_precision precision, double* Q_out, double* resid_out,
                          void* stream);
 
+/* ------------------------------------------------------------------------
+ * Resident models and the serving loop (the paper's online phase run as a
+ * service: Sec. 1 motivates FastMuyGPs by applications that need many fast
+ * successive predictions from a trained model, Sec. 3 gives the O(k) lookup).
+ * ---------------------------------------------------------------------- */
+typedef struct fmgp_model fmgp_model;
+
+/*
+ * fmgp_model_create -- register a fitted model for repeated prediction.
+ * X, nbr and C (as produced by fmgp_build_knn / fmgp_precompute with the same
+ * k, kernel and precision) are BORROWED: they must stay valid and unchanged
+ * until fmgp_model_destroy.  The model builds and OWNS the nearest-point
+ * search grid (d <= 3) and, for FMGP_PREC_MIXED, a double-float copy of X.
+ * Synchronises `stream` before returning.  *out receives the handle.
+ */
+int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
+                      int32_t nbr_ld, const void* C, int32_t k, int32_t r,
+                      const fmgp_kernel* kernel, fmgp_precision precision, fmgp_model** out,
+                      void* stream);
+
+/* fmgp_predict through a model (Eq. 7): same results, no index rebuild.
+ * Z (m x d device, the model's dtype), Yhat_out (m x r FP64 device),
+ * nearest_out (m int32 device or NULL).  Asynchronous on `stream`. */
+int fmgp_model_predict(fmgp_model* model, const void* Z, int64_t m, double* Yhat_out,
+                       int32_t* nearest_out, void* stream);
+
+/* Free the model's own buffers (waits for the device to go idle first). */
+int fmgp_model_destroy(fmgp_model* model);
+
+/* Device bytes owned by the model (grid + double-float copy), -1 for NULL. */
+int64_t fmgp_model_device_bytes(const fmgp_model* model);
+
+typedef struct fmgp_server fmgp_server;
+
+typedef struct {
+  int64_t device_budget_bytes;  /* admitted requests' device bytes (inputs + outputs) */
+  int64_t host_staging_bytes;   /* pinned staging arena; >= the largest request */
+  int32_t streams;              /* batches in flight at once (1..16) */
+  int32_t max_batch_points;     /* cap on test points per launched batch */
+} fmgp_server_config;
+
+typedef struct {
+  int64_t submitted, completed, rejected;
+  int64_t batches;              /* launched batches */
+  int64_t points;               /* completed test points */
+  double mean_batch_requests;   /* requests per batch */
+} fmgp_server_stats;
+
+/*
+ * fmgp_server_create -- a continuous-batching prediction service over
+ * `count` resident models (borrowed; they must outlive the server).  A
+ * scheduler thread admits queued requests first-come-first-served while
+ * their device bytes fit the budget, launches every admitted request of a
+ * model as one batch on the next free stream (so batches of different
+ * models and later arrivals overlap on the device), and completes requests
+ * from event polling.  Each prediction depends only on its own test point,
+ * so a request's result is bit-identical alone or inside any batch.
+ * The device current at creation is used by the scheduler thread.
+ */
+int fmgp_server_create(fmgp_model* const* models, int32_t count, const fmgp_server_config* cfg,
+                       fmgp_server** out);
+
+/*
+ * fmgp_server_submit -- enqueue a prediction request: m test points
+ * Z_host (m x d, HOST memory, the model's dtype, copied at admission so it
+ * may be reused once the request completes), results written to HOST
+ * buffers Yhat_host (m x r FP64) and nearest_host (m int32 or NULL) when
+ * the request completes.  Returns FMGP_ENOMEM if the request alone exceeds
+ * the device budget or the staging arena; *request_id identifies it.
+ */
+int fmgp_server_submit(fmgp_server* srv, int32_t model, const void* Z_host, int64_t m,
+                       double* Yhat_host, int32_t* nearest_host, uint64_t* request_id);
+
+/* Wait up to timeout_ms (< 0: forever) for a request: FMGP_OK when its
+ * results are in the host buffers, FMGP_ETIMEOUT otherwise, or the error
+ * the request failed with. */
+int fmgp_server_wait(fmgp_server* srv, uint64_t request_id, int32_t timeout_ms);
+
+/* Host-side milliseconds from submission to launch and to completion. */
+int fmgp_server_request_times(fmgp_server* srv, uint64_t request_id, double* queue_ms,
+                              double* total_ms);
+
+/* Forget a finished request (its id becomes invalid). */
+int fmgp_server_release(fmgp_server* srv, uint64_t request_id);
+
+int fmgp_server_get_stats(fmgp_server* srv, fmgp_server_stats* out);
+
+/* Stop accepting work, finish everything in flight, free the server. */
+int fmgp_server_destroy(fmgp_server* srv);
+
 /*
  * fmgp_loocv_objective_noalloc -- fmgp_loocv_objective without any device
  * allocation.  The paper has no counterpart: this is a deployment variant.

@@ -39,6 +39,17 @@ def make_kernel(kind="matern", nu=1.5, length_scale=0.1, variance=1.0, nugget=1e
                   float(length_scale), float(variance), float(nugget))
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_int64), ("host_staging_bytes", ctypes.c_int64),
+                ("streams", ctypes.c_int32), ("max_batch_points", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("points", ctypes.c_int64), ("mean_batch_requests", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -68,6 +79,25 @@ def load(build_if_missing=True):
     lib.fmgp_last_error.restype = ctypes.c_char_p
     lib.fmgp_version.restype = ctypes.c_char_p
     lib.fmgp_kernel_launches.restype = ctypes.c_uint64
+    lib.fmgp_model_create.argtypes = [P, I32, I64, I32, P, I32, P, I32, I32, KP, I32,
+                                      ctypes.POINTER(ctypes.c_void_p), P]
+    lib.fmgp_model_predict.argtypes = [P, P, I64, P, P, P]
+    lib.fmgp_model_destroy.argtypes = [P]
+    lib.fmgp_model_device_bytes.argtypes = [P]
+    lib.fmgp_model_device_bytes.restype = I64
+    lib.fmgp_server_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I32,
+                                       ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
+    lib.fmgp_server_submit.argtypes = [P, I32, P, I64, P, P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.fmgp_server_wait.argtypes = [P, ctypes.c_uint64, I32]
+    lib.fmgp_server_request_times.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]
+    lib.fmgp_server_release.argtypes = [P, ctypes.c_uint64]
+    lib.fmgp_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.fmgp_server_destroy.argtypes = [P]
+    for f in ("fmgp_model_create", "fmgp_model_predict", "fmgp_model_destroy", "fmgp_server_create",
+              "fmgp_server_submit", "fmgp_server_wait", "fmgp_server_request_times",
+              "fmgp_server_release", "fmgp_server_get_stats", "fmgp_server_destroy"):
+        getattr(lib, f).restype = I32
     _lib = lib
     return lib
 
@@ -182,3 +212,110 @@ def version():
 def kernel_launches():
     """Kernels libfmgp has enqueued since it was loaded."""
     return int(load().fmgp_kernel_launches())
+
+
+class FmgpModel:
+    """fmgp_model_create / fmgp_model_predict / fmgp_model_destroy.  Keeps
+    references to the borrowed tensors X, nbr and C for its lifetime."""
+
+    def __init__(self, X, nbr, C, k, kernel, precision=PREC_FP64, stream=None):
+        _dev(X, "X"); _dev(nbr, "nbr"); _dev(C, "C")
+        self.X, self.nbr, self.C, self.k, self.kernel, self.precision = X, nbr, C, k, kernel, precision
+        self.n, self.d = X.shape
+        self.r = C.shape[2]
+        self.dtype = X.dtype
+        h = ctypes.c_void_p()
+        _check(load().fmgp_model_create(_ptr(X), _dtype_code(X), self.n, self.d, _ptr(nbr),
+                                        nbr.shape[1], _ptr(C), int(k), self.r,
+                                        ctypes.byref(kernel), int(precision), ctypes.byref(h),
+                                        _stream(stream)))
+        self.handle = h
+
+    def predict(self, Z, Yhat_out=None, nearest_out=None, with_nearest=True, stream=None):
+        _dev(Z, "Z")
+        m = Z.shape[0]
+        if Yhat_out is None:
+            Yhat_out = torch.empty((m, self.r), dtype=torch.float64, device=Z.device)
+        if with_nearest and nearest_out is None:
+            nearest_out = torch.empty(m, dtype=torch.int32, device=Z.device)
+        _check(load().fmgp_model_predict(self.handle, _ptr(Z), m, _ptr(Yhat_out),
+                                         _ptr(nearest_out), _stream(stream)))
+        return Yhat_out, nearest_out
+
+    def device_bytes(self):
+        return int(load().fmgp_model_device_bytes(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().fmgp_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FmgpServer:
+    """fmgp_server_*: continuous-batching prediction service over resident
+    models.  submit() takes host numpy test points and returns the request id;
+    results land in host arrays returned by result()."""
+
+    def __init__(self, models, device_budget_bytes=1 << 28, host_staging_bytes=1 << 28,
+                 streams=4, max_batch_points=1 << 20):
+        self.models = list(models)
+        arr = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
+        cfg = ServerConfig(int(device_budget_bytes), int(host_staging_bytes), int(streams),
+                           int(max_batch_points))
+        h = ctypes.c_void_p()
+        _check(load().fmgp_server_create(arr, len(self.models), ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self.live = {}
+
+    def submit(self, model, Z, with_nearest=False):
+        md = self.models[model]
+        import numpy as np
+        Z = np.ascontiguousarray(Z, dtype=np.float64 if md.dtype == torch.float64 else np.float32)
+        m = Z.shape[0]
+        Y = np.empty((m, md.r), np.float64)
+        N = np.empty(m, np.int32) if with_nearest else None
+        rid = ctypes.c_uint64()
+        _check(load().fmgp_server_submit(self.handle, int(model), Z.ctypes.data_as(ctypes.c_void_p), m,
+                                         Y.ctypes.data_as(ctypes.c_void_p),
+                                         N.ctypes.data_as(ctypes.c_void_p) if N is not None else None,
+                                         ctypes.byref(rid)))
+        self.live[rid.value] = (Z, Y, N)
+        return rid.value
+
+    def wait(self, rid, timeout_ms=-1):
+        rc = load().fmgp_server_wait(self.handle, ctypes.c_uint64(rid), int(timeout_ms))
+        if rc == FMGP_ETIMEOUT:
+            return False
+        _check(rc)
+        return True
+
+    def result(self, rid):
+        _, Y, N = self.live[rid]
+        return Y, N
+
+    def times(self, rid):
+        q = ctypes.c_double()
+        t = ctypes.c_double()
+        _check(load().fmgp_server_request_times(self.handle, ctypes.c_uint64(rid), ctypes.byref(q),
+                                                ctypes.byref(t)))
+        return q.value, t.value
+
+    def release(self, rid):
+        _check(load().fmgp_server_release(self.handle, ctypes.c_uint64(rid)))
+        return self.live.pop(rid)
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().fmgp_server_get_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().fmgp_server_destroy(self.handle)
+            self.handle = None

@@ -69,6 +69,7 @@ void* Workspace::alloc(size_t bytes) {
     return nullptr;
   }
   ptrs_[count_++] = p;
+  bytes_ += bytes;
   return p;
 }
 

@@ -136,8 +136,17 @@ class Workspace {
   // Returns nullptr (and records the error) on failure.
   void* alloc(size_t bytes);
   template <typename T> T* get(size_t count) { return (T*)alloc(count * sizeof(T)); }
+  // Hand every allocation so far to the caller (who then frees them); returns the count.
+  int detach(void** out, int max) {
+    int c = count_ < max ? count_ : max;
+    for (int i = 0; i < c; ++i) out[i] = ptrs_[i];
+    count_ = 0;
+    return c;
+  }
+  size_t bytes() const { return bytes_; }
 
  private:
+  size_t bytes_ = 0;
   cudaStream_t stream_;
   void* ptrs_[32];
   int count_ = 0;

@@ -488,25 +488,6 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
   }
 }
 
-template <typename T>
-__global__ void to_df_kernel(const T* in, float2* out, int64_t count) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)in[i];
-    const float hi = (float)v;
-    out[i] = make_float2(hi, (float)(v - (double)hi));
-  }
-}
-
-int to_df(const void* in, bool f64, int64_t count, float2* out, cudaStream_t s) {
-  if (count == 0) return FMGP_OK;
-  const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), (int64_t)num_sms() * 8);
-  if (f64) FMGP_LAUNCH(to_df_kernel<double><<<blocks, 256, 0, s>>>((const double*)in, out, count));
-  else FMGP_LAUNCH(to_df_kernel<float><<<blocks, 256, 0, s>>>((const float*)in, out, count));
-  FMGP_CUDA_TRY(cudaGetLastError());
-  return FMGP_OK;
-}
-
 // A5 in DF: lane a evaluates sigma^2 phi(||z - x_{S[a]}||) in DF; the k-term
 // dot products with C[j*] are reduced by a fixed xor-butterfly in DF.
 __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
@@ -556,6 +537,25 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
 
 }  // namespace
 
+template <typename T>
+__global__ void to_df_kernel(const T* in, float2* out, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)in[i];
+    const float hi = (float)v;
+    out[i] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+int to_df(const void* in, bool f64, int64_t count, float2* out, cudaStream_t s) {
+  if (count == 0) return FMGP_OK;
+  const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), (int64_t)num_sms() * 8);
+  if (f64) FMGP_LAUNCH(to_df_kernel<double><<<blocks, 256, 0, s>>>((const double*)in, out, count));
+  else FMGP_LAUNCH(to_df_kernel<float><<<blocks, 256, 0, s>>>((const float*)in, out, count));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
 size_t mixed_bytes_per_warp(int k, int d, int r) { return mixed_layout(k, d, r).bytes; }
 
 int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int warps,
@@ -598,12 +598,13 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int 
 int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
                      const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
                      const void* Z, int64_t m, const int32_t* nearest, double* Yhat,
-                     Workspace& ws, cudaStream_t stream) {
+                     Workspace& ws, cudaStream_t stream, const float2* Xdf_cached) {
   if (m == 0) return FMGP_OK;
-  float2* Xdf = ws.get<float2>((size_t)n * d);
+  float2* Xdf = Xdf_cached ? nullptr : ws.get<float2>((size_t)n * d);
   float2* Zdf = ws.get<float2>((size_t)m * d);
-  if (!Xdf || !Zdf) return FMGP_ENOMEM;
-  int rc = to_df(X, dtype == FMGP_F64, n * d, Xdf, stream);
+  if ((!Xdf && !Xdf_cached) || !Zdf) return FMGP_ENOMEM;
+  int rc = Xdf_cached ? FMGP_OK : to_df(X, dtype == FMGP_F64, n * d, Xdf, stream);
+  if (Xdf_cached) Xdf = (float2*)Xdf_cached;
   if (!rc) rc = to_df(Z, dtype == FMGP_F64, m * d, Zdf, stream);
   if (rc) return rc;
   const int blocks = ceil_div(m * 32, 256);

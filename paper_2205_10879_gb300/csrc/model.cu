@@ -1,0 +1,121 @@
+// Resident fitted models: a model borrows the caller's X, neighbour table and
+// coefficients and owns what prediction would otherwise rebuild per call (the
+// search grid over X for d <= 3, the double-float copy of X for the mixed
+// form), so repeated prediction batches (the serving loop) only run the
+// nearest-point lookup and the gather-dot.
+#include "model.cuh"
+#include "predict.cuh"
+
+namespace fmgp {
+
+Model::~Model() {
+  for (int i = 0; i < nbufs; ++i) cudaFree(bufs[i]);
+}
+
+}  // namespace fmgp
+
+using namespace fmgp;
+
+extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d,
+                                 const int32_t* nbr, int32_t nbr_ld, const void* C, int32_t k,
+                                 int32_t r, const fmgp_kernel* kernel, fmgp_precision precision,
+                                 fmgp_model** out, void* stream) {
+  if (!out) { set_error("out must be non-NULL"); return FMGP_EINVAL; }
+  *out = nullptr;
+  if (!X || !C || (k > 1 && !nbr) || !kernel) {
+    set_error("X, C, kernel (and nbr when k > 1) must be non-NULL");
+    return FMGP_EINVAL;
+  }
+  if (dtype != FMGP_F32 && dtype != FMGP_F64) { set_error("dtype unknown"); return FMGP_EINVAL; }
+  if (precision != FMGP_PREC_FP64 && precision != FMGP_PREC_MIXED) {
+    set_error("precision unknown");
+    return FMGP_EINVAL;
+  }
+  if (n < 1 || n >= INT32_MAX || d < 1 || r < 1 || k < 1 || k > n || k > kMaxK ||
+      nbr_ld < k - 1) {
+    set_error("shape invalid: n=%lld d=%d r=%d k=%d nbr_ld=%d", (long long)n, d, r, k, nbr_ld);
+    return FMGP_EINVAL;
+  }
+  if (kernel->kind == FMGP_KERNEL_MATERN &&
+      !(kernel->nu == 0.5 || kernel->nu == 1.5 || kernel->nu == 2.5)) {
+    set_error("Matern nu = %g unsupported", kernel->nu);
+    return FMGP_EINVAL;
+  }
+  if (!(kernel->length_scale > 0) || !(kernel->variance > 0) || !(kernel->nugget >= 0)) {
+    set_error("kernel hyperparameters invalid");
+    return FMGP_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Model* m = new Model();
+  m->X = X; m->dtype = dtype; m->n = n; m->d = d; m->nbr = nbr; m->ld = nbr_ld; m->C = C;
+  m->k = k; m->r = r; m->kern = *kernel; m->prec = precision;
+  Workspace ws(s);
+  int rc = FMGP_OK;
+  if (d <= kGridMaxD) {
+    rc = build_grid(X, dtype, n, d, tune_params().grid_target, ws, s, &m->grid);
+    m->has_grid = (rc == FMGP_OK);
+  }
+  if (!rc && precision == FMGP_PREC_MIXED) {
+    m->Xdf = ws.get<float2>((size_t)n * d);
+    if (!m->Xdf) rc = FMGP_ENOMEM;
+    else rc = to_df(X, dtype == FMGP_F64, n * d, m->Xdf, s);
+  }
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  m->bytes = ws.bytes();
+  m->nbufs = ws.detach(m->bufs, Model::kMaxBufs);
+  if (rc) {
+    delete m;
+    return rc;
+  }
+  *out = reinterpret_cast<fmgp_model*>(m);
+  return FMGP_OK;
+}
+
+extern "C" int fmgp_model_predict(fmgp_model* model, const void* Z, int64_t m, double* Yhat_out,
+                                  int32_t* nearest_out, void* stream) {
+  Model* md = reinterpret_cast<Model*>(model);
+  if (!md) { set_error("model is NULL"); return FMGP_EINVAL; }
+  if (m < 0) { set_error("m = %lld must be >= 0", (long long)m); return FMGP_EINVAL; }
+  if (m == 0) return FMGP_OK;
+  if (!Z || !Yhat_out) { set_error("Z and Yhat_out must be non-NULL"); return FMGP_EINVAL; }
+  return model_predict(*md, Z, m, Yhat_out, nearest_out, (cudaStream_t)stream);
+}
+
+extern "C" int fmgp_model_destroy(fmgp_model* model) {
+  Model* md = reinterpret_cast<Model*>(model);
+  if (!md) return FMGP_EINVAL;
+  cudaDeviceSynchronize();  // in-flight work may still read the model's buffers
+  delete md;
+  return FMGP_OK;
+}
+
+extern "C" int64_t fmgp_model_device_bytes(const fmgp_model* model) {
+  const Model* md = reinterpret_cast<const Model*>(model);
+  return md ? (int64_t)md->bytes : -1;
+}
+
+namespace fmgp {
+
+int model_predict(const Model& md, const void* Z, int64_t m, double* Yhat, int32_t* nearest,
+                  cudaStream_t s) {
+  Workspace ws(s);
+  int32_t* near = nearest;
+  if (!near) {
+    near = ws.get<int32_t>(m);
+    if (!near) return FMGP_ENOMEM;
+  }
+  int rc = md.has_grid ? nearest_on_grid(md.grid, Z, md.dtype, m, near, s)
+                       : nearest_train(md.X, md.dtype, md.n, md.d, Z, m, near, tune_params(), ws, s);
+  if (rc) return rc;
+  const KParams kp = make_kparams(md.kern);
+  if (md.prec == FMGP_PREC_MIXED)
+    return gather_dot_mixed(md.X, md.dtype, md.n, md.d, md.nbr, md.ld, md.C, md.k, md.r, kp,
+                            md.kern, Z, m, near, Yhat, ws, s, md.Xdf);
+  return gather_dot(md.X, md.dtype, md.n, md.d, md.nbr, md.ld, md.C, md.k, md.r, kp, md.kern,
+                    md.prec, Z, m, near, Yhat, ws, s);
+}
+
+}  // namespace fmgp

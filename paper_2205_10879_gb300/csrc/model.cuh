@@ -1,0 +1,32 @@
+#pragma once
+#include "common.cuh"
+#include "grid.cuh"
+#include "knn.cuh"
+
+namespace fmgp {
+
+TuneParams& tune_params();
+
+struct Model {
+  static constexpr int kMaxBufs = 32;
+  const void* X = nullptr;
+  fmgp_dtype dtype = FMGP_F64;
+  int64_t n = 0;
+  int d = 0, ld = 0, k = 0, r = 0;
+  const int32_t* nbr = nullptr;
+  const void* C = nullptr;
+  fmgp_kernel kern{};
+  fmgp_precision prec = FMGP_PREC_FP64;
+  bool has_grid = false;
+  GridView grid{};
+  float2* Xdf = nullptr;
+  void* bufs[kMaxBufs];
+  int nbufs = 0;
+  size_t bytes = 0;
+  ~Model();
+};
+
+int model_predict(const Model& md, const void* Z, int64_t m, double* Yhat, int32_t* nearest,
+                  cudaStream_t s);
+
+}  // namespace fmgp

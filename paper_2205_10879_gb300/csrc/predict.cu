@@ -123,6 +123,14 @@ int launch_nn1_grid(const GridView& gv, const void* Z, fmgp_dtype dt, int64_t m,
 
 }  // namespace
 
+int nearest_on_grid(const GridView& gv, const void* Z, fmgp_dtype dtype, int64_t m,
+                    int32_t* nearest, cudaStream_t stream) {
+  if (m == 0) return FMGP_OK;
+  if (gv.D == 1) return launch_nn1_grid<1>(gv, Z, dtype, m, nearest, stream);
+  if (gv.D == 2) return launch_nn1_grid<2>(gv, Z, dtype, m, nearest, stream);
+  return launch_nn1_grid<3>(gv, Z, dtype, m, nearest, stream);
+}
+
 int nearest_train(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Z, int64_t m,
                   int32_t* nearest, const TuneParams& tp, Workspace& ws, cudaStream_t stream) {
   if (m == 0) return FMGP_OK;

@@ -1,0 +1,61 @@
+"""Serving harness: fit resident models through the C ABI and drive the
+continuous-batching server with a Poisson request stream, reporting
+predictions/s and per-request latency percentiles."""
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import _binding as fb
+
+
+def fit_model(X, Y, k, kernel_spec, precision, device="cuda"):
+    """kNN table + precompute + resident model for one training set."""
+    s = kernel_spec
+    gk = fb.make_kernel(s.kind, s.nu, s.length_scale, s.variance, s.nugget)
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).to(device)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y)).to(device)
+    nbr, _ = fb.fmgp_build_knn(Xd, max(k - 1, 1))
+    C, _ = fb.fmgp_precompute(Xd, Yd, nbr, k, gk, precision, with_status=False)
+    return fb.FmgpModel(Xd, nbr, C, k, gk, precision)
+
+
+def run_poisson(server, models, rate_hz, count, seed, max_points=65_536):
+    """Submit `count` requests with exponential inter-arrival times at
+    `rate_hz`; sizes log-uniform in [1, max_points], points uniform in the
+    unit cube of the model's dimension.  Returns per-request latencies (ms),
+    total points and the wall time from first submission to last completion."""
+    rng = np.random.default_rng(seed)
+    plan = []
+    for _ in range(count):
+        j = int(rng.integers(len(models)))
+        size = max(1, int(np.exp(rng.uniform(0.0, np.log(max_points)))))
+        plan.append((j, rng.random((size, models[j].d))))
+    gaps = rng.exponential(1.0 / rate_hz, size=count) if rate_hz > 0 else np.zeros(count)
+    ids = []
+    t0 = time.perf_counter()
+    nxt = t0
+    for (j, Z), g in zip(plan, gaps):
+        nxt += g
+        while True:
+            now = time.perf_counter()
+            if now >= nxt:
+                break
+            time.sleep(min(nxt - now, 0.0005))
+        ids.append(server.submit(j, Z))
+    lat = []
+    for rid in ids:
+        server.wait(rid, -1)
+        lat.append(server.times(rid)[1])
+    wall = time.perf_counter() - t0
+    for rid in ids:
+        server.release(rid)
+    pts = sum(Z.shape[0] for _, Z in plan)
+    return np.array(lat), pts, wall
+
+
+def latency_summary(lat, pts, wall):
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "requests": int(len(lat)),
+            "predictions_per_s": pts / wall, "points": int(pts), "wall_s": wall}

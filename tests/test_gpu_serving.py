@@ -1,0 +1,117 @@
+"""Serving form: resident models and the continuous-batching server.
+
+The key property: a request's predictions do not depend on what else is in
+flight, so results are bit-identical when each request runs alone and when
+all requests arrive at once and get batched and overlapped."""
+import threading
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2205_10879_gb300 import _binding as fb
+from paper_2205_10879_gb300 import workloads as wl
+from gpu_helpers import dev, kern_pair
+
+pytestmark = pytest.mark.gpu
+
+
+def _fit(W, k, prec):
+    _, gk = kern_pair(W.kernel)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, max(k - 1, 1))
+    C, _ = fb.fmgp_precompute(X, dev(W.Y), nbr, k, gk, prec)
+    return fb.FmgpModel(X, nbr, C, k, gk, prec)
+
+
+@pytest.mark.parametrize("prec", [fb.PREC_FP64, fb.PREC_MIXED])
+def test_model_predict_matches_fmgp_predict(cuda, prec):
+    W = wl.tiny()
+    md = _fit(W, 30, prec)
+    Z = dev(W.Z)
+    y1, n1 = md.predict(Z)
+    y2, n2 = fb.fmgp_predict(md.X, md.nbr, md.C, 30, md.kernel, Z, prec)
+    assert torch.equal(n1, n2)
+    assert torch.equal(y1, y2)
+    assert md.device_bytes() > 0
+    md.close()
+
+
+def _models():
+    a = _fit(wl.tiny(n=4000, m=10), 30, fb.PREC_FP64)
+    b = _fit(wl.large(n=60_000, m=10), 64, fb.PREC_MIXED)
+    rng = np.random.default_rng(3)
+    Xh = rng.random((3000, 16))
+    W16 = wl.Workload("d16", Xh, np.sin(Xh.sum(1, keepdims=True)), Xh[:5], Xh[:5, :1], 16,
+                      wl.KernelSpec("rbf", 0.0, 0.4, 1.0, 1e-3), np.arange(5))
+    c = _fit(W16, 16, fb.PREC_FP64)
+    return [a, b, c]
+
+
+def _requests(models, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        j = int(rng.integers(len(models)))
+        size = int(np.exp(rng.uniform(0, np.log(3000))))
+        out.append((j, rng.random((size, models[j].d))))
+    return out
+
+
+def test_server_results_same_alone_and_in_the_mix(cuda):
+    models = _models()
+    reqs = _requests(models, 36, 5)
+    # alone: one stream, each request waited for before the next is submitted
+    srv = fb.FmgpServer(models, streams=1)
+    alone = []
+    for j, Z in reqs:
+        rid = srv.submit(j, Z, with_nearest=True)
+        assert srv.wait(rid, 60_000)
+        Y, N = srv.result(rid)
+        alone.append((Y.copy(), N.copy()))
+    srv.close()
+    # mix: four streams, everything submitted at once from two threads
+    srv = fb.FmgpServer(models, streams=4)
+    ids = [None] * len(reqs)
+
+    def submit(lo, hi):
+        for q in range(lo, hi):
+            ids[q] = srv.submit(reqs[q][0], reqs[q][1], with_nearest=True)
+    ts = [threading.Thread(target=submit, args=(0, 18)), threading.Thread(target=submit, args=(18, 36))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for q, rid in enumerate(ids):
+        assert srv.wait(rid, 60_000)
+        Y, N = srv.result(rid)
+        assert np.array_equal(Y, alone[q][0]), q
+        assert np.array_equal(N, alone[q][1]), q
+    st = srv.stats()
+    assert st["completed"] == len(reqs)
+    assert st["mean_batch_requests"] > 1.0  # requests were batched together
+    srv.close()
+    # and both equal a direct prediction through the model
+    for q, (j, Z) in enumerate(reqs[:6]):
+        y, n = models[j].predict(dev(Z))
+        assert np.array_equal(y.cpu().numpy(), alone[q][0])
+
+
+def test_server_admission_by_memory(cuda):
+    md = _fit(wl.tiny(n=4000, m=10), 30, fb.PREC_FP64)
+    per_req = 1000 * (2 * 8 + 8 + 4) + 3 * 256
+    srv = fb.FmgpServer([md], device_budget_bytes=2 * per_req + 100, host_staging_bytes=1 << 22,
+                        streams=4)
+    rng = np.random.default_rng(1)
+    ids = [srv.submit(0, rng.random((1000, 2))) for _ in range(20)]
+    qs = []
+    for rid in ids:
+        assert srv.wait(rid, 60_000)
+        qs.append(srv.times(rid)[0])
+    assert max(qs) > 0.0
+    with pytest.raises(fb.FmgpError) as e:
+        srv.submit(0, rng.random((10_000, 2)))
+    assert e.value.code == fb.FMGP_ENOMEM
+    assert srv.stats()["rejected"] == 1
+    srv.close()
+    md.close()
