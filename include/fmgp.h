@@ -292,6 +292,22 @@ const char* fmgp_last_error(void);
 /* Library version, e.g. "0.1.0". */
 const char* fmgp_version(void);
 
+/*
+ * Launch-shape and path controls (results never depend on them):
+ *   "grid_target"  mean training points per grid cell of the d <= 3 search (default 12)
+ *   "block_warps"  warps per CTA of the neighbourhood kernels, 0 = automatic
+ *   "tensor_cores" 1 = tcgen05 candidate search for kNN at d >= 16 (default), 0 = off
+ * Process-wide; returns FMGP_EINVAL for an unknown key or a value out of range.
+ */
+int fmgp_tune_set(const char* key, double value);
+double fmgp_tune_get(const char* key);  /* -1 for an unknown key */
+
+/* Diagnostic counters: 0 = kernels enqueued, 1 = tensor-core kNN calls,
+ * 2 = queries of the most recent tensor-core kNN call that lacked a
+ * certificate and were redone by the exact scan (valid once that call's
+ * stream has completed). */
+int64_t fmgp_diag_counter(int32_t which);
+
 /* Number of CUDA kernels this library has enqueued since it was loaded
  * (all threads, all devices); a diagnostic counter for launch accounting. */
 uint64_t fmgp_kernel_launches(void);

@@ -79,6 +79,12 @@ def load(build_if_missing=True):
     lib.fmgp_last_error.restype = ctypes.c_char_p
     lib.fmgp_version.restype = ctypes.c_char_p
     lib.fmgp_kernel_launches.restype = ctypes.c_uint64
+    lib.fmgp_tune_set.argtypes = [ctypes.c_char_p, ctypes.c_double]
+    lib.fmgp_tune_set.restype = I32
+    lib.fmgp_tune_get.argtypes = [ctypes.c_char_p]
+    lib.fmgp_tune_get.restype = ctypes.c_double
+    lib.fmgp_diag_counter.argtypes = [I32]
+    lib.fmgp_diag_counter.restype = I64
     lib.fmgp_model_create.argtypes = [P, I32, I64, I32, P, I32, P, I32, I32, KP, I32,
                                       ctypes.POINTER(ctypes.c_void_p), P]
     lib.fmgp_model_predict.argtypes = [P, P, I64, P, P, P]
@@ -207,6 +213,18 @@ def fmgp_loocv_objective(X, Y, nbr, k, batch, kernel, precision=PREC_FP64, resid
 
 def version():
     return load().fmgp_version().decode()
+
+
+def tune_set(key, value):
+    _check(load().fmgp_tune_set(key.encode(), float(value)))
+
+
+def tune_get(key):
+    return float(load().fmgp_tune_get(key.encode()))
+
+
+def diag_counter(which):
+    return int(load().fmgp_diag_counter(int(which)))
 
 
 def kernel_launches():

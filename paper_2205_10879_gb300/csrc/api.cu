@@ -146,6 +146,23 @@ TuneParams& tune_params() {
   return tp;
 }
 
+static std::atomic<long long> g_tc_calls{0};
+static int* g_tc_fallbacks_host = nullptr;  // pinned
+
+void diag_record_tc(const int* fb_count_dev, cudaStream_t s) {
+  static std::once_flag once;
+  std::call_once(once, []() {
+    if (cudaHostAlloc((void**)&g_tc_fallbacks_host, sizeof(int), cudaHostAllocDefault) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      g_tc_fallbacks_host = nullptr;
+    }
+  });
+  g_tc_calls.fetch_add(1);
+  if (g_tc_fallbacks_host)
+    cudaMemcpyAsync(g_tc_fallbacks_host, fb_count_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+
 // Precompute / LOOCV blocks in the requested precision.
 static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo,
                       const fmgp_kernel& kern, fmgp_precision precision, Workspace& ws,
@@ -188,6 +205,42 @@ extern "C" {
 const char* fmgp_last_error(void) { return g_err; }
 const char* fmgp_version(void) { return "0.1.0"; }
 uint64_t fmgp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t fmgp_diag_counter(int32_t which) {
+  if (which == 0) return (int64_t)g_launches.load();
+  if (which == 1) return (int64_t)g_tc_calls.load();
+  if (which == 2) return g_tc_fallbacks_host ? (int64_t)*(volatile int*)g_tc_fallbacks_host : -1;
+  return -1;
+}
+
+int fmgp_tune_set(const char* key, double value) {
+  if (!key) { set_error("key is NULL"); return FMGP_EINVAL; }
+  TuneParams& tp = tune_params();
+  const std::string k(key);
+  if (k == "grid_target") {
+    if (!(value >= 1.0 && value <= 4096.0)) { set_error("grid_target out of range"); return FMGP_EINVAL; }
+    tp.grid_target = value;
+  } else if (k == "block_warps") {
+    if (!(value >= 0 && value <= 8)) { set_error("block_warps out of range"); return FMGP_EINVAL; }
+    tp.block_warps = (int)value;
+  } else if (k == "tensor_cores") {
+    tp.use_tensor_cores = value != 0.0;
+  } else {
+    set_error("unknown tuning key '%s'", key);
+    return FMGP_EINVAL;
+  }
+  return FMGP_OK;
+}
+
+double fmgp_tune_get(const char* key) {
+  if (!key) return -1.0;
+  const TuneParams& tp = tune_params();
+  const std::string k(key);
+  if (k == "grid_target") return tp.grid_target;
+  if (k == "block_warps") return tp.block_warps;
+  if (k == "tensor_cores") return tp.use_tensor_cores ? 1.0 : 0.0;
+  return -1.0;
+}
 
 int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
                    int32_t* nbr_out, double* dist_out, int32_t flags, void* stream) {

@@ -153,6 +153,11 @@ class Workspace {
 };
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Diagnostics: count a tensor-core kNN call and copy its number of queries
+// that needed the exact fallback (device int) to a host slot read by
+// fmgp_diag_counter after the stream has completed.
+void diag_record_tc(const int* fb_count_dev, cudaStream_t s);
 int num_sms();
 
 }  // namespace fmgp

@@ -89,22 +89,28 @@ __global__ void maxabs_kernel(const void* X, int f64, int64_t count, unsigned in
 template <typename T, int L>
 __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
     const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int exclude_self,
-    const unsigned int* maxabs_bits, int32_t* idx_out, double* key_out) {
+    const unsigned int* maxabs_bits, int32_t* idx_out, double* key_out, const int* qlist,
+    const int* qcount) {
   extern __shared__ float sm[];
   const int ld = d | 1;  // odd stride: conflict-free column reads
   float* tile = sm;                          // kBfTile x ld (chunk of columns)
   float* qs = sm + kBfTile * ld;             // kBfWarps x ld
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t q = (int64_t)blockIdx.x * kBfWarps + wid;
-  const bool qvalid = q < m;
+  // query of this warp: position p of the (optional) list
+  const int64_t count = qlist ? (int64_t)*qcount : m;
+  if ((int64_t)blockIdx.x * kBfWarps >= count) return;  // whole CTA idle
+  const int64_t pos = (int64_t)blockIdx.x * kBfWarps + wid;
+  const bool qvalid = pos < count;
+  const int64_t q = qvalid ? (qlist ? (int64_t)qlist[pos] : pos) : 0;
   const float M = __uint_as_float(*maxabs_bits);
   const float cerr = (sizeof(T) == 8) ? 2.5f * kU * M : 0.f;
   const float rel = 1.0f - (2.0f * d + 8.0f) * kU;
   // stage this CTA's queries (FP32)
   for (int e = threadIdx.x; e < kBfWarps * d; e += blockDim.x) {
     const int w = e / d, j = e % d;
-    const int64_t qq = (int64_t)blockIdx.x * kBfWarps + w;
-    qs[w * ld + j] = qq < m ? (float)Q[qq * d + j] : 0.f;
+    const int64_t pp = (int64_t)blockIdx.x * kBfWarps + w;
+    const int64_t qq = pp < count ? (qlist ? (int64_t)qlist[pp] : pp) : -1;
+    qs[w * ld + j] = qq >= 0 ? (float)Q[qq * d + j] : 0.f;
   }
   WarpTopK<L> top;
   top.init(kq);
@@ -161,7 +167,8 @@ int launch_grid_self(const GridView& gv, int kq, int32_t* nbr, double* dist, cud
 
 template <typename T, int L>
 int launch_brute_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
-                   const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s) {
+                   const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
+                   const int* qlist = nullptr, const int* qcount = nullptr) {
   const int ld = d | 1;
   const size_t smem = sizeof(float) * (size_t)(kBfTile + kBfWarps) * ld;
   if (smem > 200 * 1024) {
@@ -170,14 +177,15 @@ int launch_brute_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, 
   }
   auto kern = knn_brute_kernel<T, L>;
   FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(X, n, d, Q, m, kq, excl, mx, idx, key));
+  FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(X, n, d, Q, m, kq, excl, mx, idx, key, qlist, qcount));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
 
 template <typename T>
 int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
-                 Workspace& ws, int32_t* idx, double* key, cudaStream_t s) {
+                 Workspace& ws, int32_t* idx, double* key, cudaStream_t s,
+                 const int* qlist = nullptr, const int* qcount = nullptr) {
   unsigned int* mx = ws.get<unsigned int>(1);
   if (!mx) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), s));
@@ -187,13 +195,23 @@ int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, in
     const int qb = (int)std::min<int64_t>(ceil_div(m * d, 256), (int64_t)num_sms() * 8);
     if (m > 0) FMGP_LAUNCH(maxabs_kernel<<<qb, 256, 0, s>>>(Q, sizeof(T) == 8, m * d, mx));
   }
-  if (kq <= 32) return launch_brute_t<T, 1>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
-  if (kq <= 64) return launch_brute_t<T, 2>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
-  if (kq <= 96) return launch_brute_t<T, 3>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
-  return launch_brute_t<T, 4>(X, n, d, Q, m, kq, excl, mx, idx, key, s);
+  if (kq <= 32) return launch_brute_t<T, 1>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 64) return launch_brute_t<T, 2>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 96) return launch_brute_t<T, 3>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  return launch_brute_t<T, 4>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
 }
 
 }  // namespace
+
+int knn_brute_list(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
+                   int kq, bool self, const int* qlist, const int* qcount, int32_t* idx,
+                   double* key, Workspace& ws, cudaStream_t stream) {
+  if (dtype == FMGP_F64)
+    return launch_brute<double>((const double*)X, n, d, (const double*)Q, m, kq, self ? 1 : 0, ws,
+                                idx, key, stream, qlist, qcount);
+  return launch_brute<float>((const float*)X, n, d, (const float*)Q, m, kq, self ? 1 : 0, ws, idx,
+                             key, stream, qlist, qcount);
+}
 
 int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t* nbr,
              double* dist, const TuneParams& tp, Workspace& ws, cudaStream_t stream) {
@@ -205,6 +223,8 @@ int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t*
     if (d == 2) return launch_grid_self<2>(gv, kq, nbr, dist, stream);
     return launch_grid_self<3>(gv, kq, nbr, dist, stream);
   }
+  if (tc_knn_eligible(n, d, n, kq))
+    return tc_knn(X, dtype, n, d, X, n, kq, true, nbr, dist, ws, stream);
   if (dtype == FMGP_F64)
     return launch_brute<double>((const double*)X, n, d, (const double*)X, n, kq, 1, ws, nbr, dist,
                                 stream);
@@ -215,6 +235,8 @@ int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t*
 int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
                     int kq, int32_t* idx, double* key, Workspace& ws, cudaStream_t stream) {
   if (m == 0) return FMGP_OK;
+  if (tc_knn_eligible(n, d, m, kq))
+    return tc_knn(X, dtype, n, d, Q, m, kq, false, idx, key, ws, stream);
   if (dtype == FMGP_F64)
     return launch_brute<double>((const double*)X, n, d, (const double*)Q, m, kq, 0, ws, idx, key,
                                 stream);

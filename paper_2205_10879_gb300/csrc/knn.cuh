@@ -6,13 +6,28 @@ namespace fmgp {
 
 // Launch-shape choices the autotuner may change; results never depend on them.
 struct TuneParams {
-  double grid_target = 12.0;  // mean training points per grid cell
-  int block_warps = 0;        // warps per CTA for block kernels (0 = automatic)
+  double grid_target = 12.0;     // mean training points per grid cell
+  int block_warps = 0;           // warps per CTA for block kernels (0 = automatic)
+  bool use_tensor_cores = true;  // tcgen05 candidate search for d >= 16
 };
+
+TuneParams& tune_params();
 
 // Self kNN table (A1): nbr (n x kq), dist (n x kq canonical keys, or null).
 int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t* nbr,
              double* dist, const TuneParams& tp, Workspace& ws, cudaStream_t stream);
+
+// Exhaustive exact scan for the queries listed in qlist[0..*qcount) (count
+// read on the device); self = the queries are rows of X (each excluded from
+// its own list).
+int knn_brute_list(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
+                   int kq, bool self, const int* qlist, const int* qcount, int32_t* idx,
+                   double* key, Workspace& ws, cudaStream_t stream);
+
+// Tensor-core candidate search + certified exact re-rank (d >= 16).
+bool tc_knn_eligible(int64_t n, int d, int64_t m, int kq);
+int tc_knn(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m, int kq,
+           bool self, int32_t* idx_out, double* key_out, Workspace& ws, cudaStream_t s);
 
 // kq nearest training points of each of m queries by exhaustive scan (d >= 4).
 int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,

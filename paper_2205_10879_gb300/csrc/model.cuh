@@ -5,7 +5,7 @@
 
 namespace fmgp {
 
-TuneParams& tune_params();
+
 
 struct Model {
   static constexpr int kMaxBufs = 32;
