@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--k", type=int, default=50)
     p.add_argument("--b", type=int, default=10_000)
     p.add_argument("--nu", type=float, default=1.5)
+    p.add_argument("--workload", default="spatial", choices=["spatial", "highdim-knn"])
+    p.add_argument("--no-highdim", action="store_true")
     return p.parse_args()
 
 
@@ -303,6 +305,8 @@ def run_ours(a):
         "block_status": {str(v): int(c) for v, c in zip(*np.unique(st_main, return_counts=True))},
         "gpu_launches": launches, "clocks": clocks,
     }
+    if not a.no_highdim:
+        line["highdim_knn"] = highdim_knn_bench(a, dev, steps=a.steps, warmup=1)
     if not a.no_serving:
         line["serving"] = serving_bench(a, dev)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
@@ -311,6 +315,45 @@ def run_ours(a):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------- high-d kNN (A1) ----
+def highdim_knn_bench(a, dev, steps, warmup):
+    """A1 on the 784-D workload: self kNN table (kq = 29) of n = 60,000 FP32
+    points (80% exact zeros), through the tensor-core candidate search with
+    certified exact re-rank.  Tensor roofline: 2 * n_pad * n_pad * d_pad BF16
+    flops of the distance GEMM over the whole call's time (an upper bound on
+    the GEMM kernel's own time)."""
+    import torch
+    from paper_2205_10879_gb300 import _binding as fb
+    from paper_2205_10879_gb300 import workloads as wl
+    W = wl.highdim()
+    X = torch.from_numpy(W.X).to(dev)
+    nbr = torch.empty((W.n, 29), dtype=torch.int32, device=dev)
+    for _ in range(warmup):
+        fb.fmgp_build_knn(X, 29, nbr_out=nbr)
+    torch.cuda.synchronize()
+    ts = []
+    c0 = fb.diag_counter(1)
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fb.fmgp_build_knn(X, 29, nbr_out=nbr)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    n_pad = (W.n + 255) // 256 * 256
+    d_pad = (W.d + 63) // 64 * 64
+    flops = 2.0 * n_pad * n_pad * d_pad
+    peak = 1948.7
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"workload": "highdim-784 self kNN", "n": W.n, "d": W.d, "kq": 29, "ms": ms,
+            "knn_queries_per_s": W.n / (ms * 1e-3), "tensor_core_calls": fb.diag_counter(1) - c0,
+            "uncertified_queries": fb.diag_counter(2),
+            "roofline_call": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                              "frac": ach / peak, "note": "whole call incl. pack/select/re-rank"}}
 
 
 # ------------------------------------------------------------- serving ----
@@ -422,6 +465,11 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "highdim-knn":
+        import torch
+        from paper_2205_10879_gb300 import _binding as fb
+        fb.load()
+        print(json.dumps(highdim_knn_bench(a, torch.device("cuda", 0), a.steps, a.warmup)))
     else:
         run_ours(a)
 

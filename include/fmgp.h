@@ -302,6 +302,24 @@ const char* fmgp_version(void);
 int fmgp_tune_set(const char* key, double value);
 double fmgp_tune_get(const char* key);  /* -1 for an unknown key */
 
+/*
+ * Autotuner (the paper has no counterpart: launch-shape selection).
+ * fmgp_autotune_precompute times the neighbourhood kernel with each feasible
+ * warps-per-CTA on the first sample_rows rows of this problem and caches the
+ * fastest for (precision, k, d, r, dtype); later fmgp_precompute /
+ * fmgp_loocv_objective calls with that key use it.  fmgp_autotune_knn times
+ * the grid search of fmgp_build_knn at several cell occupancies and caches
+ * the fastest for (d, kq) (d <= 3; for larger d it reports 0).  Results of
+ * the path never depend on these choices.  Both synchronise `stream`.
+ */
+int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                             int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                             const fmgp_kernel* kernel, fmgp_precision precision,
+                             int64_t sample_rows, int32_t* warps_out, void* stream);
+int fmgp_autotune_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
+                      double* grid_target_out, void* stream);
+int fmgp_autotune_reset(void);
+
 /* Diagnostic counters: 0 = kernels enqueued, 1 = tensor-core kNN calls,
  * 2 = queries of the most recent tensor-core kNN call that lacked a
  * certificate and were redone by the exact scan (valid once that call's

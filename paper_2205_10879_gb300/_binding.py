@@ -85,6 +85,12 @@ def load(build_if_missing=True):
     lib.fmgp_tune_get.restype = ctypes.c_double
     lib.fmgp_diag_counter.argtypes = [I32]
     lib.fmgp_diag_counter.restype = I64
+    lib.fmgp_autotune_precompute.argtypes = [P, I32, P, I64, I32, I32, P, I32, I32, KP, I32, I64,
+                                             ctypes.POINTER(I32), P]
+    lib.fmgp_autotune_precompute.restype = I32
+    lib.fmgp_autotune_knn.argtypes = [P, I32, I64, I32, I32, ctypes.POINTER(ctypes.c_double), P]
+    lib.fmgp_autotune_knn.restype = I32
+    lib.fmgp_autotune_reset.restype = I32
     lib.fmgp_model_create.argtypes = [P, I32, I64, I32, P, I32, P, I32, I32, KP, I32,
                                       ctypes.POINTER(ctypes.c_void_p), P]
     lib.fmgp_model_predict.argtypes = [P, P, I64, P, P, P]
@@ -213,6 +219,31 @@ def fmgp_loocv_objective(X, Y, nbr, k, batch, kernel, precision=PREC_FP64, resid
 
 def version():
     return load().fmgp_version().decode()
+
+
+def fmgp_autotune_precompute(X, Y, nbr, k, kernel, precision=PREC_FP64, sample_rows=20_000,
+                             stream=None):
+    """Pick (and cache) the fastest warps-per-CTA for this precompute shape."""
+    n, d = X.shape
+    w = ctypes.c_int32(0)
+    _check(load().fmgp_autotune_precompute(_ptr(X), _dtype_code(X), _ptr(Y), n, d, Y.shape[1],
+                                           _ptr(nbr), nbr.shape[1], int(k), ctypes.byref(kernel),
+                                           int(precision), int(sample_rows), ctypes.byref(w),
+                                           _stream(stream)))
+    return w.value
+
+
+def fmgp_autotune_knn(X, kq, stream=None):
+    """Pick (and cache) the fastest grid occupancy for this kNN shape (d <= 3)."""
+    n, d = X.shape
+    t = ctypes.c_double(0)
+    _check(load().fmgp_autotune_knn(_ptr(X), _dtype_code(X), n, d, int(kq), ctypes.byref(t),
+                                    _stream(stream)))
+    return t.value
+
+
+def autotune_reset():
+    _check(load().fmgp_autotune_reset())
 
 
 def tune_set(key, value):

@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <math.h>
 #include <atomic>
+#include <map>
+#include <string>
 #include <mutex>
 #include "block.cuh"
 #include "knn.cuh"
@@ -26,6 +28,19 @@ void set_error(const char* fmt, ...) {
 int cuda_fail(cudaError_t e, const char* what) {
   set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
   return FMGP_ECUDA;
+}
+
+cudaError_t ensure_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = cache[{dev, func}];
+  if (cur >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 int num_sms() {
@@ -176,7 +191,9 @@ static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo,
               a.r, std::max(bytes, a.layout.bytes_per_warp));
     return FMGP_EUNSUPPORTED;
   }
-  const int warps = pick_warps(bytes, tune_params().block_warps);
+  int req = tune_params().block_warps;
+  if (req == 0) req = tuned_block_warps((int)precision, a.k, a.d, a.r, (int)dtype);
+  const int warps = pick_warps(bytes, req);
   if (precision == FMGP_PREC_FP64) return launch_block_f64(a, X, dtype, loo, warps, s);
   return run_block_mixed(a, X, dtype, loo, warps, kern, ws, s);
 }
@@ -254,7 +271,9 @@ int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_
   FMGP_REQUIRE(flags == 0, "flags must be 0");
   cudaStream_t s = (cudaStream_t)stream;
   Workspace ws(s);
-  return knn_self(X, dtype, n, d, kq, nbr_out, dist_out, tune_params(), ws, s);
+  TuneParams tp = tune_params();
+  tp.grid_target = grid_target_for(d, kq);
+  return knn_self(X, dtype, n, d, kq, nbr_out, dist_out, tp, ws, s);
 }
 
 static int validate_block_args(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,

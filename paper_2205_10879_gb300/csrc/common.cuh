@@ -121,6 +121,12 @@ void note_launch();
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, calling
+// cudaFuncSetAttribute only when the cached limit (per device and function)
+// is too low, so that steady-state launches (and stream capture into CUDA
+// graphs after a warm-up call) make no attribute calls.
+cudaError_t ensure_smem(const void* func, size_t bytes);
+
 #define FMGP_CUDA_TRY(call)                                  \
   do {                                                       \
     cudaError_t _e = (call);                                 \

@@ -176,7 +176,7 @@ int launch_brute_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, 
     return FMGP_EUNSUPPORTED;
   }
   auto kern = knn_brute_kernel<T, L>;
-  FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
   FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(X, n, d, Q, m, kq, excl, mx, idx, key, qlist, qcount));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;

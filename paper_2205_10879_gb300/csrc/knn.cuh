@@ -13,6 +13,10 @@ struct TuneParams {
 
 TuneParams& tune_params();
 
+// Autotuner caches (0 / the default when nothing was tuned for the key).
+int tuned_block_warps(int prec, int k, int d, int r, int dtype);
+double grid_target_for(int d, int kq);
+
 // Self kNN table (A1): nbr (n x kq), dist (n x kq canonical keys, or null).
 int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t* nbr,
              double* dist, const TuneParams& tp, Workspace& ws, cudaStream_t stream);

@@ -581,7 +581,7 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int 
   const int64_t need = (a.count + warps - 1) / warps;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
   auto kern_fn = loo ? block_mixed_kernel<true> : block_mixed_kernel<false>;
-  FMGP_CUDA_TRY(cudaFuncSetAttribute(kern_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
   FMGP_LAUNCH(kern_fn<<<blocks, warps * 32, smem, s>>>(a, mx, lay));
   FMGP_CUDA_TRY(cudaGetLastError());
   // FP64 fallback over the listed blocks (count read on the device)

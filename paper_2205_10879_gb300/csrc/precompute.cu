@@ -5,6 +5,7 @@
 // either stores W as the row C_i (precompute) or dots it with the
 // cross-covariance of x_i to form the leave-one-out residual (LOOCV).
 #include "block.cuh"
+#include "knn.cuh"
 
 namespace fmgp {
 namespace {
@@ -233,11 +234,11 @@ int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, bool l
   if (blocks <= 0) blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 16));
   if (dtype == FMGP_F64) {
     auto kern = loo ? block_f64_kernel<double, true> : block_f64_kernel<double, false>;
-    FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
     FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const double*)X));
   } else {
     auto kern = loo ? block_f64_kernel<float, true> : block_f64_kernel<float, false>;
-    FMGP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
     FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const float*)X));
   }
   FMGP_CUDA_TRY(cudaGetLastError());

@@ -129,12 +129,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Approximate squared distances for query blocks [qb0, qb0 + gridDim.x) against
-// every candidate tile.  out row (qb - qb0)*128 + i holds query qb*128 + i.
+// Approximate squared distances of query block blockIdx.x against candidate
+// tiles tile0 + blockIdx.y*tpc .. (at most tpc tiles, not past tile_end).
+// out row q (query q), column (t - tile0)*256 + j holds candidate t*256 + j.
 __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
     const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX,
-    const float* __restrict__ qnorm, const float* __restrict__ xnorm, int qb0, int n_tiles,
-    int k_chunks, int64_t ld_out, float* __restrict__ out, int* __restrict__ err) {
+    const float* __restrict__ qnorm, const float* __restrict__ xnorm, int tile0, int tile_end,
+    int tpc, int k_chunks, int64_t ld_out, float* __restrict__ out, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + (size_t)kStages * kStageBytes);
@@ -144,7 +145,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
   uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int qb = qb0 + blockIdx.x;
+  const int qb = blockIdx.x;
+  const int t_first = tile0 + blockIdx.y * tpc;
+  const int n_tiles = max(0, min(tpc, tile_end - t_first));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
           unsigned char* a = smem + (size_t)s * kStageBytes;
           mbar_expect_tx(&full[s], kStageBytes);
           tma_load_2d(a, &tmQ, &full[s], kc * kTK, qb * kTM);
-          tma_load_2d(a + kABytes, &tmX, &full[s], kc * kTK, t * kTN);
+          tma_load_2d(a + kABytes, &tmX, &full[s], kc * kTK, (t_first + t) * kTN);
         }
       }
     }
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
   } else {  // epilogue warps 0-3: TMEM lanes 32*warp .. 32*warp+31
     const int row = warp * 32 + lane;
     const float qn = qnorm[(int64_t)qb * kTM + row];
-    float* orow = out + ((int64_t)blockIdx.x * kTM + row) * ld_out;
+    float* orow = out + ((int64_t)qb * kTM + row) * ld_out;
     for (int t = 0; t < n_tiles; ++t) {
       const int b = t & 1;
       const uint32_t u = (uint32_t)(t >> 1);
@@ -223,9 +226,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
       for (int c = 0; c < kTN / 32; ++c) {
         uint32_t v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kTN + c * 32), v);
-        const int col0 = t * kTN + c * 32;
-        const float* xn = xnorm + col0;
-        float4* dst = reinterpret_cast<float4*>(orow + col0);
+        const int gcol = (t_first + t) * kTN + c * 32;
+        const float* xn = xnorm + gcol;
+        float4* dst = reinterpret_cast<float4*>(orow + (gcol - tile0 * kTN));
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           float4 o;
@@ -292,95 +295,304 @@ __global__ void pack_bf16_kernel(const T* __restrict__ X, int64_t rows, int d, i
   }
 }
 
-// One warp per query row of the pass buffer: the L smallest approximate
-// distances (negative values clamp to 0; ties by index).
+// One warp per query: merge the chunk of approximate distances (columns
+// col0 .. col0+ncols of the global candidate range, row q of Dc) into the
+// query's running list of the L smallest (FP32 keys as bits, ties by index;
+// negative values clamp to 0).  first = no previous list.
 template <int S>
-__global__ void __launch_bounds__(256) select_kernel(const float* __restrict__ Dp, int64_t ld,
-                                                     int64_t q0, int64_t rows, int64_t n, int L,
-                                                     int exclude_self, int32_t* __restrict__ cand,
-                                                     float* __restrict__ dL) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(256) select_merge_kernel(
+    const float* __restrict__ Dc, int64_t ld, int64_t m, int64_t col0, int64_t ncols, int64_t n,
+    int L, int exclude_self, int first, int32_t* __restrict__ cand, float* __restrict__ ckey,
+    float* __restrict__ dL) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= rows) return;
-  const int64_t q = q0 + w;
-  const float* row = Dp + w * ld;
+  if (q >= m) return;
   WarpTopK<S> top;
   top.init(L);
-  for (int64_t base = 0; base < n; base += 32) {
-    const int64_t j = base + lane;
-    unsigned long long ck = ~0ull;
-    int ci = INT_MAX;
-    if (j < n && !(exclude_self && j == q)) {
-      // keys are the FP32 bit patterns of non-negative values (ordered like integers)
-      const unsigned long long v = (unsigned long long)__float_as_uint(fmaxf(row[j], 0.0f));
-      if (v <= top.tk) {
-        ck = v;
-        ci = (int)j;
-      }
+  if (!first) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int g = lane * S + s;
+      const int j = cand[q * L + g];
+      top.k[s] = j == INT_MAX ? ~0ull : (unsigned long long)__float_as_uint(ckey[q * L + g]);
+      top.i[s] = j;
     }
-    top.offer(ck, ci, lane);
+    unsigned long long mk = top.k[0];
+    int mi = top.i[0];
+#pragma unroll
+    for (int s = 1; s < S; ++s)
+      if (s == top.ts) { mk = top.k[s]; mi = top.i[s]; }
+    top.tk = __shfl_sync(kFull, mk, top.tl);
+    top.ti = __shfl_sync(kFull, mi, top.tl);
   }
-  top.store(L, lane, cand + q * L, nullptr);
+  const float* row = Dc + q * ld;
+  const int64_t cols = min(ncols, n - col0);
+  for (int64_t base = 0; base < cols; base += 128) {
+    float v4[4];
+    const int64_t c = base + 4 * lane;
+    if (c + 3 < cols) {
+      const float4 f = *reinterpret_cast<const float4*>(row + c);
+      v4[0] = f.x; v4[1] = f.y; v4[2] = f.z; v4[3] = f.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v4[e] = c + e < cols ? row[c + e] : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int64_t j = col0 + c + e;
+      unsigned long long ck = ~0ull;
+      int ci = INT_MAX;
+      if (c + e < cols && !(exclude_self && j == q)) {
+        const unsigned long long v = (unsigned long long)__float_as_uint(fmaxf(v4[e], 0.0f));
+        if (v <= top.tk) { ck = v; ci = (int)j; }
+      }
+      top.offer(ck, ci, lane);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int g = lane * S + s;
+    if (g < L) {
+      cand[q * L + g] = top.i[s];
+      ckey[q * L + g] = top.i[s] == INT_MAX ? 0.f : __uint_as_float((unsigned int)top.k[s]);
+    }
+  }
   // largest approximate distance in the list (position L-1); +inf if not full
   if (lane == 0)
     dL[q] = top.full() ? __uint_as_float((unsigned int)top.tk) : __int_as_float(0x7f800000);
 }
 
 // Exact re-rank with certificate; uncertified queries go to the fallback list.
-template <typename T, int S>
-__global__ void __launch_bounds__(256) rerank_kernel(
+// One warp per query.  Candidate rows are read through a shared-memory tile
+// (32 rows x 64 features, padded) so every global read is coalesced and each
+// lane then walks its own row.
+//   A: FP32 squared distances of the L candidates with rigorous bounds
+//      (relative (d+4)u for the FP32 sum, plus the FP64->FP32 conversion of
+//      both vectors); U = the kq-th smallest upper bound.
+//   B: only candidates whose lower bound does not exceed U can be among the
+//      kq nearest: they are compacted and get their canonical FP64 keys.
+constexpr int kRrWarps = 4;
+constexpr int kRrChunk = 32;
+
+template <typename T>
+__device__ __forceinline__ void load_rows(const T* X, int d, const int* rows, int nrows, int c0,
+                                          int cw, T* tile, int lane) {
+  // tile: 32 rows x (kRrChunk + 1).  Full 16-byte-aligned chunks are read with
+  // 16-byte loads, several rows per warp instruction.
+  constexpr int V = 16 / sizeof(T);            // elements per 16-byte load
+  constexpr int PER_ROW = kRrChunk / V;        // loads per row chunk
+  if (cw == kRrChunk && (d % V) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    for (int e = lane; e < nrows * PER_ROW; e += 32) {
+      const int r = e / PER_ROW, v = e - r * PER_ROW;
+      const int j = rows[r];
+      if (j < 0) continue;
+      const T* src = X + (int64_t)j * d + c0 + v * V;
+      const float4 f = *reinterpret_cast<const float4*>(src);
+      const T* fv = reinterpret_cast<const T*>(&f);
+#pragma unroll
+      for (int t = 0; t < V; ++t) tile[r * (kRrChunk + 1) + v * V + t] = fv[t];
+    }
+    return;
+  }
+  for (int r = 0; r < nrows; ++r) {
+    const int j = rows[r];
+    if (j < 0) continue;
+    const T* src = X + (int64_t)j * d + c0;
+    for (int p = lane; p < cw; p += 32) tile[r * (kRrChunk + 1) + p] = src[p];
+  }
+}
+
+template <typename T, int S, int KS>
+__global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     const T* __restrict__ X, const T* __restrict__ Q, int d, int64_t m, int L, int kq,
     const int32_t* __restrict__ cand, const float* __restrict__ dL,
     const float* __restrict__ qnorm2, const float* __restrict__ qdelta,
-    const unsigned int* __restrict__ xstats, const unsigned int* __restrict__ qstats,
-    const int* __restrict__ err, int32_t* __restrict__ idx_out, double* __restrict__ key_out,
-    int* fb_list, int* fb_count) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= m) return;
+    const unsigned int* __restrict__ xstats, const int* __restrict__ err,
+    int32_t* __restrict__ idx_out, double* __restrict__ key_out, int* fb_list, int* fb_count) {
+  __shared__ T tiles[kRrWarps][33 * (kRrChunk + 1)];
+  __shared__ int lists[kRrWarps][2][128];
+  __shared__ float ivl[kRrWarps][2][128];  // FP32 interval (lo, hi) per candidate slot
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kRrWarps + wid;
+  if (w >= m) return;  // warps are independent: no CTA-wide barrier below
+  T* tile = tiles[wid];
+  T* qrow = tile + 32 * (kRrChunk + 1);
+  int* rowlist = lists[wid][0];
+  int* keep = lists[wid][1];
   const T* qr = Q + w * d;
-  WarpTopK<S> top;
-  top.init(kq);
-  for (int base = 0; base < L; base += 32) {
-    const int a = base + lane;
-    unsigned long long ck = ~0ull;
-    int ci = INT_MAX;
-    if (a < L) {
-      const int j = cand[w * L + a];
-      if (j >= 0 && j != INT_MAX) {
-        const T* xr = X + (int64_t)j * d;
-        double t = __dsub_rn((double)qr[0], (double)xr[0]);
-        double s = __dmul_rn(t, t);
-        for (int p = 1; p < d; ++p) {
-          t = __dsub_rn((double)qr[p], (double)xr[p]);
-          s = __dadd_rn(s, __dmul_rn(t, t));
+  const float u = 5.9604645e-8f;
+  const float gam = (d + 4) * u * 1.1f;
+  const float xmaxn = __uint_as_float(xstats[0]);
+  const float qnrm = sqrtf(qnorm2[w]) * 1.0001f + qdelta[w];
+  const float econv = (sizeof(T) == 8) ? 1.01f * u * (qnrm + xmaxn + __uint_as_float(xstats[1])) : 0.f;
+  // A: FP32 bounds for all L candidates
+  float lo[S], hi[S];
+  WarpTopK<KS> ub;
+  ub.init(kq);
+#pragma unroll
+  for (int g = 0; g < S; ++g) {
+    const int a = 32 * g + lane;
+    const int j = a < L ? cand[w * L + a] : INT_MAX;
+    rowlist[lane] = (j == INT_MAX) ? -1 : j;
+    __syncwarp();
+    float acc = 0.f;
+    for (int c0 = 0; c0 < d; c0 += kRrChunk) {
+      const int cw = min(kRrChunk, d - c0);
+      load_rows<T>(X, d, rowlist, 32, c0, cw, tile, lane);
+      for (int p = lane; p < cw; p += 32) qrow[p] = qr[c0 + p];
+      __syncwarp();
+      const T* myrow = tile + lane * (kRrChunk + 1);
+      for (int p = 0; p < cw; ++p) {
+        const float t = (float)qrow[p] - (float)myrow[p];
+        acc = fmaf(t, t, acc);
+      }
+      __syncwarp();
+    }
+    const bool valid = rowlist[lane] >= 0;
+    const float l = fmaxf(sqrtf(acc * (1.0f - gam)) - econv, 0.0f);
+    const float h = sqrtf(acc * (1.0f + gam)) + econv;
+    lo[g] = valid ? l * l * (1.0f - 1e-6f) : __int_as_float(0x7f800000);
+    hi[g] = valid ? h * h * (1.0f + 1e-6f) : __int_as_float(0x7f800000);
+    if (a < 128) {
+      ivl[wid][0][a] = lo[g];
+      ivl[wid][1][a] = hi[g];
+      lists[wid][1][a] = rowlist[lane];
+    }
+    ub.offer(valid ? (unsigned long long)__float_as_uint(hi[g]) : ~0ull, valid ? a : INT_MAX, lane);
+    __syncwarp();
+  }
+  const float U = ub.full() ? __uint_as_float((unsigned int)ub.tk) : __int_as_float(0x7f800000);
+  __syncwarp();
+  // Without requested distances, FP64 keys are needed only when the FP32
+  // intervals leave membership or order open.  If exactly kq candidates have
+  // lower bound <= U (the kq-th smallest upper bound) and, ordered by
+  // midpoint, consecutive intervals are disjoint, that order is the exact one.
+  if (key_out == nullptr) {
+    int cnt = 0;
+#pragma unroll
+    for (int g = 0; g < S; ++g)
+      cnt += __popc(__ballot_sync(kFull, 32 * g + lane < L && lo[g] <= U));
+    if (cnt == kq) {
+      WarpTopK<KS> ord;
+      ord.init(kq);
+#pragma unroll
+      for (int g = 0; g < S; ++g) {
+        const int a = 32 * g + lane;
+        const bool in = a < L && lo[g] <= U;
+        const float mid = 0.5f * lo[g] + 0.5f * hi[g];
+        ord.offer(in ? (unsigned long long)__float_as_uint(mid) : ~0ull, in ? a : INT_MAX, lane);
+      }
+      // positions lane*KS + s hold candidate slots ord.i[s]; check each
+      // position's interval against the next position's
+      bool ok = true;
+      const int nxt0 = __shfl_down_sync(kFull, ord.i[0], 1);
+#pragma unroll
+      for (int s2 = 0; s2 < KS; ++s2) {
+        const int pos = lane * KS + s2;
+        if (pos + 1 < kq) {
+          const int a = ord.i[s2];
+          const int b = (s2 + 1 < KS) ? ord.i[(s2 + 1 < KS) ? s2 + 1 : s2] : nxt0;
+          if (!(ivl[wid][1][a] < ivl[wid][0][b])) ok = false;
         }
-        ck = dbits(s);
-        ci = j;
+      }
+      if (__all_sync(kFull, ok)) {
+        float hk = 0.0f;
+#pragma unroll
+        for (int s2 = 0; s2 < KS; ++s2) {
+          const int pos = lane * KS + s2;
+          if (pos < kq) idx_out[w * kq + pos] = lists[wid][1][ord.i[s2]];
+          if (pos == kq - 1) hk = ivl[wid][1][ord.i[s2]];
+        }
+        hk = __shfl_sync(kFull, hk, (kq - 1) / KS);
+        // certificate with the kq-th member's upper bound
+        const float xdel0 = __uint_as_float(xstats[1]);
+        const float qn0 = sqrtf(qnorm2[w]) * 1.0001f;
+        const float E0 =
+            2.0f * d * 4.0f * u * qn0 * xmaxn + d * u * (qn0 * qn0 + xmaxn * xmaxn) + 1e-30f;
+        const float Dl0 = dL[w];
+        float lb0 = fmaxf(sqrtf(fmaxf(Dl0 - E0, 0.0f)) - qdelta[w] - xdel0, 0.0f);
+        lb0 = lb0 * lb0 * (1.0f - 1e-5f);
+        const bool cert0 = (*err == 0) && (Dl0 == __int_as_float(0x7f800000) || lb0 > hk);
+        if (!cert0 && lane == 0) {
+          const int pos = atomicAdd(fb_count, 1);
+          fb_list[pos] = (int)w;
+        }
+        return;
       }
     }
-    top.offer(ck, ci, lane);
   }
-  // certificate: lower bound of the true distance of any candidate outside
-  // the list (approximate distance >= dL) must exceed the kq-th exact key.
-  const float xmaxn = __uint_as_float(xstats[0]), xdel = __uint_as_float(xstats[1]);
+  // B: compact the candidates that can still be among the kq nearest
+  int nkeep = 0;
+#pragma unroll
+  for (int g = 0; g < S; ++g) {
+    const int a = 32 * g + lane;
+    const bool take = a < L && lo[g] <= U;
+    const unsigned bal = __ballot_sync(kFull, take);
+    if (take) keep[nkeep + __popc(bal & ((1u << lane) - 1u))] = cand[w * L + a];
+    nkeep += __popc(bal);
+  }
+  __syncwarp();
+  WarpTopK<KS> top;
+  top.init(kq);
+  for (int base = 0; base < nkeep; base += 32) {
+    const int cnt = min(32, nkeep - base);
+    rowlist[lane] = lane < cnt ? keep[base + lane] : -1;
+    __syncwarp();
+    double s = 0.0;
+    for (int c0 = 0; c0 < d; c0 += kRrChunk) {
+      const int cw = min(kRrChunk, d - c0);
+      load_rows<T>(X, d, rowlist, cnt, c0, cw, tile, lane);
+      for (int p = lane; p < cw; p += 32) qrow[p] = qr[c0 + p];
+      __syncwarp();
+      if (lane < cnt) {
+        const T* myrow = tile + lane * (kRrChunk + 1);
+        int p = 0;
+        if (c0 == 0) {  // canonical key: first term t0*t0, then left-to-right rounded sums
+          const double t = __dsub_rn((double)qrow[0], (double)myrow[0]);
+          s = __dmul_rn(t, t);
+          p = 1;
+        }
+        for (; p < cw; ++p) {
+          const double t = __dsub_rn((double)qrow[p], (double)myrow[p]);
+          s = __dadd_rn(s, __dmul_rn(t, t));
+        }
+      }
+      __syncwarp();
+    }
+    top.offer(lane < cnt ? dbits(s) : ~0ull, lane < cnt ? rowlist[lane] : INT_MAX, lane);
+    __syncwarp();
+  }
+  // certificate for candidates outside the list (approximate distance >= dL)
+  const float xdel = __uint_as_float(xstats[1]);
   const float qn = sqrtf(qnorm2[w]) * 1.0001f;
-  const float u = 5.9604645e-8f;
   const float E = 2.0f * d * 4.0f * u * qn * xmaxn + d * u * (qn * qn + xmaxn * xmaxn) + 1e-30f;
   const float Dl = dL[w];
-  float lo = sqrtf(fmaxf(Dl - E, 0.0f)) - qdelta[w] - xdel;
-  lo = fmaxf(lo, 0.0f);
-  lo = lo * lo * (1.0f - 1e-5f);
+  float lb = fmaxf(sqrtf(fmaxf(Dl - E, 0.0f)) - qdelta[w] - xdel, 0.0f);
+  lb = lb * lb * (1.0f - 1e-5f);
   const float kth_up = key_bits_to_float_up(top.tk);
   // a distance pass that gave up (err) certifies nothing: every query is redone
-  const bool cert = (*err == 0) && top.full() && (Dl == __int_as_float(0x7f800000) || lo > kth_up);
+  const bool cert =
+      (*err == 0) && top.full() && (Dl == __int_as_float(0x7f800000) || lb > kth_up);
   if (cert) {
     top.store(kq, lane, idx_out + w * kq, key_out ? key_out + w * kq : nullptr);
   } else if (lane == 0) {
     const int pos = atomicAdd(fb_count, 1);
     fb_list[pos] = (int)w;
   }
-  (void)qstats;
+}
+
+template <typename T, int S>
+int launch_rerank(const T* X, const T* Q, int d, int64_t m, int L, int kq, const int32_t* cand,
+                  const float* dL, const float* qn2, const float* qdl, const unsigned int* xst,
+                  const int* err, int32_t* idx, double* key, int* fbl, int* fbc, cudaStream_t s) {
+  const int blocks = ceil_div(m, kRrWarps);
+  const int KS = (kq + 31) / 32;
+  if (KS == 1) FMGP_LAUNCH((rerank_kernel<T, S, 1><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else if (KS == 2) FMGP_LAUNCH((rerank_kernel<T, S, 2><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else if (KS == 3) FMGP_LAUNCH((rerank_kernel<T, S, 3><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else FMGP_LAUNCH((rerank_kernel<T, S, 4><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -455,47 +667,50 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   rc = make_map(&tmQ, Qb, self && m_pad <= n_pad ? n_pad : m_pad, d_pad, kTM);
   if (!rc) rc = make_map(&tmX, Xb, n_pad, d_pad, kTN);
   if (rc) return rc;
-  // pass buffer: at most ~1 GB of approximate distances
-  int64_t qblocks = m_pad / kTM;
-  int64_t pass_blocks = std::max<int64_t>(1, (int64_t)(1ll << 30) / (n_pad * 4 * kTM));
-  pass_blocks = std::min(pass_blocks, qblocks);
-  float* Dp = ws.get<float>((size_t)pass_blocks * kTM * n_pad);
+  // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
+  const int n_tiles = (int)(n_pad / kTN), k_chunks = d_pad / kTK;
+  const int64_t qblocks = m_pad / kTM;
+  int chunk_tiles = (int)std::max<int64_t>(1, (int64_t)(1ll << 30) / (m_pad * 4 * kTN));
+  chunk_tiles = std::min(chunk_tiles, n_tiles);
+  // tiles per CTA: enough CTAs for two waves over the SMs
+  const int64_t want = 2ll * num_sms();
+  int tpc = chunk_tiles;
+  while (tpc > 1 && qblocks * ((chunk_tiles + tpc - 1) / tpc) < want) tpc = (tpc + 1) / 2;
+  const int ysplit = (chunk_tiles + tpc - 1) / tpc;
+  float* Dc = ws.get<float>((size_t)m_pad * chunk_tiles * kTN);
   int32_t* cand = ws.get<int32_t>((size_t)m * L);
+  float* ckey = ws.get<float>((size_t)m * L);
   float* dL = ws.get<float>(m);
   int* err = ws.get<int>(1);
   int* fb_list = ws.get<int>(m);
   int* fb_count = ws.get<int>(1);
-  if (!Dp || !cand || !dL || !err || !fb_list || !fb_count) return FMGP_ENOMEM;
+  if (!Dc || !cand || !ckey || !dL || !err || !fb_list || !fb_count) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   FMGP_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(int), s));
-  FMGP_CUDA_TRY(cudaFuncSetAttribute(tc_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kTcSmem));
-  const int n_tiles = (int)(n_pad / kTN), k_chunks = d_pad / kTK;
-  for (int64_t qb0 = 0; qb0 < qblocks; qb0 += pass_blocks) {
-    const int nb = (int)std::min(pass_blocks, qblocks - qb0);
-    FMGP_LAUNCH(tc_dist_kernel<<<nb, kTcThreads, kTcSmem, s>>>(
-        tmQ, tmX, qn2, xn2, (int)qb0, n_tiles, k_chunks, n_pad, Dp, err));
-    const int64_t q0 = qb0 * kTM;
-    const int64_t rows = std::min<int64_t>((int64_t)nb * kTM, m - q0);
-    if (rows > 0) {
-      const int blocks = ceil_div(rows * 32, 256);
-      switch (S) {
-        case 1: FMGP_LAUNCH(select_kernel<1><<<blocks, 256, 0, s>>>(Dp, n_pad, q0, rows, n, L, self, cand, dL)); break;
-        case 2: FMGP_LAUNCH(select_kernel<2><<<blocks, 256, 0, s>>>(Dp, n_pad, q0, rows, n, L, self, cand, dL)); break;
-        case 3: FMGP_LAUNCH(select_kernel<3><<<blocks, 256, 0, s>>>(Dp, n_pad, q0, rows, n, L, self, cand, dL)); break;
-        default: FMGP_LAUNCH(select_kernel<4><<<blocks, 256, 0, s>>>(Dp, n_pad, q0, rows, n, L, self, cand, dL)); break;
-      }
+  FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel, kTcSmem));
+  const int64_t ldc = (int64_t)chunk_tiles * kTN;
+  const int sblocks = ceil_div(m * 32, 256);
+  for (int t0 = 0; t0 < n_tiles; t0 += chunk_tiles) {
+    const int t1 = std::min(n_tiles, t0 + chunk_tiles);
+    FMGP_LAUNCH(tc_dist_kernel<<<dim3((unsigned)qblocks, (unsigned)ysplit), kTcThreads, kTcSmem, s>>>(
+        tmQ, tmX, qn2, xn2, t0, t1, tpc, k_chunks, ldc, Dc, err));
+    const int64_t col0 = (int64_t)t0 * kTN, ncols = (int64_t)(t1 - t0) * kTN;
+    const int first = t0 == 0 ? 1 : 0;
+    switch (S) {
+      case 1: FMGP_LAUNCH(select_merge_kernel<1><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+      case 2: FMGP_LAUNCH(select_merge_kernel<2><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+      case 3: FMGP_LAUNCH(select_merge_kernel<3><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+      default: FMGP_LAUNCH(select_merge_kernel<4><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
     }
   }
   FMGP_CUDA_TRY(cudaGetLastError());
-  const int blocks = ceil_div(m * 32, 256);
-  const int KS = (kq + 31) / 32;
-  switch (KS) {
-    case 1: FMGP_LAUNCH((rerank_kernel<T, 1><<<blocks, 256, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, qst, err, idx_out, key_out, fb_list, fb_count))); break;
-    case 2: FMGP_LAUNCH((rerank_kernel<T, 2><<<blocks, 256, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, qst, err, idx_out, key_out, fb_list, fb_count))); break;
-    case 3: FMGP_LAUNCH((rerank_kernel<T, 3><<<blocks, 256, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, qst, err, idx_out, key_out, fb_list, fb_count))); break;
-    default: FMGP_LAUNCH((rerank_kernel<T, 4><<<blocks, 256, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, qst, err, idx_out, key_out, fb_list, fb_count))); break;
+  switch (S) {
+    case 1: rc = launch_rerank<T, 1>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 2: rc = launch_rerank<T, 2>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 3: rc = launch_rerank<T, 3>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    default: rc = launch_rerank<T, 4>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
   }
+  if (rc) return rc;
   FMGP_CUDA_TRY(cudaGetLastError());
   diag_record_tc(fb_count, s);
   // exhaustive exact scan for uncertified queries

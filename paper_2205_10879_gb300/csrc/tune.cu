@@ -1,0 +1,167 @@
+// Autotuner: times candidate launch shapes on the caller's own data and
+// caches the fastest per problem key.  Only speed depends on the choice:
+// every shape computes identical results.
+//   block kernels (precompute / LOOCV): warps per CTA, key (precision, k, d, r, dtype)
+//   grid kNN (d <= 3): mean points per cell, key (d, kq)
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+#include "block.cuh"
+#include "knn.cuh"
+
+namespace fmgp {
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_warps;
+std::map<std::tuple<int, int>, double> g_grid;
+
+}  // namespace
+
+int tuned_block_warps(int prec, int k, int d, int r, int dtype) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_warps.find({prec, k, d, r, dtype});
+  return it == g_warps.end() ? 0 : it->second;
+}
+
+double grid_target_for(int d, int kq) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_grid.find({d, kq});
+    if (it != g_grid.end()) return it->second;
+  }
+  return tune_params().grid_target;
+}
+
+}  // namespace fmgp
+
+using namespace fmgp;
+
+namespace {
+
+// Mean of `reps` timed calls of f() on stream s (after one untimed call).
+template <typename F>
+int time_ms(cudaStream_t s, int reps, F&& f, float* out) {
+  int rc = f();
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  FMGP_CUDA_TRY(cudaEventCreate(&e0));
+  FMGP_CUDA_TRY(cudaEventCreate(&e1));
+  FMGP_CUDA_TRY(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps && !rc; ++i) rc = f();
+  FMGP_CUDA_TRY(cudaEventRecord(e1, s));
+  FMGP_CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *out = ms / reps;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const double* Y,
+                                        int64_t n, int32_t d, int32_t r, const int32_t* nbr,
+                                        int32_t nbr_ld, int32_t k, const fmgp_kernel* kernel,
+                                        fmgp_precision precision, int64_t sample_rows,
+                                        int32_t* warps_out, void* stream) {
+  if (!X || !Y || !nbr || !kernel || !warps_out) {
+    set_error("X, Y, nbr, kernel and warps_out are required");
+    return FMGP_EINVAL;
+  }
+  if (n < 1 || d < 1 || r < 1 || k < 1 || k > n || k > kMaxK || nbr_ld < k - 1 ||
+      sample_rows < 1 || (precision != FMGP_PREC_FP64 && precision != FMGP_PREC_MIXED) ||
+      (dtype != FMGP_F32 && dtype != FMGP_F64)) {
+    set_error("autotune: arguments out of range");
+    return FMGP_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  const int64_t cnt = sample_rows < n ? sample_rows : n;
+  void* Ctmp = ws.alloc((size_t)cnt * k * r * 8);
+  int* fails = ws.get<int>(1);
+  if (!Ctmp || !fails) return FMGP_ENOMEM;
+  BlockArgs a{};
+  a.Y = Y;
+  a.nbr = nbr;
+  a.C = Ctmp;
+  a.fail_count = fails;
+  a.n = n;
+  a.count = cnt;
+  a.d = d;
+  a.r = r;
+  a.ld = nbr_ld;
+  a.k = k;
+  a.kp = make_kparams(*kernel);
+  a.layout = block_layout(k, d, r, dtype == FMGP_F64 ? 8 : 4, false);
+  const size_t bytes = precision == FMGP_PREC_FP64 ? a.layout.bytes_per_warp
+                                                   : mixed_bytes_per_warp(k, d, r);
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int w : {1, 2, 4, 6, 8}) {
+    if ((size_t)w * bytes > 200 * 1024) continue;
+    float ms = 0.f;
+    int rc = time_ms(s, 2, [&]() {
+      Workspace inner(s);
+      return precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, false, w, s)
+                                         : run_block_mixed(a, X, dtype, false, w, *kernel, inner, s);
+    }, &ms);
+    if (rc) return rc;
+    if (ms < best_ms) { best_ms = ms; best = w; }
+  }
+  if (!best) {
+    set_error("autotune: no feasible warps-per-CTA for k=%d d=%d r=%d", k, d, r);
+    return FMGP_EUNSUPPORTED;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_warps[{(int)precision, k, d, r, (int)dtype}] = best;
+  }
+  *warps_out = best;
+  return FMGP_OK;
+}
+
+extern "C" int fmgp_autotune_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
+                                 double* grid_target_out, void* stream) {
+  if (!X || !grid_target_out || n < 2 || d < 1 || kq < 1 || kq > n - 1 || kq > kMaxK ||
+      (dtype != FMGP_F32 && dtype != FMGP_F64)) {
+    set_error("autotune: arguments out of range");
+    return FMGP_EINVAL;
+  }
+  if (d > kGridMaxD) {
+    *grid_target_out = 0.0;  // nothing to tune: exhaustive / tensor-core search
+    return FMGP_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  int32_t* nbr = ws.get<int32_t>((size_t)n * kq);
+  if (!nbr) return FMGP_ENOMEM;
+  double best = 0.0;
+  float best_ms = 1e30f;
+  for (double t : {4.0, 6.0, 8.0, 12.0, 16.0, 24.0, 32.0}) {
+    TuneParams tp = tune_params();
+    tp.grid_target = t;
+    float ms = 0.f;
+    int rc = time_ms(s, 2, [&]() {
+      Workspace inner(s);
+      return knn_self(X, dtype, n, d, kq, nbr, nullptr, tp, inner, s);
+    }, &ms);
+    if (rc) return rc;
+    if (ms < best_ms) { best_ms = ms; best = t; }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_grid[{(int)d, (int)kq}] = best;
+  }
+  *grid_target_out = best;
+  return FMGP_OK;
+}
+
+extern "C" int fmgp_autotune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_warps.clear();
+  g_grid.clear();
+  return FMGP_OK;
+}
