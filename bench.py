@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--k", type=int, default=50)
     p.add_argument("--b", type=int, default=10_000)
     p.add_argument("--nu", type=float, default=1.5)
-    p.add_argument("--workload", default="spatial", choices=["spatial", "highdim-knn"])
+    p.add_argument("--workload", default="spatial", choices=["spatial", "large", "highdim-knn"])
+    p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-highdim", action="store_true")
     return p.parse_args()
 
@@ -63,9 +64,20 @@ def dist_env():
 
 
 def workload_config(a):
+    if a.workload == "large":
+        return {"workload": "large-3d", "n_train": 10_000_000, "m_test": 1_000_000, "d": 3,
+                "k": 64, "r": 1, "kernel": "matern nu=2.5 rho=0.1 tau2=1e-5", "loocv_batch": 10_000,
+                "l2": "inputs larger than L2 (129 MB)"}
     return {"workload": "spatial-2d", "n_train": a.n, "m_test": a.m, "d": 2, "k": a.k,
             "r": 1, "kernel": f"matern nu={a.nu} rho=0.1 tau2=1e-3", "loocv_batch": a.b,
             "l2": "flushed between steps (512 MB write)"}
+
+
+def make_workload(a):
+    from paper_2205_10879_gb300 import workloads as wl
+    if a.workload == "large":
+        return wl.large()
+    return wl.spatial(n=a.n, m=a.m, k=a.k, nu=a.nu, b=a.b)
 
 
 # ----------------------------------------------------------------- flops --
@@ -143,7 +155,7 @@ def run_ours(a):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     fb.load()
-    W = wl.spatial(n=a.n, m=a.m, k=a.k, nu=a.nu, b=a.b)
+    W = make_workload(a)
     s = W.kernel
     gk = fb.make_kernel(s.kind, s.nu, s.length_scale, s.variance, s.nugget)
     k, kq = W.k, W.k  # one table serves precompute (k-1 columns) and LOOCV (k columns)
@@ -225,7 +237,7 @@ def run_ours(a):
     out = {}
     # the plain FP64 path on the same workload, for the "vs FP64 plain" comparison
     fp64 = None
-    if prec != fb.PREC_FP64:
+    if prec != fb.PREC_FP64 and not a.no_fp64:
         C64 = torch.empty((n, k, 1), dtype=torch.float64, device=dev)
         ph64, _ = timed(fb.PREC_FP64, C64, max(2, a.steps // 2), 1)
         y64 = yh.cpu().numpy().copy()
@@ -237,7 +249,7 @@ def run_ours(a):
                 "rel_rms_vs_fp64": float(np.linalg.norm(yh_main - y64) / np.linalg.norm(y64))}
         del C64
     # roofline of the dominant kernel (the precompute block kernel: one launch per step)
-    fl = precompute_flops_per_point(k, 2, 1) * n
+    fl = precompute_flops_per_point(k, W.d, 1) * n
     pre_s = phase_ms[1] * 1e-3
     if prec == fb.PREC_FP64:
         peak = 152 * 4 * 2070e6 / 1e12  # FP64: 2 DFMA/clk/SM
@@ -310,7 +322,8 @@ def run_ours(a):
     if not a.no_serving:
         line["serving"] = serving_bench(a, dev)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(W, a, samples=(20000, 20000, 5000))
+        samples = (2000, 2000, 1000) if a.workload == "large" else (20000, 20000, 5000)
+        line["cpu_baseline"] = oracle_sample(W, a, samples=samples)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -442,10 +455,11 @@ def run_reference(a):
     if rank != 0:
         return
     from paper_2205_10879_gb300 import workloads as wl
-    W = wl.spatial(n=a.n, m=a.m, k=a.k, nu=a.nu, b=a.b)
+    W = make_workload(a)
     res = []
     for i in range(a.warmup + a.steps):
-        r = oracle_sample(W, a, samples=(5000, 5000, 1000))
+        r = oracle_sample(W, a, samples=(500, 500, 200) if a.workload == "large"
+                          else (5000, 5000, 1000))
         if i >= a.warmup:
             res.append(r)
     v = float(np.mean([r["value"] for r in res]))

@@ -141,60 +141,6 @@ MixedLayout mixed_layout(int k, int d, int r) {
   return l;
 }
 
-// Sum_{p<j} a0[p] b[p] and Sum_{p<j} a1[p] b[p] over 16-byte aligned rows
-// (b read once for both), eight independent accumulators.
-__device__ __forceinline__ void row_dot2(const float* a0, const float* a1, const float* b, int j,
-                                         bool use1, float& out0, float& out1) {
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-  const int j4 = j & ~3;
-  if (use1) {
-    int p = 0;
-    for (; p + 8 <= j4; p += 8) {
-      const float4 y = *reinterpret_cast<const float4*>(b + p);
-      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
-      const float4 z = *reinterpret_cast<const float4*>(a1 + p);
-      const float4 y2 = *reinterpret_cast<const float4*>(b + p + 4);
-      const float4 x2 = *reinterpret_cast<const float4*>(a0 + p + 4);
-      const float4 z2 = *reinterpret_cast<const float4*>(a1 + p + 4);
-      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
-      t0 = fmaf(z.x, y.x, t0); t1 = fmaf(z.y, y.y, t1); t2 = fmaf(z.z, y.z, t2); t3 = fmaf(z.w, y.w, t3);
-      s0 = fmaf(x2.x, y2.x, s0); s1 = fmaf(x2.y, y2.y, s1); s2 = fmaf(x2.z, y2.z, s2); s3 = fmaf(x2.w, y2.w, s3);
-      t0 = fmaf(z2.x, y2.x, t0); t1 = fmaf(z2.y, y2.y, t1); t2 = fmaf(z2.z, y2.z, t2); t3 = fmaf(z2.w, y2.w, t3);
-    }
-    for (; p < j4; p += 4) {
-      const float4 y = *reinterpret_cast<const float4*>(b + p);
-      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
-      const float4 z = *reinterpret_cast<const float4*>(a1 + p);
-      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
-      t0 = fmaf(z.x, y.x, t0); t1 = fmaf(z.y, y.y, t1); t2 = fmaf(z.z, y.z, t2); t3 = fmaf(z.w, y.w, t3);
-    }
-    for (int p = j4; p < j; ++p) {
-      s0 = fmaf(a0[p], b[p], s0);
-      t0 = fmaf(a1[p], b[p], t0);
-    }
-  } else {
-    int p = 0;
-    for (; p + 8 <= j4; p += 8) {
-      const float4 y = *reinterpret_cast<const float4*>(b + p);
-      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
-      const float4 y2 = *reinterpret_cast<const float4*>(b + p + 4);
-      const float4 x2 = *reinterpret_cast<const float4*>(a0 + p + 4);
-      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
-      t0 = fmaf(x2.x, y2.x, t0); t1 = fmaf(x2.y, y2.y, t1); t2 = fmaf(x2.z, y2.z, t2); t3 = fmaf(x2.w, y2.w, t3);
-    }
-    for (; p < j4; p += 4) {
-      const float4 y = *reinterpret_cast<const float4*>(b + p);
-      const float4 x = *reinterpret_cast<const float4*>(a0 + p);
-      s0 = fmaf(x.x, y.x, s0); s1 = fmaf(x.y, y.y, s1); s2 = fmaf(x.z, y.z, s2); s3 = fmaf(x.w, y.w, s3);
-    }
-    for (int p = j4; p < j; ++p) s0 = fmaf(a0[p], b[p], s0);
-    s0 += (t0 + t1) + (t2 + t3);
-    t0 = t1 = t2 = t3 = 0.f;
-  }
-  out0 = (s0 + s1) + (s2 + s3);
-  out1 = (t0 + t1) + (t2 + t3);
-}
-
 // L y = b then L^T x = y for column c of R (k x r), L the lower triangle of
 // M (stride ldl) with inverse diagonal invd.  Rows are taken 32 at a time,
 // lane = row within the block: contributions of finished blocks are
@@ -351,40 +297,93 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
     }
     for (int a = lane; a < k; a += 32) M[a * ldl + a] = kp.diag.hi;
     __syncwarp();
-    // FP32 Cholesky (Crout order), lower triangle of M.  Rows r0 = lane and
-    // r1 = lane + 32 share one pass over row j; rows 64.. (k > 64) follow.
-    // The pivot's reciprocal square root is broadcast by shuffle.
+    // FP32 Cholesky of the lower triangle of M, left-looking in blocks of four
+    // columns: the dot products of every row with the block's four columns
+    // over the finished prefix are formed in one pass (each row chunk read
+    // once for four columns), then the 4-column panel is factored in Crout
+    // order with pivots broadcast by shuffle.  Lane l owns rows l, l+32, ...
     bool fail = false;
-    for (int j = 0; j < k; ++j) {
-      const float* mj = M + j * ldl;
-      const int r0 = lane, r1 = lane + 32, r2 = lane + 64, r3 = lane + 96;
-      const bool a0 = r0 >= j && r0 < k, a1 = r1 >= j && r1 < k;
-      float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, d3 = 0.0f;
-      if (a0 || a1) row_dot2(M + (a0 ? r0 : r1) * ldl, M + r1 * ldl, mj, j, a0 && a1, d0, d1);
-      if (!a0) { d1 = d0; d0 = 0.0f; }
-      if (k > 64) {
-        const bool a2 = r2 >= j && r2 < k, a3 = r3 >= j && r3 < k;
-        if (a2 || a3) row_dot2(M + (a2 ? r2 : r3) * ldl, M + r3 * ldl, mj, j, a2 && a3, d2, d3);
-        if (!a2) { d3 = d2; d2 = 0.0f; }
+    for (int j0 = 0; j0 < k; j0 += 4) {
+      const int nb = min(4, k - j0);
+      float acc[kMaxSlots][4];
+      bool act[kMaxSlots];
+#pragma unroll
+      for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+        const int r = lane + 32 * s4;
+        act[s4] = (s4 == 0 || k > 32 * s4) && r >= j0 && r < k;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          acc[s4][c] = (act[s4] && c < nb && j0 + c <= r) ? M[r * ldl + j0 + c] : 0.0f;
       }
-      float inv = 0.0f;
-      if (lane == (j & 31)) {
-        const int sj = j >> 5;
-        const float dj = sj == 0 ? d0 : (sj == 1 ? d1 : (sj == 2 ? d2 : d3));
-        const float v = M[j * ldl + j] - dj;
-        if (v > 0.0f) {
-          inv = rsqrtf(v);
-          M[j * ldl + j] = v * inv;
-          invd[j] = inv;
+      for (int p = 0; p < j0; p += 4) {
+        float4 bc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          bc[c] = c < nb ? *reinterpret_cast<const float4*>(M + (j0 + c) * ldl + p)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+          if (!act[s4]) continue;
+          const float4 a4 = *reinterpret_cast<const float4*>(M + (lane + 32 * s4) * ldl + p);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float t = acc[s4][c];
+            t = fmaf(-a4.x, bc[c].x, t);
+            t = fmaf(-a4.y, bc[c].y, t);
+            t = fmaf(-a4.z, bc[c].z, t);
+            t = fmaf(-a4.w, bc[c].w, t);
+            acc[s4][c] = t;
+          }
         }
       }
-      inv = __shfl_sync(kFull, inv, j & 31);
-      if (!(inv > 0.0f)) { fail = true; break; }
-      if (r0 > j && r0 < k) M[r0 * ldl + j] = (M[r0 * ldl + j] - d0) * inv;
-      if (r1 > j && r1 < k) M[r1 * ldl + j] = (M[r1 * ldl + j] - d1) * inv;
-      if (r2 > j && r2 < k) M[r2 * ldl + j] = (M[r2 * ldl + j] - d2) * inv;
-      if (r3 > j && r3 < k) M[r3 * ldl + j] = (M[r3 * ldl + j] - d3) * inv;
+      // panel: columns j0 .. j0+nb-1 in order
+      float lr[kMaxSlots][4];
+#pragma unroll
+      for (int s4 = 0; s4 < kMaxSlots; ++s4)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) lr[s4][c] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c >= nb) break;
+        const int col = j0 + c;
+        const int owner = col & 31, os = col >> 5;
+        // the pivot row's finished entries L[col][j0 .. col-1] and its reduced diagonal
+        float lc[4], dv = 0.0f;
+#pragma unroll
+        for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+          if (s4 == os) {
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) lc[c2] = __shfl_sync(kFull, lr[s4][c2], owner);
+            dv = __shfl_sync(kFull, acc[s4][c], owner);
+          }
+        }
+#pragma unroll
+        for (int c2 = 0; c2 < 4; ++c2)
+          if (c2 < c) dv = fmaf(-lc[c2], lc[c2], dv);
+        if (!(dv > 0.0f)) { fail = true; break; }
+        const float inv = rsqrtf(dv);
+        if (lane == owner) {
+          M[col * ldl + col] = dv * inv;
+          invd[col] = inv;
+        }
+#pragma unroll
+        for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+          const int r = lane + 32 * s4;
+          if (act[s4] && r > col) {
+            float t = acc[s4][c];
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2)
+              if (c2 < c) t = fmaf(-lr[s4][c2], lc[c2], t);
+            t *= inv;
+            lr[s4][c] = t;
+            M[r * ldl + col] = t;
+          } else if (act[s4] && r == col) {
+            lr[s4][c] = dv * inv;
+          }
+        }
+      }
       __syncwarp();
+      if (fail) break;
     }
     if (lane == 0) *flag = fail ? 1 : 0;
     __syncwarp();
