@@ -13,6 +13,37 @@ namespace {
 constexpr float kU = 5.9604645e-8f;  // 2^-24
 
 // ---------------------------------------------------------------- grid ----
+// Initial distance threshold from the local density: the number of points in
+// the 3^D block of cells around the query, over the block's volume, gives the
+// radius expected to hold ~1.6 kq points.  It only prunes: if the search ends
+// with fewer than kq points inside it, or with a k-th key above it, the query
+// is searched again without it, so the result never depends on the guess.
+template <int D>
+__device__ __forceinline__ float density_threshold(const GridView& gv, const GridGeom& g,
+                                                   const int* cq, int kq) {
+  int cnt = 0;
+  float vol = 1.f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const int lo = max(cq[j] - 1, 0), hi = min(cq[j] + 1, g.G - 1);
+    vol *= (float)(hi - lo + 1) * g.w[j];
+  }
+  const int lo0 = max(cq[0] - 1, 0), hi0 = min(cq[0] + 1, g.G - 1);
+  const int lo1 = D > 1 ? max(cq[D > 1 ? 1 : 0] - 1, 0) : 0;
+  const int hi1 = D > 1 ? min(cq[D > 1 ? 1 : 0] + 1, g.G - 1) : 0;
+  const int lo2 = D > 2 ? max(cq[D > 2 ? 2 : 0] - 1, 0) : 0;
+  const int hi2 = D > 2 ? min(cq[D > 2 ? 2 : 0] + 1, g.G - 1) : 0;
+  for (int c2 = lo2; c2 <= hi2; ++c2)
+    for (int c1 = lo1; c1 <= hi1; ++c1)
+      cnt += gv.cell_start[cell_linear(hi0, c1, c2, g.G, D) + 1] -
+             gv.cell_start[cell_linear(lo0, c1, c2, g.G, D)];
+  if (cnt < 2 || !(vol > 0.f)) return __int_as_float(0x7f800000);
+  const float unit = D == 1 ? 2.f : (D == 2 ? 3.14159265f : 4.18879020f);
+  const float rD = 1.6f * (float)kq * vol / ((float)cnt * unit);  // r^D
+  const float r = D == 1 ? rD : (D == 2 ? sqrtf(rD) : cbrtf(rD));
+  return r * r;
+}
+
 template <int D, int L>
 __global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
                                                             int32_t* nbr_out, double* dist_out) {
@@ -34,33 +65,45 @@ __global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
   int cq[3] = {0, 0, 0};
   cell_of<D>(g, qf, cq);
   WarpTopK<L> top;
-  top.init(kq);
-  for (int r = 0;; ++r) {
-    for_ring_segments<D>(r, cq, g.G, [&](int c0a, int c0b, int c1, int c2) {
-      if (top.full() && box_lower<D>(g, qf, margin, c0a, c0b, c1, c2) > top.t_up) return;
-      const int s0 = gv.cell_start[cell_linear(c0a, c1, c2, g.G, D)];
-      const int e0 = gv.cell_start[cell_linear(c0b, c1, c2, g.G, D) + 1];
-      for (int base = s0; base < e0; base += 32) {
-        const int j = base + lane;
-        unsigned long long ck = ~0ull;
-        int ci = INT_MAX;
-        if (j < e0) {
-          const int id = gv.ids[j];
-          if (id != qi) {
-            float xf[D];
+  float pre = density_threshold<D>(gv, g, cq, kq);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    top.init(kq);
+    for (int r = 0;; ++r) {
+      for_ring_segments<D>(r, cq, g.G, [&](int c0a, int c0b, int c1, int c2) {
+        const float lim = fminf(top.t_up, pre);
+        if (lim < __int_as_float(0x7f800000) && box_lower<D>(g, qf, margin, c0a, c0b, c1, c2) > lim)
+          return;
+        const int s0 = gv.cell_start[cell_linear(c0a, c1, c2, g.G, D)];
+        const int e0 = gv.cell_start[cell_linear(c0b, c1, c2, g.G, D) + 1];
+        for (int base = s0; base < e0; base += 32) {
+          const int j = base + lane;
+          unsigned long long ck = ~0ull;
+          int ci = INT_MAX;
+          if (j < e0) {
+            const int id = gv.ids[j];
+            if (id != qi) {
+              float xf[D];
 #pragma unroll
-            for (int t = 0; t < D; ++t) xf[t] = gv.xs32[(int64_t)j * D + t];
-            if (dist_lower_f32<D>(qf, xf, cerr) <= top.t_up) {
-              ck = dbits(canon_key<double>(q64, gv.xs64 + (int64_t)j * D, D));
-              ci = id;
+              for (int t = 0; t < D; ++t) xf[t] = gv.xs32[(int64_t)j * D + t];
+              if (dist_lower_f32<D>(qf, xf, cerr) <= fminf(top.t_up, pre)) {
+                ck = dbits(canon_key<double>(q64, gv.xs64 + (int64_t)j * D, D));
+                ci = id;
+              }
             }
           }
+          top.offer(ck, ci, lane);
         }
-        top.offer(ck, ci, lane);
-      }
-    });
-    if (top.full() && outside_lower<D>(g, qf, margin, cq, r) > top.t_up) break;
-    if (r >= g.G) break;
+      });
+      const float out = outside_lower<D>(g, qf, margin, cq, r);
+      if (top.full() && out > top.t_up) break;
+      if (out > pre) break;  // nothing outside can pass the threshold
+      if (r >= g.G) break;
+    }
+    // exact iff the kq-th key does not exceed the threshold (every skipped
+    // candidate has key > pre); otherwise search again without it
+    if (top.full() && top.t_up <= pre) break;
+    if (pre == __int_as_float(0x7f800000)) break;
+    pre = __int_as_float(0x7f800000);
   }
   top.store(kq, lane, nbr_out + (int64_t)qi * kq, dist_out ? dist_out + (int64_t)qi * kq : nullptr);
 }
