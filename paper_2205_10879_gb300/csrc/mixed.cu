@@ -16,6 +16,7 @@
 // cross-covariance and the dot product with C in DF.
 #include <math.h>
 #include <mutex>
+#include <type_traits>
 #include "block.cuh"
 #include "df.cuh"
 #include "predict.cuh"
@@ -226,7 +227,7 @@ __device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* 
   }
 }
 
-template <bool LOO>
+template <bool LOO, int NS, int CB>
 __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
                                                           MixedLayout lay) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -303,30 +304,30 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
     // once for four columns), then the 4-column panel is factored in Crout
     // order with pivots broadcast by shuffle.  Lane l owns rows l, l+32, ...
     bool fail = false;
-    for (int j0 = 0; j0 < k; j0 += 4) {
-      const int nb = min(4, k - j0);
-      float acc[kMaxSlots][4];
-      bool act[kMaxSlots];
+    for (int j0 = 0; j0 < k; j0 += CB) {
+      const int nb = min(CB, k - j0);
+      float acc[NS][CB];
+      bool act[NS];
 #pragma unroll
-      for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+      for (int s4 = 0; s4 < NS; ++s4) {
         const int r = lane + 32 * s4;
-        act[s4] = (s4 == 0 || k > 32 * s4) && r >= j0 && r < k;
+        act[s4] = r >= j0 && r < k;
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < CB; ++c)
           acc[s4][c] = (act[s4] && c < nb && j0 + c <= r) ? M[r * ldl + j0 + c] : 0.0f;
       }
       for (int p = 0; p < j0; p += 4) {
-        float4 bc[4];
+        float4 bc[CB];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < CB; ++c)
           bc[c] = c < nb ? *reinterpret_cast<const float4*>(M + (j0 + c) * ldl + p)
                          : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+        for (int s4 = 0; s4 < NS; ++s4) {
           if (!act[s4]) continue;
           const float4 a4 = *reinterpret_cast<const float4*>(M + (lane + 32 * s4) * ldl + p);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < CB; ++c) {
             float t = acc[s4][c];
             t = fmaf(-a4.x, bc[c].x, t);
             t = fmaf(-a4.y, bc[c].y, t);
@@ -337,28 +338,28 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
         }
       }
       // panel: columns j0 .. j0+nb-1 in order
-      float lr[kMaxSlots][4];
+      float lr[NS][CB];
 #pragma unroll
-      for (int s4 = 0; s4 < kMaxSlots; ++s4)
+      for (int s4 = 0; s4 < NS; ++s4)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) lr[s4][c] = 0.0f;
+        for (int c = 0; c < CB; ++c) lr[s4][c] = 0.0f;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < CB; ++c) {
         if (c >= nb) break;
         const int col = j0 + c;
         const int owner = col & 31, os = col >> 5;
         // the pivot row's finished entries L[col][j0 .. col-1] and its reduced diagonal
-        float lc[4], dv = 0.0f;
+        float lc[CB], dv = 0.0f;
 #pragma unroll
-        for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+        for (int s4 = 0; s4 < NS; ++s4) {
           if (s4 == os) {
 #pragma unroll
-            for (int c2 = 0; c2 < 4; ++c2) lc[c2] = __shfl_sync(kFull, lr[s4][c2], owner);
+            for (int c2 = 0; c2 < CB; ++c2) lc[c2] = __shfl_sync(kFull, lr[s4][c2], owner);
             dv = __shfl_sync(kFull, acc[s4][c], owner);
           }
         }
 #pragma unroll
-        for (int c2 = 0; c2 < 4; ++c2)
+        for (int c2 = 0; c2 < CB; ++c2)
           if (c2 < c) dv = fmaf(-lc[c2], lc[c2], dv);
         if (!(dv > 0.0f)) { fail = true; break; }
         const float inv = rsqrtf(dv);
@@ -367,12 +368,12 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
           invd[col] = inv;
         }
 #pragma unroll
-        for (int s4 = 0; s4 < kMaxSlots; ++s4) {
+        for (int s4 = 0; s4 < NS; ++s4) {
           const int r = lane + 32 * s4;
           if (act[s4] && r > col) {
             float t = acc[s4][c];
 #pragma unroll
-            for (int c2 = 0; c2 < 4; ++c2)
+            for (int c2 = 0; c2 < CB; ++c2)
               if (c2 < c) t = fmaf(-lr[s4][c2], lc[c2], t);
             t *= inv;
             lr[s4][c] = t;
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
       for (int step = 1; step <= kMaxRefine; ++step) {
         // residual y - K x in DF; lane owns rows; K_ab = (upper hi, packed lo)
 #pragma unroll
-        for (int s = 0; s < kMaxSlots; ++s) {
+        for (int s = 0; s < NS; ++s) {
           const int row = lane + 32 * s;
           if (row < k) {
             const int rb = row * (row - 1) / 2;
@@ -456,10 +457,10 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
       if (args.status && lane == 0) args.status[i] = FMGP_BLOCK_OK;
     } else {
       // leave-one-out residual of x_i from its k neighbours, in DF
-      dfl kx[kMaxSlots];
+      dfl kx[NS];
       const float2* xi = mx.Xdf + i * d;
 #pragma unroll
-      for (int s = 0; s < kMaxSlots; ++s) {
+      for (int s = 0; s < NS; ++s) {
         const int a = lane + 32 * s;
         kx[s] = dfl{0.0f, 0.0f};
         if (a < k) kx[s] = corr_df(kp, sqdist_df(xi, XS + a * d, d), mx.K);
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
       for (int c = 0; c < r; ++c) {
         dfl acc = {0.0f, 0.0f};
 #pragma unroll
-        for (int s = 0; s < kMaxSlots; ++s) {
+        for (int s = 0; s < NS; ++s) {
           const int a = lane + 32 * s;
           if (a < k) acc = df_add(acc, df_mul(kx[s], XV[a * r + c]));
         }
@@ -579,7 +580,17 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int 
   const size_t smem = lay.bytes * warps;
   const int64_t need = (a.count + warps - 1) / warps;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
-  auto kern_fn = loo ? block_mixed_kernel<true> : block_mixed_kernel<false>;
+  // rows per lane (k <= 32 S) and Cholesky block width are compile-time
+  auto pick = [&](auto sconst) {
+    constexpr int SS = decltype(sconst)::value;
+    constexpr int CB = SS <= 2 ? 8 : 4;
+    return loo ? block_mixed_kernel<true, SS, CB> : block_mixed_kernel<false, SS, CB>;
+  };
+  const int S = (a.k + 31) / 32;
+  auto kern_fn = S == 1 ? pick(std::integral_constant<int, 1>{})
+               : S == 2 ? pick(std::integral_constant<int, 2>{})
+               : S == 3 ? pick(std::integral_constant<int, 3>{})
+                        : pick(std::integral_constant<int, 4>{});
   FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
   FMGP_LAUNCH(kern_fn<<<blocks, warps * 32, smem, s>>>(a, mx, lay));
   FMGP_CUDA_TRY(cudaGetLastError());
