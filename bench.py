@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--nu", type=float, default=1.5)
     p.add_argument("--workload", default="spatial", choices=["spatial", "large", "highdim-knn"])
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-muygps", action="store_true")
     p.add_argument("--no-highdim", action="store_true")
     return p.parse_args()
 
@@ -248,6 +249,27 @@ def run_ours(a):
                 "rmse": float(np.sqrt(np.mean((y64 - W.Ztrue) ** 2))),
                 "rel_rms_vs_fp64": float(np.linalg.norm(yh_main - y64) / np.linalg.norm(y64))}
         del C64
+    # the paper's comparator on the same test points: plain MuyGPs prediction
+    # (each test point's own k neighbours and one Cholesky per test point)
+    muy = None
+    if not a.no_muygps:
+        ymu = torch.empty((m, 1), dtype=torch.float64, device=dev)
+        fb.fmgp_muygps_predict(X, Y, Z, k, gk, prec, Yhat_out=ymu)
+        torch.cuda.synchronize()
+        tm = []
+        for _ in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fb.fmgp_muygps_predict(X, Y, Z, k, gk, prec, Yhat_out=ymu)
+            e1.record()
+            torch.cuda.synchronize()
+            tm.append(e0.elapsed_time(e1))
+        mu_ms = float(np.mean(tm))
+        yv = ymu.cpu().numpy()
+        muy = {"ms": mu_ms, "predictions_per_s": m / (mu_ms * 1e-3),
+               "rmse": float(np.sqrt(np.mean((yv - W.Ztrue) ** 2))),
+               "fastmuygps_speedup_predict": mu_ms / phase_ms[2]}
     # roofline of the dominant kernel (the precompute block kernel: one launch per step)
     fl = precompute_flops_per_point(k, W.d, 1) * n
     pre_s = phase_ms[1] * 1e-3
@@ -313,7 +335,7 @@ def run_ours(a):
         "predictions_per_s": m / (phase_ms[2] * 1e-3),
         "knn_queries_per_s": n / (phase_ms[0] * 1e-3),
         "loocv_pts_per_s": b / (phase_ms[3] * 1e-3),
-        "rmse": rmse, "fp64_path": fp64, "roofline": roof, "e2e": e2e,
+        "rmse": rmse, "fp64_path": fp64, "muygps_predict": muy, "roofline": roof, "e2e": e2e,
         "block_status": {str(v): int(c) for v, c in zip(*np.unique(st_main, return_counts=True))},
         "gpu_launches": launches, "clocks": clocks,
     }

@@ -168,6 +168,23 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
                          fmgp_precision precision, double* Q_out, double* resid_out,
                          void* stream);
 
+/*
+ * fmgp_muygps_predict -- plain MuyGPs prediction (Eq. 8), the method
+ * FastMuyGPs accelerates: every test point z_t uses its OWN k nearest
+ * training points N*_t (canonical key, ties to the lowest index) and one
+ * neighbourhood solve, Yhat[t] = K(z_t, X_N*) K(X_N*, X_N*)^{-1} Y(X_N*)
+ * (nugget on the block diagonal only).  O(k^3) per test point instead of
+ * FastMuyGPs' O(k).
+ *   X n x d, Y n x r (FP64), Z m x d (X's dtype), 1 <= k <= min(n, 128).
+ *   Yhat_out m x r FP64; nbr_out m x k int32 neighbour table or NULL.
+ * A block that is not positive definite yields NaN predictions for its test
+ * point.  Asynchronous on `stream`.
+ */
+int fmgp_muygps_predict(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                        int32_t r, const void* Z, int64_t m, int32_t k, const fmgp_kernel* kernel,
+                        fmgp_precision precision, double* Yhat_out, int32_t* nbr_out,
+                        void* stream);
+
 /* ------------------------------------------------------------------------
  * Resident models and the serving loop (the paper's online phase run as a
  * service: Sec. 1 motivates FastMuyGPs by applications that need many fast

@@ -53,6 +53,8 @@ def _load():
         lib.fmgp_oracle_loocv.restype = I64
         lib.fmgp_oracle_loocv_ld.argtypes = lib.fmgp_oracle_loocv.argtypes
         lib.fmgp_oracle_loocv_ld.restype = I64
+        lib.fmgp_oracle_muygps_predict.argtypes = [P, P, I64, I32, I32, P, I64, I32, KP, P, P]
+        lib.fmgp_oracle_muygps_predict.restype = I64
         lib.fmgp_oracle_set_threads.argtypes = [I32]
         lib.fmgp_oracle_max_threads.restype = I32
         _lib = lib
@@ -226,3 +228,23 @@ def loocv(X, Y, nbr, k, batch, kern, long_double=False):
     if f < 0:
         raise ValueError("oracle loocv: bad arguments")
     return float(Q[0]), res
+
+
+def muygps_predict(X, Y, Z, k, kern):
+    """MuyGPs prediction (Eq. 8): (Yhat m x r, neighbour table m x k) with each
+    test point's own k nearest training points."""
+    X = _c(X, np.float64)
+    Y = _c(Y, np.float64)
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    Z = _c(Z, np.float64).reshape(-1, X.shape[1])
+    n, d = X.shape
+    r = Y.shape[1]
+    m = Z.shape[0]
+    Yh = np.zeros((m, r), np.float64)
+    N = np.zeros((m, k), np.int32)
+    f = _load().fmgp_oracle_muygps_predict(_p(X), _p(Y), n, d, r, _p(Z), m, int(k),
+                                           ctypes.byref(kern), _p(Yh), _p(N))
+    if f < 0:
+        raise ValueError("oracle muygps_predict: bad arguments")
+    return Yh, N

@@ -214,6 +214,22 @@ int fmgp_oracle_fit_predict_ld(const double* X, const double* Y, int64_t n, int 
   return 0;
 }
 
+/* MuyGPs prediction (Eq. 8) with a brute-force kNN of each test point (k
+ * nearest training points, ties to the lowest index).  nbr_out (m x k) may
+ * be NULL.  Returns -1 on bad arguments, else the number of failed blocks. */
+int64_t fmgp_oracle_muygps_predict(const double* X, const double* Y, int64_t n, int d, int r,
+                                   const double* Z, int64_t m, int k,
+                                   const fmgp_oracle_kernel* kp, double* Yhat, int32_t* nbr_out) {
+  if (!kernel_ok(kp) || n < 1 || d < 1 || r < 1 || k < 1 || k > n || m < 0) return -1;
+  if (m == 0) return 0;
+  int32_t* N = (int32_t*)malloc(sizeof(int32_t) * (size_t)m * k);
+  fmgp_oracle_knn(X, n, d, Z, m, k, NULL, N, NULL);
+  int64_t f = predict_muygps_f64(X, Y, d, r, N, k, kp, Z, m, Yhat);
+  if (nbr_out) memcpy(nbr_out, N, sizeof(int32_t) * (size_t)m * k);
+  free(N);
+  return f;
+}
+
 /* Eq. 5 LOOCV objective; returns -1 on bad arguments, else the number of
  * failed blocks.  resid (b) receives the per-point squared residuals. */
 int64_t fmgp_oracle_loocv(const double* X, const double* Y, int64_t n, int d, int r,

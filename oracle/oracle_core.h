@@ -204,3 +204,36 @@ static int64_t FN(loocv)(const double* X, const double* Y, int64_t n, int d, int
   *Q = s / (REAL)b;
   return failed;
 }
+
+/* MuyGPs prediction (Eq. 8): each test point z_t is predicted from its OWN k
+ * nearest training points N*_t (rows of Nz, ascending by key):
+ * yhat_t = K(z_t, X_N*) K(X_N*, X_N*)^{-1} Y(X_N*), one Cholesky per test
+ * point.  Returns the number of blocks whose Cholesky failed (their yhat is NaN). */
+static int64_t FN(predict_muygps)(const double* X, const double* Y, int d, int r,
+                                  const int32_t* Nz, int k, const fmgp_oracle_kernel* kp,
+                                  const double* Z, int64_t m, REAL* Yhat) {
+  int64_t failed = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : failed)
+  for (int64_t t = 0; t < m; ++t) {
+    const int32_t* N = Nz + t * k;
+    REAL* K = (REAL*)malloc(sizeof(REAL) * k * k);
+    REAL* w = (REAL*)malloc(sizeof(REAL) * k * r);
+    FN(assemble)(X, d, N, k, kp, K);
+    if (FN(cholesky)(K, k)) {
+      for (int c = 0; c < r; ++c) Yhat[t * r + c] = NAN;
+      failed += 1;
+    } else {
+      for (int a = 0; a < k; ++a)
+        for (int c = 0; c < r; ++c) w[a * r + c] = (REAL)Y[(int64_t)N[a] * r + c];
+      FN(chol_solve)(K, k, w, r);
+      for (int c = 0; c < r; ++c) Yhat[t * r + c] = 0;
+      for (int a = 0; a < k; ++a) {
+        REAL kz = (REAL)kp->variance * FN(phi)(kp, FN(sqdist)(Z + t * d, X + (int64_t)N[a] * d, d));
+        for (int c = 0; c < r; ++c) Yhat[t * r + c] = Yhat[t * r + c] + kz * w[a * r + c];
+      }
+    }
+    free(K);
+    free(w);
+  }
+  return failed;
+}

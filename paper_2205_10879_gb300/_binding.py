@@ -79,6 +79,8 @@ def load(build_if_missing=True):
     lib.fmgp_last_error.restype = ctypes.c_char_p
     lib.fmgp_version.restype = ctypes.c_char_p
     lib.fmgp_kernel_launches.restype = ctypes.c_uint64
+    lib.fmgp_muygps_predict.argtypes = [P, I32, P, I64, I32, I32, P, I64, I32, KP, I32, P, P, P]
+    lib.fmgp_muygps_predict.restype = I32
     lib.fmgp_tune_set.argtypes = [ctypes.c_char_p, ctypes.c_double]
     lib.fmgp_tune_set.restype = I32
     lib.fmgp_tune_get.argtypes = [ctypes.c_char_p]
@@ -195,6 +197,23 @@ def fmgp_predict(X, nbr, C, k, kernel, Z, precision=PREC_FP64, Yhat_out=None, ne
                                int(k), r, ctypes.byref(kernel), int(precision), _ptr(Z), m,
                                _ptr(Yhat_out), _ptr(nearest_out), _stream(stream)))
     return Yhat_out, nearest_out
+
+
+def fmgp_muygps_predict(X, Y, Z, k, kernel, precision=PREC_FP64, Yhat_out=None, nbr_out=None,
+                        with_nbr=False, stream=None):
+    """MuyGPs prediction (Eq. 8): (Yhat m x r, neighbour table m x k or None)."""
+    _dev(X, "X"); _dev(Y, "Y"); _dev(Z, "Z")
+    n, d = X.shape
+    r = Y.shape[1]
+    m = Z.shape[0]
+    if Yhat_out is None:
+        Yhat_out = torch.empty((m, r), dtype=torch.float64, device=X.device)
+    if with_nbr and nbr_out is None:
+        nbr_out = torch.empty((m, k), dtype=torch.int32, device=X.device)
+    _check(load().fmgp_muygps_predict(_ptr(X), _dtype_code(X), _ptr(Y), n, d, r, _ptr(Z), m,
+                                      int(k), ctypes.byref(kernel), int(precision),
+                                      _ptr(Yhat_out), _ptr(nbr_out), _stream(stream)))
+    return Yhat_out, nbr_out
 
 
 def fmgp_loocv_objective(X, Y, nbr, k, batch, kernel, precision=PREC_FP64, resid_out=None,

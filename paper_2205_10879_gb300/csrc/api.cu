@@ -179,7 +179,7 @@ void diag_record_tc(const int* fb_count_dev, cudaStream_t s) {
 }
 
 // Precompute / LOOCV blocks in the requested precision.
-static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo,
+static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, int mode,
                       const fmgp_kernel& kern, fmgp_precision precision, Workspace& ws,
                       cudaStream_t s) {
   const int xb = dtype == FMGP_F64 ? 8 : 4;
@@ -194,8 +194,8 @@ static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo,
   int req = tune_params().block_warps;
   if (req == 0) req = tuned_block_warps((int)precision, a.k, a.d, a.r, (int)dtype);
   const int warps = pick_warps(bytes, req);
-  if (precision == FMGP_PREC_FP64) return launch_block_f64(a, X, dtype, loo, warps, s);
-  return run_block_mixed(a, X, dtype, loo, warps, kern, ws, s);
+  if (precision == FMGP_PREC_FP64) return launch_block_f64(a, X, dtype, mode, warps, s);
+  return run_block_mixed(a, X, dtype, mode, warps, kern, ws, s);
 }
 
 // Deterministic single-CTA sum of the LOOCV residuals: thread t adds
@@ -317,7 +317,7 @@ int fmgp_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
   a.ld = nbr_ld;
   a.k = k;
   a.kp = make_kparams(*kernel);
-  rc = run_blocks(a, X, dtype, false, *kernel, precision, ws, s);
+  rc = run_blocks(a, X, dtype, kModePrecompute, *kernel, precision, ws, s);
   if (rc) return rc;
   if (!status_out) {
     int h = 0;
@@ -393,7 +393,7 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
   a.ld = nbr_ld;
   a.k = k;
   a.kp = make_kparams(*kernel);
-  rc = run_blocks(a, X, dtype, true, *kernel, precision, ws, s);
+  rc = run_blocks(a, X, dtype, kModeLoocv, *kernel, precision, ws, s);
   if (rc) return rc;
   FMGP_LAUNCH(loocv_reduce<<<1, 1024, 0, s>>>(resid, b, qd));
   FMGP_CUDA_TRY(cudaGetLastError());
@@ -406,6 +406,52 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
     return FMGP_ENOTSPD;
   }
   return FMGP_OK;
+}
+
+int fmgp_muygps_predict(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                        int32_t r, const void* Z, int64_t m, int32_t k, const fmgp_kernel* kernel,
+                        fmgp_precision precision, double* Yhat_out, int32_t* nbr_out,
+                        void* stream) {
+  g_err[0] = 0;
+  if (!dtype_ok(dtype) || !kernel_ok(kernel) || !prec_ok(precision)) return FMGP_EINVAL;
+  FMGP_REQUIRE(X && Y, "X and Y must be non-NULL");
+  FMGP_REQUIRE(n >= 1 && n < INT32_MAX, "n = %lld out of range [1, 2^31)", (long long)n);
+  FMGP_REQUIRE(d >= 1 && r >= 1, "d and r must be >= 1");
+  FMGP_REQUIRE(k >= 1 && k <= n && k <= kMaxK, "k = %d must be in [1, min(n, %d)]", k, kMaxK);
+  FMGP_REQUIRE(m >= 0, "m = %lld must be >= 0", (long long)m);
+  if (m == 0) return FMGP_OK;
+  FMGP_REQUIRE(Z && Yhat_out, "Z and Yhat_out must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  int32_t* nbr = nbr_out ? nbr_out : ws.get<int32_t>((size_t)m * k);
+  int* fails = ws.get<int>(1);
+  if (!nbr || !fails) return FMGP_ENOMEM;
+  TuneParams tp = tune_params();
+  tp.grid_target = grid_target_for(d, k);
+  int rc = knn_query(X, dtype, n, d, Z, m, k, nbr, nullptr, tp, ws, s);
+  if (rc) return rc;
+  FMGP_CUDA_TRY(cudaMemsetAsync(fails, 0, sizeof(int), s));
+  BlockArgs a{};
+  a.Y = Y;
+  a.nbr = nbr;
+  a.fail_count = fails;
+  a.Zq = Z;
+  a.yhat = Yhat_out;
+  a.n = n;
+  a.count = m;
+  a.d = d;
+  a.r = r;
+  a.ld = k;
+  a.k = k;
+  a.kp = make_kparams(*kernel);
+  if (precision == FMGP_PREC_MIXED) {
+    float2* Zdf = ws.get<float2>((size_t)m * d);
+    if (!Zdf) return FMGP_ENOMEM;
+    rc = to_df(Z, dtype == FMGP_F64, m * d, Zdf, s);
+    if (rc) return rc;
+    a.Zdf = Zdf;
+  }
+  return run_blocks(a, X, dtype, kModeMuygps, *kernel, precision, ws, s);
 }
 
 }  // extern "C"

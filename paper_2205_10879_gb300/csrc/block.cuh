@@ -14,6 +14,13 @@ struct BlockLayout {
 
 BlockLayout block_layout(int k, int d, int r, int xbytes, bool f32_factor);
 
+// What a neighbourhood kernel produces.
+enum BlockMode {
+  kModePrecompute = 0,  // S_i = [i, N_i] -> row C_i (Eq. 6)
+  kModeLoocv = 1,       // N_i of batch points -> squared LOO residual (Eq. 5)
+  kModeMuygps = 2       // N*_t of test points -> prediction (Eq. 8)
+};
+
 struct BlockArgs {
   const double* Y;
   const int32_t* nbr;
@@ -21,6 +28,9 @@ struct BlockArgs {
   void* C;               // precompute only
   int8_t* status;        // precompute only (may be null)
   double* resid;         // LOOCV only
+  const void* Zq;        // MuyGPs prediction: test points (m x d, X's dtype)
+  const float2* Zdf;     // MuyGPs prediction, mixed: double-float copy of Zq
+  double* yhat;          // MuyGPs prediction: m x r
   int* fail_count;       // device counter of failed blocks
   int64_t n, count;      // count = n (precompute) or b (LOOCV)
   int d, r, ld, k;
@@ -35,12 +45,12 @@ struct BlockArgs {
 };
 
 // blocks = 0 picks a grid covering `count`; the list mode needs an explicit grid.
-int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo, int warps,
+int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mode, int warps,
                      cudaStream_t stream, int blocks = 0);
 
 // Mixed-precision form (FP32 factor + double-float refinement + FP64 fallback).
 size_t mixed_bytes_per_warp(int k, int d, int r);
-int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int warps,
+int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps,
                     const fmgp_kernel& kern, Workspace& ws, cudaStream_t s);
 
 }  // namespace fmgp

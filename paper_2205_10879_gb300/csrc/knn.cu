@@ -44,27 +44,17 @@ __device__ __forceinline__ float density_threshold(const GridView& gv, const Gri
   return r * r;
 }
 
+// Exact kq-nearest search of one query (q64/qf, excluding training index
+// `excl`, -1 for none) on the grid; the result is left in `top`.
 template <int D, int L>
-__global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
-                                                            int32_t* nbr_out, double* dist_out) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= gv.n) return;
-  const GridGeom g = *gv.geom;
-  double q64[D];
-  float qf[D];
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    q64[j] = gv.xs64[w * D + j];
-    qf[j] = gv.xs32[w * D + j];
-  }
-  const int qi = gv.ids[w];
+__device__ __forceinline__ void grid_knn_search(const GridView& gv, const GridGeom& g,
+                                                const double* q64, const float* qf, int excl,
+                                                int kq, int lane, WarpTopK<L>& top) {
   const float qs = query_slack<D>(qf);
   const float margin = g.margin + qs;
   const float cerr = g.conv_err + (g.conv_err > 0.f ? qs : 0.f);
   int cq[3] = {0, 0, 0};
   cell_of<D>(g, qf, cq);
-  WarpTopK<L> top;
   float pre = density_threshold<D>(gv, g, cq, kq);
   for (int attempt = 0; attempt < 2; ++attempt) {
     top.init(kq);
@@ -81,7 +71,7 @@ __global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
           int ci = INT_MAX;
           if (j < e0) {
             const int id = gv.ids[j];
-            if (id != qi) {
+            if (id != excl) {
               float xf[D];
 #pragma unroll
               for (int t = 0; t < D; ++t) xf[t] = gv.xs32[(int64_t)j * D + t];
@@ -105,7 +95,49 @@ __global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
     if (pre == __int_as_float(0x7f800000)) break;
     pre = __int_as_float(0x7f800000);
   }
+}
+
+// A1: queries are the training points themselves, in cell order (warp w takes
+// sorted point w), each excluded from its own list.
+template <int D, int L>
+__global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
+                                                            int32_t* nbr_out, double* dist_out) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= gv.n) return;
+  const GridGeom g = *gv.geom;
+  double q64[D];
+  float qf[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    q64[j] = gv.xs64[w * D + j];
+    qf[j] = gv.xs32[w * D + j];
+  }
+  const int qi = gv.ids[w];
+  WarpTopK<L> top;
+  grid_knn_search<D, L>(gv, g, q64, qf, qi, kq, lane, top);
   top.store(kq, lane, nbr_out + (int64_t)qi * kq, dist_out ? dist_out + (int64_t)qi * kq : nullptr);
+}
+
+// kq nearest training points of external query points (MuyGPs prediction).
+template <int D, int L, typename T>
+__global__ void __launch_bounds__(256) knn_grid_query_kernel(GridView gv, const T* Q, int64_t m,
+                                                             int kq, int32_t* idx_out,
+                                                             double* key_out) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= m) return;
+  const GridGeom g = *gv.geom;
+  double q64[D];
+  float qf[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    q64[j] = (double)Q[w * D + j];
+    qf[j] = (float)Q[w * D + j];
+  }
+  WarpTopK<L> top;
+  grid_knn_search<D, L>(gv, g, q64, qf, -1, kq, lane, top);
+  top.store(kq, lane, idx_out + w * kq, key_out ? key_out + w * kq : nullptr);
 }
 
 // ---------------------------------------------------------- brute force ----
@@ -208,6 +240,18 @@ int launch_grid_self(const GridView& gv, int kq, int32_t* nbr, double* dist, cud
   return FMGP_OK;
 }
 
+template <int D, typename T>
+int launch_grid_query(const GridView& gv, const T* Q, int64_t m, int kq, int32_t* idx,
+                      double* key, cudaStream_t s) {
+  const int blocks = ceil_div(m * 32, 256);
+  if (kq <= 32) FMGP_LAUNCH((knn_grid_query_kernel<D, 1, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
+  else if (kq <= 64) FMGP_LAUNCH((knn_grid_query_kernel<D, 2, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
+  else if (kq <= 96) FMGP_LAUNCH((knn_grid_query_kernel<D, 3, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
+  else FMGP_LAUNCH((knn_grid_query_kernel<D, 4, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
 template <typename T, int L>
 int launch_brute_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
                    const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
@@ -273,6 +317,27 @@ int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t*
                                 stream);
   return launch_brute<float>((const float*)X, n, d, (const float*)X, n, kq, 1, ws, nbr, dist,
                              stream);
+}
+
+int knn_query(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m, int kq,
+              int32_t* idx, double* key, const TuneParams& tp, Workspace& ws, cudaStream_t stream) {
+  if (m == 0) return FMGP_OK;
+  if (d <= kGridMaxD) {
+    GridView gv;
+    int rc = build_grid(X, dtype, n, d, tp.grid_target, ws, stream, &gv);
+    if (rc) return rc;
+    if (dtype == FMGP_F64) {
+      const double* q = (const double*)Q;
+      if (d == 1) return launch_grid_query<1>(gv, q, m, kq, idx, key, stream);
+      if (d == 2) return launch_grid_query<2>(gv, q, m, kq, idx, key, stream);
+      return launch_grid_query<3>(gv, q, m, kq, idx, key, stream);
+    }
+    const float* q = (const float*)Q;
+    if (d == 1) return launch_grid_query<1>(gv, q, m, kq, idx, key, stream);
+    if (d == 2) return launch_grid_query<2>(gv, q, m, kq, idx, key, stream);
+    return launch_grid_query<3>(gv, q, m, kq, idx, key, stream);
+  }
+  return knn_query_brute(X, dtype, n, d, Q, m, kq, idx, key, ws, stream);
 }
 
 int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,

@@ -28,6 +28,11 @@ int knn_brute_list(const void* X, fmgp_dtype dtype, int64_t n, int d, const void
                    int kq, bool self, const int* qlist, const int* qcount, int32_t* idx,
                    double* key, Workspace& ws, cudaStream_t stream);
 
+// kq nearest training points of each of m query points (no exclusion):
+// grid search for d <= 3, tensor-core or exhaustive search otherwise.
+int knn_query(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m, int kq,
+              int32_t* idx, double* key, const TuneParams& tp, Workspace& ws, cudaStream_t stream);
+
 // Tensor-core candidate search + certified exact re-rank (d >= 16).
 bool tc_knn_eligible(int64_t n, int d, int64_t m, int kq);
 int tc_knn(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m, int kq,

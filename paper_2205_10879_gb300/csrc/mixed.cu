@@ -227,9 +227,10 @@ __device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* 
   }
 }
 
-template <bool LOO, int NS, int CB>
+template <int MODE, int NS, int CB>
 __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
                                                           MixedLayout lay) {
+  constexpr bool LOO = MODE == kModeLoocv;
   extern __shared__ __align__(16) unsigned char smem[];
   const int wpb = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -250,10 +251,10 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
        item += (int64_t)gridDim.x * wpb) {
     int64_t i = LOO ? args.batch[item] : item;
     bool bad = false;
-    if (i < 0 || i >= args.n) { bad = true; i = 0; }
+    if (MODE != kModeMuygps && (i < 0 || i >= args.n)) { bad = true; i = 0; }
     for (int a = lane; a < k; a += 32) {
-      int64_t idx = LOO ? (int64_t)args.nbr[i * args.ld + a]
-                        : (a == 0 ? i : (int64_t)args.nbr[i * args.ld + a - 1]);
+      int64_t idx = MODE != kModePrecompute ? (int64_t)args.nbr[i * args.ld + a]
+                                            : (a == 0 ? i : (int64_t)args.nbr[i * args.ld + a - 1]);
       if (idx < 0 || idx >= args.n) { bad = true; idx = 0; }
       S[a] = (int)idx;
     }
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
         const int pos = atomicAdd(mx.fb_count, 1);
         mx.fb_list[pos] = (int)item;
       }
-    } else if (!LOO) {
+    } else if (MODE == kModePrecompute) {
       float2* Ci = (float2*)args.C + i * (int64_t)k * r;
       for (int e = lane; e < k * r; e += 32) {
         const dfl cv = df_mul(XV[e], kp.inv_var);
@@ -456,9 +457,9 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
       }
       if (args.status && lane == 0) args.status[i] = FMGP_BLOCK_OK;
     } else {
-      // leave-one-out residual of x_i from its k neighbours, in DF
+      // cross-covariance of the query point (x_i for LOOCV, z_t for MuyGPs), in DF
       dfl kx[NS];
-      const float2* xi = mx.Xdf + i * d;
+      const float2* xi = MODE == kModeMuygps ? args.Zdf + i * d : mx.Xdf + i * d;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         const int a = lane + 32 * s;
@@ -478,11 +479,16 @@ __global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, Mix
           const dfl o = {__shfl_xor_sync(kFull, acc.hi, off), __shfl_xor_sync(kFull, acc.lo, off)};
           acc = df_add(acc, o);
         }
-        const float2 y = mx.Ydf[i * r + c];
-        const dfl e = df_add(dfl{y.x, y.y}, df_neg(acc));
-        e2 = df_add_fast(e2, df_sqr(e));
+        if (MODE == kModeMuygps) {
+          // correlations times M^{-1} y; sigma^2 cancels (K = sigma^2 M)
+          if (lane == 0) args.yhat[i * r + c] = df_to_double(acc);
+        } else {
+          const float2 y = mx.Ydf[i * r + c];
+          const dfl e = df_add(dfl{y.x, y.y}, df_neg(acc));
+          e2 = df_add_fast(e2, df_sqr(e));
+        }
       }
-      if (lane == 0) args.resid[item] = df_to_double(e2);
+      if (lane == 0 && MODE == kModeLoocv) args.resid[item] = df_to_double(e2);
     }
     __syncwarp();
   }
@@ -558,8 +564,9 @@ int to_df(const void* in, bool f64, int64_t count, float2* out, cudaStream_t s) 
 
 size_t mixed_bytes_per_warp(int k, int d, int r) { return mixed_layout(k, d, r).bytes; }
 
-int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int warps,
+int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps,
                     const fmgp_kernel& kern, Workspace& ws, cudaStream_t s) {
+  const bool loo = mode != kModePrecompute;
   MixedArgs mx;
   float2* Xdf = ws.get<float2>((size_t)a.n * a.d);
   float2* Ydf = ws.get<float2>((size_t)a.n * a.r);
@@ -584,7 +591,9 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int 
   auto pick = [&](auto sconst) {
     constexpr int SS = decltype(sconst)::value;
     constexpr int CB = SS <= 2 ? 8 : 4;
-    return loo ? block_mixed_kernel<true, SS, CB> : block_mixed_kernel<false, SS, CB>;
+    return mode == kModeLoocv    ? block_mixed_kernel<kModeLoocv, SS, CB>
+           : mode == kModeMuygps ? block_mixed_kernel<kModeMuygps, SS, CB>
+                                 : block_mixed_kernel<kModePrecompute, SS, CB>;
   };
   const int S = (a.k + 31) / 32;
   auto kern_fn = S == 1 ? pick(std::integral_constant<int, 1>{})
@@ -602,7 +611,7 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, bool loo, int 
   f.layout = block_layout(a.k, a.d, a.r, dtype == FMGP_F64 ? 8 : 4, false);
   int fw = (int)((200 * 1024) / f.layout.bytes_per_warp);
   fw = fw > 4 ? 4 : (fw < 1 ? 1 : fw);
-  return launch_block_f64(f, X, dtype, loo, fw, s, num_sms() * 2);
+  return launch_block_f64(f, X, dtype, mode, fw, s, num_sms() * 2);
 }
 
 int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,

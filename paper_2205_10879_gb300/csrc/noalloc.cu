@@ -136,7 +136,7 @@ extern "C" int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, con
   }
   int warps = (int)((200 * 1024) / a.layout.bytes_per_warp);
   if (warps > 8) warps = 8;
-  rc = launch_block_f64(a, X, dtype, true, warps, s);
+  rc = launch_block_f64(a, X, dtype, kModeLoocv, warps, s);
   if (rc) return rc;
   FMGP_LAUNCH(noalloc_reduce<<<1, 1024, 0, s>>>(a.resid, b, &sc->q));
   FMGP_CUDA_TRY(cudaGetLastError());

@@ -20,8 +20,9 @@ __device__ __forceinline__ void pair_of(int p, int& a, int& b) {
   b = p - x * (x - 1) / 2;
 }
 
-template <typename T, bool LOO>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const T* X) {
+  constexpr bool LOO = MODE == kModeLoocv;
   extern __shared__ __align__(16) unsigned char smem[];
   const BlockLayout lay = args.layout;
   const int wpb = blockDim.x >> 5;
@@ -41,12 +42,12 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
        it += (int64_t)gridDim.x * wpb) {
     const int64_t item = args.list ? (int64_t)args.list[it] : it;
     int64_t i = LOO ? args.batch[item] : item;
-    // S: precompute S_i = [i, N_i]; LOOCV N_i (self excluded)
+    // S: precompute S_i = [i, N_i]; LOOCV N_i (self excluded); MuyGPs N*_t
     bool bad = false;
-    if (i < 0 || i >= args.n) { bad = true; i = 0; }
+    if (MODE != kModeMuygps && (i < 0 || i >= args.n)) { bad = true; i = 0; }
     for (int a = lane; a < k; a += 32) {
-      int64_t idx = LOO ? (int64_t)args.nbr[i * args.ld + a]
-                        : (a == 0 ? i : (int64_t)args.nbr[i * args.ld + a - 1]);
+      int64_t idx = MODE != kModePrecompute ? (int64_t)args.nbr[i * args.ld + a]
+                                            : (a == 0 ? i : (int64_t)args.nbr[i * args.ld + a - 1]);
       if (idx < 0 || idx >= args.n) { bad = true; idx = 0; }
       S[a] = (int)idx;
     }
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
         __syncwarp();
       }
     }
-    if (!LOO) {
+    if (MODE == kModePrecompute) {
       if (args.c_df) {
         float2* Ci = (float2*)args.C + i * (int64_t)k * r;
         for (int e = lane; e < k * r; e += 32) {
@@ -169,9 +170,9 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
                                      : (args.list ? FMGP_BLOCK_FP64_RETRY : FMGP_BLOCK_OK));
       if (fail && lane == 0) atomicAdd(args.fail_count, 1);
     } else {
-      // leave-one-out residual of x_i against its neighbours
+      // cross-covariance of the query point (x_i for LOOCV, z_t for MuyGPs)
       double kx[kMaxSlots];
-      const T* xi = X + i * d;
+      const T* xi = MODE == kModeMuygps ? (const T*)args.Zq + i * d : X + i * d;
 #pragma unroll
       for (int s = 0; s < kMaxSlots; ++s) {
         const int a = lane + 32 * s;
@@ -195,11 +196,16 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
         }
 #pragma unroll
         for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-        const double e = args.Y[i * r + c] - acc;
-        e2 = fma(e, e, e2);
+        if (MODE == kModeMuygps) {
+          if (lane == 0)
+            args.yhat[i * r + c] = fail ? __longlong_as_double(0x7ff8000000000000ll) : acc;
+        } else {
+          const double e = args.Y[i * r + c] - acc;
+          e2 = fma(e, e, e2);
+        }
       }
       if (lane == 0) {
-        args.resid[item] = fail ? __longlong_as_double(0x7ff8000000000000ll) : e2;
+        if (MODE == kModeLoocv) args.resid[item] = fail ? __longlong_as_double(0x7ff8000000000000ll) : e2;
         if (fail) atomicAdd(args.fail_count, 1);
       }
     }
@@ -226,18 +232,22 @@ BlockLayout block_layout(int k, int d, int r, int xbytes, bool f32_factor) {
   return l;
 }
 
-int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, bool loo, int warps,
+int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mode, int warps,
                      cudaStream_t stream, int blocks) {
   const size_t smem = a.layout.bytes_per_warp * warps;
   const int sms = num_sms();
   const int64_t need = (a.count + warps - 1) / warps;
   if (blocks <= 0) blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 16));
   if (dtype == FMGP_F64) {
-    auto kern = loo ? block_f64_kernel<double, true> : block_f64_kernel<double, false>;
+    auto kern = mode == kModeLoocv    ? block_f64_kernel<double, kModeLoocv>
+                : mode == kModeMuygps ? block_f64_kernel<double, kModeMuygps>
+                                      : block_f64_kernel<double, kModePrecompute>;
     FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
     FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const double*)X));
   } else {
-    auto kern = loo ? block_f64_kernel<float, true> : block_f64_kernel<float, false>;
+    auto kern = mode == kModeLoocv    ? block_f64_kernel<float, kModeLoocv>
+                : mode == kModeMuygps ? block_f64_kernel<float, kModeMuygps>
+                                      : block_f64_kernel<float, kModePrecompute>;
     FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
     FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const float*)X));
   }

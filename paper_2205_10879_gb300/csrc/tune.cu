@@ -105,8 +105,8 @@ extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const d
     float ms = 0.f;
     int rc = time_ms(s, 2, [&]() {
       Workspace inner(s);
-      return precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, false, w, s)
-                                         : run_block_mixed(a, X, dtype, false, w, *kernel, inner, s);
+      return precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, kModePrecompute, w, s)
+                                         : run_block_mixed(a, X, dtype, kModePrecompute, w, *kernel, inner, s);
     }, &ms);
     if (rc) return rc;
     if (ms < best_ms) { best_ms = ms; best = w; }

@@ -223,3 +223,33 @@ def test_accuracy_is_plausible_on_tiny():
     yh, _ = oracle.predict(W.X, nbr, C, kern, W.Z)
     rmse = np.sqrt(np.mean((yh - W.Ztrue) ** 2))
     assert rmse < 0.05
+
+
+def test_muygps_with_k_equal_n_is_the_dense_gp_mean():
+    """Eq. 8 with every training point as neighbour reduces to Eq. 2."""
+    rng = np.random.default_rng(9)
+    n, r = 50, 2
+    X = rng.random((n, 2))
+    Y = rng.normal(size=(n, r))
+    Z = rng.random((20, 2))
+    rho, var, tau2 = 0.3, 1.5, 1e-3
+    kern = oracle.kernel("matern", 2.5, rho, var, tau2)
+    yh, _ = oracle.muygps_predict(X, Y, Z, n, kern)
+    Kxx = _dense_kernel(X, X, 2.5, rho, var) + var * tau2 * np.eye(n)
+    ref = _dense_kernel(Z, X, 2.5, rho, var) @ sl.cho_solve(sl.cho_factor(Kxx, lower=True), Y)
+    np.testing.assert_allclose(yh, ref, rtol=1e-8, atol=1e-8 * np.abs(ref).max())
+
+
+def test_muygps_equals_fastmuygps_at_training_points():
+    """At z = x_j the test point's own k nearest neighbours are j and its k-1
+    nearest others, i.e. S_j, so Eq. 8 and Eq. 7 are the same formula."""
+    W = wl.tiny(n=600, m=10)
+    kern = oracle.kernel("matern", 1.5, 0.1, 1.0, 1e-4)
+    nbr, _ = oracle.self_knn(W.X, 29)
+    C, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern)
+    rows = np.array([3, 44, 101, 599])
+    yf, _ = oracle.predict(W.X, nbr, C, kern, W.X[rows])
+    ym, N = oracle.muygps_predict(W.X, W.Y, W.X[rows], 30, kern)
+    np.testing.assert_array_equal(N[:, 0], rows)
+    np.testing.assert_array_equal(N[:, 1:], nbr[rows])
+    np.testing.assert_allclose(ym, yf, rtol=1e-9, atol=1e-12)
