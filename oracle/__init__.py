@@ -61,6 +61,32 @@ def _load():
     return _lib
 
 
+class use_library:
+    """Context manager: route every oracle call through another build of the
+    oracle (used by the mutation test to run the pins against planted bugs)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        _lib = None
+        real = _build.build
+        _build.build = lambda *a, **k: self.path
+        try:
+            _load()
+        finally:
+            _build.build = real
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
 def kernel(kind="matern", nu=1.5, length_scale=0.1, variance=1.0, nugget=1e-4):
     """Hyperparameters theta = [sigma, rho, nu, tau] of Eq. 3 (variance = sigma^2,
     nugget = tau^2).  kind is 'matern' (nu in {0.5, 1.5, 2.5}) or 'rbf'."""

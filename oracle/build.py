@@ -16,6 +16,14 @@ def needs_build() -> bool:
     return any(os.path.getmtime(s) > t for s in SOURCES)
 
 
+def build_variant(defines, target):
+    """Compile the oracle with extra -D macros into `target` (mutation tests)."""
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared"] + [f"-D{m}" for m in defines] + ["-o", target, SOURCES[0], "-lm"]
+    subprocess.run(cmd, check=True, cwd=HERE)
+    return target
+
+
 def build(force: bool = False) -> str:
     if force or needs_build():
         tmp = TARGET + f".tmp{os.getpid()}"

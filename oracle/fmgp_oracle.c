@@ -11,6 +11,10 @@
  * Arithmetic: IEEE FP64, compiled with -O2 -ffp-contract=off (no FMA
  * contraction, no fast-math), OpenMP across independent rows only.
  *
+ * Blocks guarded by ORACLE_MUTANT_* plant one mistake each; only the mutation
+ * test compiles them (tests/test_oracle_mutations.py) to show that the pins
+ * catch it.  The oracle proper is built without any of these macros.
+ *
  * Parity pins (tests/test_oracle_pins.py): Matern closed forms against the
  * Bessel form of Eq. 3 (scipy.special.kv); kNN against an all-pairs numpy
  * lexsort on tie-heavy integer grids; blocks symmetric and SPD; k = n reduces
@@ -98,9 +102,15 @@ int fmgp_oracle_knn(const double* X, int64_t n, int d, const double* Q, int64_t 
     for (int64_t j = 0; j < n; ++j) {
       if (exclude && j == exclude[q]) continue;
       double D = fmgp_oracle_key(Q + q * d, X + j * d, d);
+#ifdef ORACLE_MUTANT_TIE_HIGH
+      if (cnt == kq && !(D <= best[kq - 1])) continue;
+      int p = (cnt < kq) ? cnt : kq - 1;
+      while (p > 0 && best[p - 1] >= D) {
+#else
       if (cnt == kq && !(D < best[kq - 1])) continue;
       int p = (cnt < kq) ? cnt : kq - 1;
       while (p > 0 && best[p - 1] > D) {
+#endif
         best[p] = best[p - 1];
         bidx[p] = bidx[p - 1];
         --p;

@@ -36,12 +36,18 @@ static REAL FN(sqdist)(const double* a, const double* b, int d) {
 static REAL FN(phi)(const fmgp_oracle_kernel* kp, REAL D) {
   REAL rho = (REAL)kp->length_scale;
   if (kp->kind == 1) {
+#ifdef ORACLE_MUTANT_RBF_SCALE
+    return EXP(-D / (rho * rho));
+#endif
     return EXP(-D / (2 * rho * rho));
   }
   REAL u = SQRT(D) / rho;
   if (kp->nu == 0.5) return EXP(-u);
   if (kp->nu == 1.5) {
     REAL s3 = SQRT((REAL)3);
+#ifdef ORACLE_MUTANT_MATERN_POLY
+    return (1 + u) * EXP(-s3 * u);
+#endif
     return (1 + s3 * u) * EXP(-s3 * u);
   }
   /* nu == 2.5 (validated by the caller) */
@@ -58,6 +64,10 @@ static void FN(assemble)(const double* X, int d, const int32_t* S, int k,
   for (int a = 0; a < k; ++a) {
     for (int b = 0; b < k; ++b) {
       if (a == b) {
+#ifdef ORACLE_MUTANT_NUGGET_UNSCALED
+        K[a * k + b] = s2 + (REAL)kp->nugget;
+        continue;
+#endif
         K[a * k + b] = s2 * (1 + (REAL)kp->nugget);
       } else {
         REAL D = FN(sqdist)(X + (int64_t)S[a] * d, X + (int64_t)S[b] * d, d);
@@ -96,7 +106,11 @@ static void FN(chol_solve)(const REAL* L, int k, REAL* y, int r) {
     }
     for (int i = k - 1; i >= 0; --i) {
       REAL s = y[i * r + c];
+#ifdef ORACLE_MUTANT_BACKSOLVE_TRANSPOSE
+      for (int p = i + 1; p < k; ++p) s = s - L[i * k + p] * y[p * r + c];
+#else
       for (int p = i + 1; p < k; ++p) s = s - L[p * k + i] * y[p * r + c];
+#endif
       y[i * r + c] = s / L[i * k + i];
     }
   }
@@ -120,8 +134,13 @@ static int64_t FN(precompute)(const double* X, const double* Y, int64_t n, int d
     int32_t* S = (int32_t*)malloc(sizeof(int32_t) * k);
     REAL* K = (REAL*)malloc(sizeof(REAL) * k * k);
     REAL* w = (REAL*)malloc(sizeof(REAL) * k * r);
+#ifdef ORACLE_MUTANT_SELF_LAST
+    for (int a = 0; a < k - 1; ++a) S[a] = nbr[i * ld + a];
+    S[k - 1] = (int32_t)i;
+#else
     S[0] = (int32_t)i;
     for (int a = 1; a < k; ++a) S[a] = nbr[i * ld + (a - 1)];
+#endif
     FN(assemble)(X, d, S, k, kp, K);
     int bad = FN(cholesky)(K, k);
     for (int a = 0; a < k; ++a)
@@ -151,6 +170,9 @@ static void FN(predict_given)(const double* X, int d, const int32_t* nbr, int ld
     for (int a = 0; a < k; ++a) {
       int64_t s = (a == 0) ? j : nbr[j * ld + (a - 1)];
       REAL kz = (REAL)kp->variance * FN(phi)(kp, FN(sqdist)(z, X + s * d, d));
+#ifdef ORACLE_MUTANT_CROSS_NUGGET
+      if (FN(sqdist)(z, X + s * d, d) == 0) kz = kz + (REAL)kp->variance * (REAL)kp->nugget;
+#endif
       for (int c = 0; c < r; ++c) Yhat[t * r + c] = Yhat[t * r + c] + kz * C[(j * k + a) * r + c];
     }
   }
@@ -191,7 +213,11 @@ static int64_t FN(loocv)(const double* X, const double* Y, int64_t n, int d, int
       for (int c = 0; c < r; ++c) {
         REAL yh = 0;
         for (int a = 0; a < k; ++a) yh = yh + kx[a] * w[a * r + c];
+#ifdef ORACLE_MUTANT_LOO_SIGN
+        REAL e = (REAL)Y[i * r + c] + yh;
+#else
         REAL e = (REAL)Y[i * r + c] - yh;
+#endif
         e2 = e2 + e * e;
       }
       resid[q] = e2;

@@ -45,18 +45,21 @@ def optimize_hyperparameters(X, Y, batch, k, kernel, params=("length_scale",), b
             setattr(kk, p, float(math.exp(v)))
         return kk
 
+    # the optimiser sees log Q: Q itself can be tiny (1e-4 and below), which
+    # would put its gradient under L-BFGS-B's default tolerance at once
     def objective(x):
         q, _ = fb.fmgp_loocv_objective(X, Y, nbr, k, batch, make(x), precision,
                                        raise_on_not_spd=False)
-        if not math.isfinite(q):
+        if not (math.isfinite(q) and q > 0):
             q = 1e300
         history.append((x.copy(), q))
-        return q
+        return math.log(q)
 
-    q0 = objective(x0)
+    q0 = math.exp(objective(x0))
     res = minimize(objective, x0, method="L-BFGS-B", bounds=list(zip(lb, ub)),
-                   options={"maxiter": maxiter, "eps": 1e-4})
+                   options={"maxiter": maxiter, "eps": 1e-5, "ftol": 1e-12, "gtol": 1e-8})
     best = make(res.x)
-    return {"kernel": best, "q_start": q0, "q_best": float(res.fun), "evaluations": len(history),
+    return {"kernel": best, "q_start": q0, "q_best": float(math.exp(res.fun)),
+            "evaluations": len(history),
             "theta": {p: float(math.exp(v)) for p, v in zip(params, res.x)},
             "converged": bool(res.success), "history": history}
