@@ -23,6 +23,7 @@
 #include <mutex>
 #include "knn.cuh"
 #include "topk.cuh"
+#include "df.cuh"
 
 namespace fmgp {
 namespace {
@@ -521,6 +522,83 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
       }
     }
   }
+  // FP32 inputs: when at most 32 candidates can still be among the kq nearest
+  // (lower bound <= U), rank them by double-float distance (relative error
+  // <= (d+8) 2^-45, which also covers the canonical FP64 key's rounding).  If
+  // every neighbouring gap up to rank kq exceeds both values' error bounds,
+  // membership and order are those of the canonical keys.
+  if (key_out == nullptr && sizeof(T) == 4 && kq <= 32) {
+    int cnt = 0;
+#pragma unroll
+    for (int g = 0; g < S; ++g)
+      cnt += __popc(__ballot_sync(kFull, 32 * g + lane < L && lo[g] <= U));
+    if (cnt <= 32) {
+      int my_slot = -1, base = 0;
+#pragma unroll
+      for (int g = 0; g < S; ++g) {
+        const int a = 32 * g + lane;
+        const bool in = a < L && lo[g] <= U;
+        const unsigned bal = __ballot_sync(kFull, in);
+        const int pos = base + __popc(bal & ((1u << lane) - 1u));
+        // member with position pos is held by lane pos
+        for (int src = 0; src < 32; ++src) {
+          const int ps = __shfl_sync(kFull, pos, src);
+          const int inn = __shfl_sync(kFull, (int)in, src);
+          if (inn && ps == lane) my_slot = 32 * g + src;
+        }
+        base += __popc(bal);
+      }
+      rowlist[lane] = my_slot >= 0 ? lists[wid][1][my_slot] : -1;
+      __syncwarp();
+      dfl acc = {0.0f, 0.0f};
+      for (int c0 = 0; c0 < d; c0 += kRrChunk) {
+        const int cw = min(kRrChunk, d - c0);
+        load_rows<T>(X, d, rowlist, 32, c0, cw, tile, lane);
+        for (int p = lane; p < cw; p += 32) qrow[p] = qr[c0 + p];
+        __syncwarp();
+        if (my_slot >= 0) {
+          const T* myrow = tile + lane * (kRrChunk + 1);
+          for (int p = 0; p < cw; ++p) {
+            const dfl t = df_two_sum((float)qrow[p], -(float)myrow[p]);
+            acc = df_add_fast(acc, df_sqr(t));
+          }
+        }
+        __syncwarp();
+      }
+      const float eps = (d + 8) * 2.85e-14f;
+      WarpTopK<1> o2;
+      o2.init(cnt);
+      o2.offer(my_slot >= 0 ? (unsigned long long)__float_as_uint(acc.hi) : ~0ull,
+               my_slot >= 0 ? lane : INT_MAX, lane);
+      const int src = o2.i[0] < 32 ? o2.i[0] : 0;  // lane holding the member ranked here
+      const dfl mine = {__shfl_sync(kFull, acc.hi, src), __shfl_sync(kFull, acc.lo, src)};
+      const dfl next = {__shfl_down_sync(kFull, mine.hi, 1), __shfl_down_sync(kFull, mine.lo, 1)};
+      bool ok2 = true;
+      if (lane < kq && lane + 1 < cnt) {
+        const dfl gap = df_add(next, df_neg(mine));
+        ok2 = gap.hi > eps * (mine.hi + next.hi) + 1e-37f;
+      }
+      if (cnt >= kq && __all_sync(kFull, ok2)) {
+        const int slot = __shfl_sync(kFull, my_slot, src);
+        if (lane < kq) idx_out[w * kq + lane] = lists[wid][1][slot];
+        float hk = __shfl_sync(kFull, mine.hi + fabsf(mine.lo), kq - 1);
+        hk = hk * (1.0f + 1e-6f) + 1e-37f;  // upper bound of the kq-th canonical key
+        const float xdel0 = __uint_as_float(xstats[1]);
+        const float qn0 = sqrtf(qnorm2[w]) * 1.0001f;
+        const float E0 =
+            2.0f * d * 4.0f * u * qn0 * xmaxn + d * u * (qn0 * qn0 + xmaxn * xmaxn) + 1e-30f;
+        const float Dl0 = dL[w];
+        float lb0 = fmaxf(sqrtf(fmaxf(Dl0 - E0, 0.0f)) - qdelta[w] - xdel0, 0.0f);
+        lb0 = lb0 * lb0 * (1.0f - 1e-5f);
+        const bool cert0 = (*err == 0) && (Dl0 == __int_as_float(0x7f800000) || lb0 > hk);
+        if (!cert0 && lane == 0) {
+          const int pos = atomicAdd(fb_count, 1);
+          fb_list[pos] = (int)w;
+        }
+        return;
+      }
+    }
+  }
   // B: compact the candidates that can still be among the kq nearest
   int nkeep = 0;
 #pragma unroll
@@ -667,9 +745,9 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   rc = make_map(&tmQ, Qb, self && m_pad <= n_pad ? n_pad : m_pad, d_pad, kTM);
   if (!rc) rc = make_map(&tmX, Xb, n_pad, d_pad, kTN);
   if (rc) return rc;
-  // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
   const int n_tiles = (int)(n_pad / kTN), k_chunks = d_pad / kTK;
   const int64_t qblocks = m_pad / kTM;
+  // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
   int chunk_tiles = (int)std::max<int64_t>(1, (int64_t)(1ll << 30) / (m_pad * 4 * kTN));
   chunk_tiles = std::min(chunk_tiles, n_tiles);
   // tiles per CTA: enough CTAs for two waves over the SMs
