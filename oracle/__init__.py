@@ -55,6 +55,9 @@ def _load():
         lib.fmgp_oracle_loocv_ld.restype = I64
         lib.fmgp_oracle_muygps_predict.argtypes = [P, P, I64, I32, I32, P, I64, I32, KP, P, P]
         lib.fmgp_oracle_muygps_predict.restype = I64
+        lib.fmgp_oracle_mcmc.argtypes = [P, I64, I32, P, I32, P, I32, I32, KP, P, I32, D, D, D,
+                                         I32, D, D, I32, I64, P, P, P, P, P, P]
+        lib.fmgp_oracle_mcmc.restype = I64
         lib.fmgp_oracle_set_threads.argtypes = [I32]
         lib.fmgp_oracle_max_threads.restype = I32
         _lib = lib
@@ -254,6 +257,33 @@ def loocv(X, Y, nbr, k, batch, kern, long_double=False):
     if f < 0:
         raise ValueError("oracle loocv: bad arguments")
     return float(Q[0]), res
+
+
+def mcmc(X, nbr, C, kern, z0, dim, lo, hi, f_obs, sigma, step, x0, noise, expo, col=0):
+    """Metropolis calibration of input coordinate `dim` (Sec. 4.2).  noise and
+    expo are (steps x chains) N(0,1) and Exp(1) draws.  Returns (samples
+    steps x chains, accepted per chain, margin steps x chains)."""
+    X = _c(X, np.float64)
+    nbr = _c(nbr, np.int32)
+    C = _c(C, np.float64)
+    z0 = _c(z0, np.float64)
+    x0 = _c(x0, np.float64)
+    noise = _c(noise, np.float64)
+    expo = _c(expo, np.float64)
+    n, d = X.shape
+    _, k, r = C.shape
+    steps, chains = noise.shape
+    samples = np.zeros((steps, chains), np.float64)
+    margin = np.zeros((steps, chains), np.float64)
+    acc = np.zeros(chains, np.int64)
+    rc = _load().fmgp_oracle_mcmc(_p(X), n, d, _p(nbr), nbr.shape[1], _p(C), k, r,
+                                  ctypes.byref(kern), _p(z0), int(dim), float(lo), float(hi),
+                                  float(f_obs), int(col), float(sigma), float(step), int(chains),
+                                  int(steps), _p(x0), _p(noise), _p(expo), _p(samples), _p(acc),
+                                  _p(margin))
+    if rc:
+        raise ValueError("oracle mcmc: bad arguments")
+    return samples, acc, margin
 
 
 def muygps_predict(X, Y, Z, k, kern):

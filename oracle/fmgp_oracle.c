@@ -21,8 +21,10 @@
  * to the dense GP mean of Eq. 2 (scipy cho_solve); interpolation identity at
  * z = x_i; leave-one-out block-inverse identity linking Eq. 6 to Eq. 5;
  * sigma^2 invariance of the mean; long-double re-evaluation of the FP64
- * rounding error.  The paper prints no worked example, so no printed value
- * pins the oracle directly.
+ * rounding error; the Metropolis calibration chain of Sec. 4.2 against the
+ * closed-form (truncated Gaussian) posterior of a linear response, and its
+ * greedy and always-accept limits.  The paper prints no worked example, so
+ * no printed value pins the oracle directly.
  */
 #include <math.h>
 #include <stdint.h>
@@ -264,6 +266,83 @@ int64_t fmgp_oracle_loocv_ld(const double* X, const double* Y, int64_t n, int d,
   *Q = (double)Ql;
   free(rl);
   return f;
+}
+
+/* Metropolis calibration of one input coordinate against one observation
+ * (Sec. 4.2, the borehole inverse problem), with the posterior mean of Eq. 7
+ * as the emulator.  The input is z0 with coordinate `dim` replaced by the
+ * chain state x; the prior on x is uniform on [lo, hi]; the likelihood of
+ * the observation f_obs of response column `col` is Gaussian with standard
+ * deviation sigma.  Chain c starts at x0[c]; its step t proposes
+ *   x' = x + step * noise[t * chains + c].
+ * A proposal outside [lo, hi] has zero prior density and is rejected (its
+ * margin is -inf).  Otherwise, with e = f_obs - yhat(x)[col] and e' the same
+ * at x',
+ *   delta = (e^2 - e'^2) / (2 sigma^2)     (the log likelihood ratio)
+ * and the proposal is accepted iff margin = delta + expo[t * chains + c] > 0:
+ * the Metropolis test u < exp(delta) written with expo = -log u ~ Exp(1), so
+ * that no transcendental function decides a move.  samples[t * chains + c]
+ * is the state after step t, accepted[c] the number of accepted moves.
+ * Returns -1 on bad arguments, else 0. */
+static double mcmc_emulate(const double* X, int64_t n, int d, const int32_t* nbr, int ld,
+                           const double* C, int k, int r, const fmgp_oracle_kernel* kp,
+                           double* z, double* yh, int col) {
+  int32_t near = 0;
+  fmgp_oracle_knn(X, n, d, z, 1, 1, NULL, &near, NULL);
+  predict_given_f64(X, d, nbr, ld, C, k, r, kp, z, 1, &near, yh);
+  return yh[col];
+}
+
+int64_t fmgp_oracle_mcmc(const double* X, int64_t n, int d, const int32_t* nbr, int ld,
+                         const double* C, int k, int r, const fmgp_oracle_kernel* kp,
+                         const double* z0, int dim, double lo, double hi, double f_obs, int col,
+                         double sigma, double step, int chains, int64_t steps, const double* x0,
+                         const double* noise, const double* expo, double* samples,
+                         int64_t* accepted, double* margin) {
+  if (!kernel_ok(kp) || !shape_ok(n, d, r, ld, k) || dim < 0 || dim >= d || col < 0 ||
+      col >= r || !(lo <= hi) || !(sigma > 0) || chains < 0 || steps < 0)
+    return -1;
+  for (int c = 0; c < chains; ++c)
+    if (!(x0[c] >= lo && x0[c] <= hi)) return -1;
+  const double two_s2 = 2.0 * sigma * sigma;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int c = 0; c < chains; ++c) {
+    double* z = (double*)malloc(sizeof(double) * d);
+    double* yh = (double*)malloc(sizeof(double) * r);
+    memcpy(z, z0, sizeof(double) * d);
+    double x = x0[c];
+    z[dim] = x;
+    double e = f_obs - mcmc_emulate(X, n, d, nbr, ld, C, k, r, kp, z, yh, col);
+    int64_t acc = 0;
+    for (int64_t t = 0; t < steps; ++t) {
+      const int64_t at = t * chains + c;
+      const double xp = x + step * noise[at];
+      double mg = -INFINITY;
+      if (xp >= lo && xp <= hi) {
+        z[dim] = xp;
+        const double ep = f_obs - mcmc_emulate(X, n, d, nbr, ld, C, k, r, kp, z, yh, col);
+#if defined(ORACLE_MUTANT_MCMC_SIGN)
+        const double delta = (ep * ep - e * e) / two_s2;
+#elif defined(ORACLE_MUTANT_MCMC_NO_HALF)
+        const double delta = (e * e - ep * ep) / (sigma * sigma);
+#else
+        const double delta = (e * e - ep * ep) / two_s2;
+#endif
+        mg = delta + expo[at];
+        if (mg > 0) {
+          x = xp;
+          e = ep;
+          ++acc;
+        }
+      }
+      samples[at] = x;
+      if (margin) margin[at] = mg;
+    }
+    if (accepted) accepted[c] = acc;
+    free(z);
+    free(yh);
+  }
+  return 0;
 }
 
 void fmgp_oracle_set_threads(int t) {

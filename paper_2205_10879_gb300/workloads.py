@@ -19,7 +19,11 @@ with the paper's shapes):
            (stands in for the 400-D star-galaxy images of Sec. 4.3)
   large    n=10,000,000 m=1,000,000 d=3, 50 random Fourier features + N(0, 0.02^2),
            Matern nu=2.5, rho=0.1, tau^2=1e-5, k=64
-Seeds: workload number c (tiny=1, spatial=2, highdim=3, large=4, serving=5)
+  borehole n=100,000 m=20,000 d=8 (4 varying), the borehole flow function of
+           Sec. 4.2 on a Latin hypercube, inputs pre-scaled per coordinate, RBF,
+           k=150; also the MCMC calibration target of Sec. 4.2 (r_w = 0.09)
+Seeds: workload number c (tiny=1, spatial=2, highdim=3, large=4, serving=5,
+borehole=6)
 uses 1000c for X, +1 noise, +2 Z, +3 Fourier features / linear map, +4 the
 LOOCV batch, +5 held-out test noise.
 """
@@ -28,7 +32,7 @@ from typing import Optional
 
 import numpy as np
 
-WORKLOAD_IDS = {"tiny": 1, "spatial": 2, "highdim": 3, "large": 4, "serving": 5}
+WORKLOAD_IDS = {"tiny": 1, "spatial": 2, "highdim": 3, "large": 4, "serving": 5, "borehole": 6}
 
 
 @dataclass
@@ -187,5 +191,59 @@ def serving_requests(models, count, seed=5005, max_points=65_536):
     return out
 
 
+# Borehole flow (Sec. 4.2).  Physical inputs in the order r_w, r, T_u, H_u,
+# T_l, H_l, L, K_w with the ranges the paper lists; flow in m^3/yr.
+BOREHOLE_LO = np.array([0.05, 100.0, 63070.0, 990.0, 63.1, 700.0, 1120.0, 9855.0])
+BOREHOLE_HI = np.array([0.15, 50000.0, 115600.0, 1110.0, 116.0, 820.0, 1680.0, 12045.0])
+# per-coordinate divisors that make the model anisotropic (Sec. 4.2)
+BOREHOLE_SCALE = np.array([0.0625, 0.25, 1.0, 0.25, 0.5, 0.25, 0.125, 0.5])
+BOREHOLE_VARYING = (0, 1, 2, 4)        # r_w, r, T_u, T_l; the rest sit at mid-range
+
+
+def borehole_flow(P):
+    """The borehole function on physical inputs P (N x 8)."""
+    rw, r, tu, hu, tl, hl, ln, kw = (P[:, j] for j in range(8))
+    lg = np.log(r / rw)
+    return 2.0 * np.pi * tu * (hu - hl) / (lg * (1.0 + 2.0 * ln * tu / (lg * rw * rw * kw) + tu / tl))
+
+
+def borehole_unit_to_model(U):
+    """Unit-cube coordinates (N x 8) -> model inputs (each column divided by its scale)."""
+    return U / BOREHOLE_SCALE
+
+
+def borehole_unit_to_physical(U):
+    return BOREHOLE_LO + U * (BOREHOLE_HI - BOREHOLE_LO)
+
+
+def borehole(n=100_000, m=20_000, k=150, b=10_000, length_scale=43.27, nugget=1e-8):
+    """One Latin hypercube of n + m points over the four varying inputs (the
+    fixed four at mid-range), split at random into n training and m test
+    points; responses centred by the training mean.  extra holds the MCMC
+    calibration target: r_w = 0.09 (unit coordinate 0.4) with the other
+    inputs at mid-range, its centred flow, and the base model input z0."""
+    c = 6
+    N = n + m
+    g = _rng(c, 0)
+    U = np.full((N, 8), 0.5)
+    for j in BOREHOLE_VARYING:
+        U[:, j] = (g.permutation(N) + g.random(N)) / N
+    perm = _rng(c, 2).permutation(N)
+    tr, te = np.sort(perm[:n]), np.sort(perm[n:])
+    f = borehole_flow(borehole_unit_to_physical(U))
+    mean = float(f[tr].mean())
+    X = borehole_unit_to_model(U[tr])
+    Z = borehole_unit_to_model(U[te])
+    u_true = np.full((1, 8), 0.5)
+    u_true[0, 0] = (0.09 - BOREHOLE_LO[0]) / (BOREHOLE_HI[0] - BOREHOLE_LO[0])
+    f_obs = float(borehole_flow(borehole_unit_to_physical(u_true))[0]) - mean
+    extra = {"y_mean": mean, "u_true": float(u_true[0, 0]), "f_obs": f_obs,
+             "z0": borehole_unit_to_model(u_true)[0], "dim": 0,
+             "lo": 0.0, "hi": 1.0 / BOREHOLE_SCALE[0], "scale": float(BOREHOLE_SCALE[0])}
+    return Workload("borehole", X, (f[tr] - mean)[:, None], Z, (f[te] - mean)[:, None], k,
+                    KernelSpec("rbf", 0.0, length_scale, 1.0, nugget), _batch(c, n, b), extra)
+
+
 def by_name(name, **kw):
-    return {"tiny": tiny, "spatial": spatial, "highdim": highdim, "large": large}[name](**kw)
+    return {"tiny": tiny, "spatial": spatial, "highdim": highdim, "large": large,
+            "borehole": borehole}[name](**kw)

@@ -19,6 +19,8 @@ PIN_CALLS = [
     ("interpolation", pins.test_interpolation_identity),
     ("loo_identity", pins.test_loo_identity_links_loocv_to_precompute),
     ("sigma2", pins.test_sigma2_invariance),
+    ("mcmc_posterior", lambda: [pins.test_mcmc_reproduces_the_closed_form_posterior(f) for f in (1.5, 0.15)]),
+    ("mcmc_greedy", pins.test_mcmc_takes_only_strictly_better_moves_when_expo_is_zero),
 ]
 
 MUTANTS = {
@@ -30,6 +32,8 @@ MUTANTS = {
     "ORACLE_MUTANT_LOO_SIGN": "LOO residual sign flipped",
     "ORACLE_MUTANT_BACKSOLVE_TRANSPOSE": "back substitution with L instead of L^T",
     "ORACLE_MUTANT_TIE_HIGH": "distance ties to the highest index",
+    "ORACLE_MUTANT_MCMC_SIGN": "Metropolis log ratio with the sign flipped",
+    "ORACLE_MUTANT_MCMC_NO_HALF": "Gaussian log likelihood without the 1/2",
 }
 
 

@@ -16,6 +16,11 @@ Each pin is chosen so that a plausible slip in the oracle fails it:
    precomputed C (Eq. 6).
  - sigma^2 invariance of the mean and 1/sigma^2 scaling of C.
  - Long-double re-evaluation bounds the FP64 rounding error.
+ - Metropolis calibration (Sec. 4.2): with a linear response the posterior of
+   the calibrated input is a (truncated) Gaussian in closed form, which the
+   chains must reproduce (sign, factor 1/2, prior rejection); with Exp(1)
+   draws fixed at 0 the chain only takes strictly better moves; with them at
+   +inf every in-range proposal is taken and the others rejected.
 """
 import numpy as np
 import pytest
@@ -253,3 +258,84 @@ def test_muygps_equals_fastmuygps_at_training_points():
     np.testing.assert_array_equal(N[:, 0], rows)
     np.testing.assert_array_equal(N[:, 1:], nbr[rows])
     np.testing.assert_allclose(ym, yf, rtol=1e-9, atol=1e-12)
+
+
+# ------------------------------------------------------------------ MCMC --
+def _linear_emulator(slope=3.0):
+    """A 1-D emulator of y = slope * x on [0, 1]: dense training grid, so the
+    posterior mean reproduces the line to ~1e-6."""
+    X = np.linspace(0.0, 1.0, 201)[:, None]
+    Y = slope * X
+    kern = oracle.kernel("rbf", 0.0, 0.05, 1.0, 1e-10)
+    nbr, _ = oracle.self_knn(X, 11)
+    C, st = oracle.precompute(X, Y, nbr, 12, kern)
+    assert not st.any()
+    yh, _ = oracle.predict(X, nbr, C, kern, np.array([[0.25], [0.5], [0.75]]))
+    np.testing.assert_allclose(yh[:, 0], slope * np.array([0.25, 0.5, 0.75]), atol=1e-5)
+    return X, nbr, C, kern
+
+
+def _draws(seed, steps, chains):
+    g = np.random.default_rng(seed)
+    return g.standard_normal((steps, chains)), g.exponential(1.0, (steps, chains))
+
+
+@pytest.mark.parametrize("f_obs", [1.5, 0.15])
+def test_mcmc_reproduces_the_closed_form_posterior(f_obs):
+    """Likelihood N(f_obs; 3x, 0.3^2) and a uniform prior on [0, 1]: the
+    posterior of x is N(f_obs/3, 0.1^2) truncated to [0, 1].  f_obs = 1.5
+    puts the mode mid-range; 0.15 puts it half a standard deviation from the
+    lower bound, where the truncation moves the mean to about 0.1009."""
+    from scipy.stats import truncnorm
+    X, nbr, C, kern = _linear_emulator()
+    slope, sig = 3.0, 0.3
+    mu, sd = f_obs / slope, sig / slope
+    ref = truncnorm((0.0 - mu) / sd, (1.0 - mu) / sd, loc=mu, scale=sd)
+    steps, chains, burn = 25_000, 16, 500
+    noise, expo = _draws(77, steps, chains)
+    x0 = np.linspace(0.2, 0.8, chains)
+    S, acc, _ = oracle.mcmc(X, nbr, C, kern, [0.0], 0, 0.0, 1.0, f_obs, sig, 0.25, x0, noise,
+                            expo)
+    post = S[burn:].ravel()
+    assert post.min() >= 0.0 and post.max() <= 1.0
+    assert abs(post.mean() - ref.mean()) < 4e-3
+    assert abs(post.std() / ref.std() - 1.0) < 0.04
+    rate = acc.sum() / (steps * chains)
+    assert 0.2 < rate < 0.8
+
+
+def test_mcmc_takes_only_strictly_better_moves_when_expo_is_zero():
+    X, nbr, C, kern = _linear_emulator()
+    steps, chains = 300, 4
+    noise, _ = _draws(78, steps, chains)
+    expo = np.zeros_like(noise)
+    x0 = np.array([0.05, 0.3, 0.7, 0.95])
+    S, acc, margin = oracle.mcmc(X, nbr, C, kern, [0.0], 0, 0.0, 1.0, 1.2, 0.3, 0.1, x0, noise,
+                                 expo)
+    path = np.vstack([x0[None, :], S])
+    yh, _ = oracle.predict(X, nbr, C, kern, path.reshape(-1, 1))
+    err = np.abs(1.2 - yh[:, 0]).reshape(path.shape)
+    moved = path[1:] != path[:-1]
+    assert np.all(err[1:][moved] < err[:-1][moved])
+    assert np.all(err[1:][~moved] == err[:-1][~moved])
+    assert np.all(margin[moved] > 0) and np.all(margin[~moved] <= 0)
+    assert np.array_equal(acc, moved.sum(axis=0))
+    assert np.all(np.abs(path[-1] - 0.4) < 0.02)
+
+
+def test_mcmc_with_infinite_expo_takes_every_in_range_proposal():
+    X, nbr, C, kern = _linear_emulator()
+    steps, chains = 200, 3
+    noise, _ = _draws(79, steps, chains)
+    expo = np.full_like(noise, np.inf)
+    x0 = np.array([0.1, 0.5, 0.9])
+    S, acc, margin = oracle.mcmc(X, nbr, C, kern, [0.0], 0, 0.0, 1.0, 1.5, 0.3, 0.2, x0, noise,
+                                 expo)
+    x = x0.copy()
+    for t in range(steps):
+        prop = x + 0.2 * noise[t]
+        ok = (prop >= 0.0) & (prop <= 1.0)
+        x = np.where(ok, prop, x)
+        np.testing.assert_array_equal(S[t], x)
+        assert np.all(np.isneginf(margin[t][~ok]))
+    assert np.array_equal(acc, (S != np.vstack([x0[None, :], S[:-1]])).sum(axis=0))
