@@ -8,7 +8,8 @@ with paper_2205_10879_gb300 (the CUDA path) and imports nothing from it.
 Parity pins live in tests/test_oracle_pins.py (closed forms vs the Bessel form
 of Eq. 3, brute-force kNN vs an all-pairs sort, SPD blocks, k = n vs the dense
 GP mean of Eq. 2, interpolation and leave-one-out identities, sigma^2
-invariance, long-double rounding bound).  Parity against numbers printed in
+invariance, long-double rounding bound, the Metropolis calibration chain of
+Sec. 4.2 against the closed-form posterior of a linear response).  Parity against numbers printed in
 the paper is unpinned: the paper prints no worked example.
 """
 import ctypes
