@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-muygps", action="store_true")
     p.add_argument("--no-highdim", action="store_true")
+    p.add_argument("--no-borehole", action="store_true")
+    p.add_argument("--mcmc-chains", type=int, default=8192)
+    p.add_argument("--mcmc-steps", type=int, default=1221)
     return p.parse_args()
 
 
@@ -384,6 +387,8 @@ def run_ours(a):
     }
     if not a.no_highdim:
         line["highdim_knn"] = highdim_knn_bench(a, dev, steps=a.steps, warmup=1)
+    if not a.no_borehole:
+        line["borehole"] = borehole_bench(a, dev)
     if not a.no_serving:
         line["serving"] = serving_bench(a, dev)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
@@ -432,6 +437,82 @@ def highdim_knn_bench(a, dev, steps, warmup):
             "uncertified_queries": fb.diag_counter(2),
             "roofline_call": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                               "frac": ach / peak, "note": "whole call incl. pack/select/re-rank"}}
+
+
+# ------------------------------------------------- borehole + MCMC (4.2) ----
+def _timed(fn, dev):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def borehole_bench(a, dev):
+    """The borehole emulator of Sec. 4.2 (Table 1): n = 100,000 training and
+    m = 20,000 test points, 8 inputs (4 varying), RBF rho = 43.27, k = 150,
+    FP64 path (the near-flat kernel puts the blocks far beyond FP32's reach).
+    Times kNN, precompute, the test-set prediction (the paper's 0.109 s on a
+    P100) and plain MuyGPs prediction (its 1.32 s), RMSE against the exact
+    flow; then the MCMC calibration of r_w from the flow at r_w = 0.09:
+    chains x steps Metropolis samples (10^7 by default) on the device."""
+    import torch
+    from paper_2205_10879_gb300 import _binding as fb
+    from paper_2205_10879_gb300 import workloads as wl
+    W = wl.borehole()
+    kern = W.kernel
+    gk = fb.make_kernel(kern.kind, kern.nu, kern.length_scale, kern.variance, kern.nugget)
+    X, Y, Z = (torch.from_numpy(v).to(dev) for v in (W.X, W.Y, W.Z))
+    k = W.k
+    fb.fmgp_build_knn(X, k - 1)  # warm-up (module load, pools)
+    (nbr, _), ms_knn = _timed(lambda: fb.fmgp_build_knn(X, k - 1), dev)
+    (C, st), ms_pre = _timed(lambda: fb.fmgp_precompute(X, Y, nbr, k, gk, fb.PREC_FP64), dev)
+    fb.fmgp_predict(X, nbr, C, k, gk, Z, fb.PREC_FP64)
+    (yh, _), ms_pred = _timed(lambda: fb.fmgp_predict(X, nbr, C, k, gk, Z, fb.PREC_FP64), dev)
+    rmse = float(np.sqrt(np.mean((yh.cpu().numpy() - W.Ztrue) ** 2)))
+    (ym, _), ms_muy = _timed(lambda: fb.fmgp_muygps_predict(X, Y, Z, k, gk, fb.PREC_FP64), dev)
+    rmse_muy = float(np.sqrt(np.mean((ym.cpu().numpy() - W.Ztrue) ** 2)))
+    (_, stm), ms_pre_mixed = _timed(lambda: fb.fmgp_precompute(X, Y, nbr, k, gk, fb.PREC_MIXED), dev)
+    out = {"workload": "borehole n=100000 m=20000 d=8 k=150 rbf rho=43.27 tau2=1e-8",
+           "knn_ms": ms_knn, "precompute_ms": ms_pre, "predict_ms": ms_pred,
+           "predictions_per_s": W.m / (ms_pred * 1e-3), "rmse": rmse,
+           "paper_predict_s": 0.109, "paper_rmse": 1.12e-2,
+           "muygps_predict_ms": ms_muy, "muygps_rmse": rmse_muy, "paper_muygps_predict_s": 1.32,
+           "not_spd_blocks": int((st.cpu().numpy() == 1).sum()),
+           "mixed_precompute_ms": ms_pre_mixed,
+           "mixed_block_status": {str(v): int(c) for v, c in
+                                  zip(*np.unique(stm.cpu().numpy(), return_counts=True))}}
+    # MCMC calibration of r_w (coordinate 0): prior uniform over its range
+    e = W.extra
+    model = fb.FmgpModel(X, nbr, C, k, gk, fb.PREC_FP64)
+    chains, steps = a.mcmc_chains, a.mcmc_steps
+    g = torch.Generator(device=dev)
+    g.manual_seed(6006)
+    noise = torch.randn((steps, chains), generator=g, dtype=torch.float64, device=dev)
+    expo = torch.empty((steps, chains), dtype=torch.float64, device=dev).exponential_(1.0, generator=g)
+    x0 = np.random.default_rng(6007).uniform(e["lo"], e["hi"], chains)
+    sigma, step = 1.0, 0.3
+    w = max(1, min(steps, 8))
+    model.mcmc(e["z0"], e["dim"], e["lo"], e["hi"], e["f_obs"], sigma, step, x0, noise[:w].contiguous(),
+               expo[:w].contiguous())
+    (S, acc, _), ms_mcmc = _timed(lambda: model.mcmc(e["z0"], e["dim"], e["lo"], e["hi"], e["f_obs"],
+                                                     sigma, step, x0, noise, expo), dev)
+    burn = min(200, steps // 2)
+    post = S[burn:] * e["scale"]  # unit-cube coordinate of r_w
+    mean_u = float(post.mean())
+    out["mcmc"] = {"chains": chains, "steps": steps, "samples": chains * steps, "ms": ms_mcmc,
+                   "samples_per_s": chains * steps / (ms_mcmc * 1e-3),
+                   "accept_rate": float(acc.sum().item()) / (chains * steps),
+                   "posterior_mean_unit": mean_u, "posterior_sd_unit": float(post.std()),
+                   "truth_unit": e["u_true"], "rel_error": abs(mean_u - e["u_true"]) / e["u_true"],
+                   "paper_posterior_mean_unit": 0.3998, "burn_in_steps": burn,
+                   "sigma_obs": sigma, "proposal_sd": step}
+    model.close()
+    return out
 
 
 # ------------------------------------------------------------- serving ----

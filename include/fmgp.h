@@ -217,6 +217,41 @@ int fmgp_model_destroy(fmgp_model* model);
 /* Device bytes owned by the model (grid + double-float copy), -1 for NULL. */
 int64_t fmgp_model_device_bytes(const fmgp_model* model);
 
+/*
+ * fmgp_model_mcmc -- Metropolis calibration of one model input against one
+ * observation, the model's posterior mean (Eq. 7) as the emulator (Sec. 4.2:
+ * recovering the borehole radius from an observed flow by MCMC).
+ *
+ * The emulator input of a chain in state x is z0 (d doubles, HOST) with
+ * coordinate `dim` replaced by x.  Prior: uniform on [lo, hi].  Likelihood:
+ * Gaussian, standard deviation sigma, of the observation f_obs of response
+ * column `col`.  `chains` independent random-walk chains advance together;
+ * chain c starts at x0[c] (HOST, chains doubles, each inside [lo, hi]) and its
+ * step t (0 <= t < steps) does, in FP64 with every operation rounded as written:
+ *   x' = x + step * noise[t * chains + c]
+ *   rejected when x' < lo or x' > hi (zero prior density); otherwise
+ *   e = f_obs - yhat(x)[col], e' = f_obs - yhat(x')[col],
+ *   delta = (e*e - e'*e') / (2 * sigma * sigma),
+ *   accepted iff delta + expo[t * chains + c] > 0.
+ * With expo = -log u this is the usual test u < exp(delta).  The random draws
+ * are inputs: noise (N(0,1)) and expo (Exp(1)) are DEVICE arrays of
+ * steps x chains doubles, step-major.
+ *
+ * Outputs (DEVICE, caller-owned, each may be NULL): samples_out (steps x
+ * chains doubles, the state after each step, step-major), accepted_out
+ * (chains int64, accepted moves), x_out (chains doubles, final state).
+ * Every step emulates all chains at once (nearest training point + gather-
+ * dot), so the work per step is that of fmgp_model_predict with m = chains.
+ * Errors: FMGP_EINVAL for a NULL model or z0, dim or col out of range,
+ * non-finite or inverted bounds, sigma <= 0, non-finite step, f_obs or z0,
+ * an x0 outside [lo, hi], missing draws; FMGP_ENOMEM for workspace.
+ * Asynchronous on `stream` (x0 and z0 are read before the call returns).
+ */
+int fmgp_model_mcmc(fmgp_model* model, const double* z0, int32_t dim, double lo, double hi,
+                    double f_obs, int32_t col, double sigma, double step, int64_t chains,
+                    int64_t steps, const double* x0, const double* noise, const double* expo,
+                    double* samples_out, int64_t* accepted_out, double* x_out, void* stream);
+
 typedef struct fmgp_server fmgp_server;
 
 typedef struct {

@@ -99,6 +99,8 @@ def load(build_if_missing=True):
     lib.fmgp_model_destroy.argtypes = [P]
     lib.fmgp_model_device_bytes.argtypes = [P]
     lib.fmgp_model_device_bytes.restype = I64
+    D = ctypes.c_double
+    lib.fmgp_model_mcmc.argtypes = [P, P, I32, D, D, D, I32, D, D, I64, I64, P, P, P, P, P, P, P]
     lib.fmgp_server_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I32,
                                        ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]
     lib.fmgp_server_submit.argtypes = [P, I32, P, I64, P, P, ctypes.POINTER(ctypes.c_uint64)]
@@ -312,6 +314,37 @@ class FmgpModel:
 
     def device_bytes(self):
         return int(load().fmgp_model_device_bytes(self.handle))
+
+    def mcmc(self, z0, dim, lo, hi, f_obs, sigma, step, x0, noise, expo, col=0,
+             samples_out=None, accepted_out=None, x_out=None, with_samples=True, stream=None):
+        """fmgp_model_mcmc: z0 (d) and x0 (chains) host arrays; noise and expo
+        CUDA tensors (steps x chains FP64).  Returns (samples steps x chains or
+        None, accepted per chain, final states), all on the device."""
+        import numpy as np
+        z0 = np.ascontiguousarray(z0, dtype=np.float64)
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        _dev(noise, "noise"); _dev(expo, "expo")
+        if noise.dtype != torch.float64 or expo.dtype != torch.float64:
+            raise TypeError("noise and expo must be float64")
+        steps, chains = noise.shape
+        if tuple(expo.shape) != (steps, chains) or x0.shape[0] != chains:
+            raise ValueError("noise, expo must be steps x chains and x0 must have chains entries")
+        if z0.shape[0] != self.d:
+            raise ValueError("z0 must have d entries")
+        dev = noise.device
+        if with_samples and samples_out is None:
+            samples_out = torch.empty((steps, chains), dtype=torch.float64, device=dev)
+        if accepted_out is None:
+            accepted_out = torch.empty(chains, dtype=torch.int64, device=dev)
+        if x_out is None:
+            x_out = torch.empty(chains, dtype=torch.float64, device=dev)
+        _check(load().fmgp_model_mcmc(self.handle, z0.ctypes.data_as(ctypes.c_void_p), int(dim),
+                                      float(lo), float(hi), float(f_obs), int(col), float(sigma),
+                                      float(step), int(chains), int(steps),
+                                      x0.ctypes.data_as(ctypes.c_void_p), _ptr(noise), _ptr(expo),
+                                      _ptr(samples_out if with_samples else None),
+                                      _ptr(accepted_out), _ptr(x_out), _stream(stream)))
+        return samples_out if with_samples else None, accepted_out, x_out
 
     def close(self):
         if self.handle:

@@ -10,7 +10,7 @@ namespace fmgp {
 
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxK = 128;  // largest neighbourhood a block kernel handles
+constexpr int kMaxK = 160;  // largest neighbourhood a block kernel handles (5 slots of 32)
 
 // Kernel hyperparameters as the device sees them.  phi(D) is the correlation
 // at squared distance D (Eq. 3; RBF as its nu -> infinity limit).

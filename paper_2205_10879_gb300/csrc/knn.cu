@@ -3,6 +3,8 @@
 //            Chebyshev distance with box pruning and an exact stop test.
 //   d >= 4 : tiled scan of all training points; a CTA of 8 warps (8 queries)
 //            stages 32 candidate rows at a time in shared memory as FP32.
+//   nearest point only, 4 <= d <= 15: one thread per query over slices of
+//            the training points, then a minimum over the slices.
 // Both rank on the canonical FP64 key; FP32 is used only for lower bounds.
 #include "knn.cuh"
 #include "topk.cuh"
@@ -235,7 +237,8 @@ int launch_grid_self(const GridView& gv, int kq, int32_t* nbr, double* dist, cud
   if (kq <= 32) FMGP_LAUNCH(knn_grid_self_kernel<D, 1><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
   else if (kq <= 64) FMGP_LAUNCH(knn_grid_self_kernel<D, 2><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
   else if (kq <= 96) FMGP_LAUNCH(knn_grid_self_kernel<D, 3><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
-  else FMGP_LAUNCH(knn_grid_self_kernel<D, 4><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
+  else if (kq <= 128) FMGP_LAUNCH(knn_grid_self_kernel<D, 4><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
+  else FMGP_LAUNCH(knn_grid_self_kernel<D, 5><<<blocks, 256, 0, s>>>(gv, kq, nbr, dist));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
@@ -247,7 +250,8 @@ int launch_grid_query(const GridView& gv, const T* Q, int64_t m, int kq, int32_t
   if (kq <= 32) FMGP_LAUNCH((knn_grid_query_kernel<D, 1, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
   else if (kq <= 64) FMGP_LAUNCH((knn_grid_query_kernel<D, 2, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
   else if (kq <= 96) FMGP_LAUNCH((knn_grid_query_kernel<D, 3, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
-  else FMGP_LAUNCH((knn_grid_query_kernel<D, 4, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
+  else if (kq <= 128) FMGP_LAUNCH((knn_grid_query_kernel<D, 4, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
+  else FMGP_LAUNCH((knn_grid_query_kernel<D, 5, T><<<blocks, 256, 0, s>>>(gv, Q, m, kq, idx, key)));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
@@ -270,22 +274,151 @@ int launch_brute_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, 
 }
 
 template <typename T>
+int launch_brute_mx(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
+                    const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
+                    const int* qlist = nullptr, const int* qcount = nullptr) {
+  if (kq <= 32) return launch_brute_t<T, 1>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 64) return launch_brute_t<T, 2>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 96) return launch_brute_t<T, 3>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 128) return launch_brute_t<T, 4>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  return launch_brute_t<T, 5>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+}
+
+template <typename T>
 int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
                  Workspace& ws, int32_t* idx, double* key, cudaStream_t s,
                  const int* qlist = nullptr, const int* qcount = nullptr) {
   unsigned int* mx = ws.get<unsigned int>(1);
   if (!mx) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), s));
-  const int blocks = (int)std::min<int64_t>(ceil_div(n * d, 256), (int64_t)num_sms() * 8);
-  FMGP_LAUNCH(maxabs_kernel<<<blocks, 256, 0, s>>>(X, sizeof(T) == 8, n * d, mx));
-  if (Q != X) {
-    const int qb = (int)std::min<int64_t>(ceil_div(m * d, 256), (int64_t)num_sms() * 8);
-    if (m > 0) FMGP_LAUNCH(maxabs_kernel<<<qb, 256, 0, s>>>(Q, sizeof(T) == 8, m * d, mx));
+  int rc = maxabs_into(X, sizeof(T) == 8, n * d, mx, s);
+  if (!rc && Q != X) rc = maxabs_into(Q, sizeof(T) == 8, m * d, mx, s);
+  if (rc) return rc;
+  return launch_brute_mx<T>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+}
+
+// ------------------------------------------- nearest point, 4 <= d < 16 --
+// One thread per query keeps the query in registers; CTA (x, y) scans slice
+// y of the training points, staged kNnTile rows at a time in shared memory as
+// FP32 and read by all threads at the same address.  The FP32 lower bound is
+// the exhaustive scan's; a candidate whose bound does not exceed the current
+// best gets its canonical FP64 key.  Each slice's exact (key, index) minimum
+// goes to part; nn1_merge_kernel takes the minimum over slices.
+constexpr int kNnThreads = 128;
+constexpr int kNnTile = 256;
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kNnThreads) nn1_scan_kernel(
+    const T* __restrict__ X, int64_t n, const T* __restrict__ Q, int64_t m,
+    const unsigned int* maxabs_bits, int64_t slice, unsigned long long* part_key,
+    int* part_idx) {
+  __shared__ __align__(16) float tile[kNnTile * D];
+  const int64_t q = blockIdx.x * (int64_t)kNnThreads + threadIdx.x;
+  const bool qv = q < m;
+  const int64_t c0 = (int64_t)blockIdx.y * slice;
+  const int64_t c1 = min(n, c0 + slice);
+  const float M = __uint_as_float(*maxabs_bits);
+  const float cerr = (sizeof(T) == 8) ? 2.5f * kU * M : 0.f;
+  const float rel = 1.0f - (2.0f * D + 8.0f) * kU;
+  float qf[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) qf[j] = qv ? (float)Q[q * D + j] : 0.f;
+  unsigned long long best = ~0ull;
+  int bi = INT_MAX;
+  float bup = __int_as_float(0x7f800000);
+  for (int64_t base = c0; base < c1; base += kNnTile) {
+    const int rows = (int)min((int64_t)kNnTile, c1 - base);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * D; e += kNnThreads) tile[e] = (float)X[base * D + e];
+    __syncthreads();
+    if (!qv) continue;
+    for (int rr = 0; rr < rows; ++rr) {
+      const float* xr = tile + rr * D;
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float t = fabsf(qf[j] - xr[j]) * (1.0f - 2.0f * kU) - cerr;
+        t = fmaxf(t, 0.f);
+        acc = fmaf(t, t, acc);
+      }
+      if (acc * rel <= bup) {
+        const int64_t cand = base + rr;
+        const T* xg = X + cand * D;
+        const T* qg = Q + q * D;
+        double t = __dsub_rn((double)qg[0], (double)xg[0]);
+        double sum = __dmul_rn(t, t);
+#pragma unroll
+        for (int j = 1; j < D; ++j) {
+          t = __dsub_rn((double)qg[j], (double)xg[j]);
+          sum = __dadd_rn(sum, __dmul_rn(t, t));
+        }
+        const unsigned long long ck = dbits(sum);
+        if (key_less(ck, (int)cand, best, bi)) {
+          best = ck;
+          bi = (int)cand;
+          bup = key_bits_to_float_up(best);
+        }
+      }
+    }
   }
-  if (kq <= 32) return launch_brute_t<T, 1>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 64) return launch_brute_t<T, 2>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 96) return launch_brute_t<T, 3>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  return launch_brute_t<T, 4>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (qv) {
+    part_key[q * gridDim.y + blockIdx.y] = best;
+    part_idx[q * gridDim.y + blockIdx.y] = bi;
+  }
+}
+
+__global__ void nn1_merge_kernel(const unsigned long long* part_key, const int* part_idx,
+                                 int64_t m, int slices, int32_t* nearest) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  unsigned long long bk = part_key[q * slices];
+  int bi = part_idx[q * slices];
+  for (int y = 1; y < slices; ++y) {
+    const unsigned long long k = part_key[q * slices + y];
+    const int i = part_idx[q * slices + y];
+    if (key_less(k, i, bk, bi)) { bk = k; bi = i; }
+  }
+  nearest[q] = bi;
+}
+
+template <typename T, int D>
+int launch_nn1_scan(const T* X, int64_t n, const T* Q, int64_t m, const unsigned int* mx,
+                    int32_t* nearest, Workspace& ws, cudaStream_t s) {
+  const int qblocks = ceil_div(m, kNnThreads);
+  // about eight CTAs per SM in total, slices of at least 2048 rows
+  int slices = (int)std::max<int64_t>(1, ((int64_t)num_sms() * 8 + qblocks - 1) / qblocks);
+  slices = (int)std::min<int64_t>(slices, std::max<int64_t>(1, n / 2048));
+  const int64_t slice = (n + slices - 1) / slices;
+  unsigned long long* pk = ws.get<unsigned long long>((size_t)m * slices);
+  int* pi = ws.get<int>((size_t)m * slices);
+  if (!pk || !pi) return FMGP_ENOMEM;
+  FMGP_LAUNCH((nn1_scan_kernel<T, D><<<dim3((unsigned)qblocks, (unsigned)slices), kNnThreads, 0, s>>>(
+      X, n, Q, m, mx, slice, pk, pi)));
+  FMGP_LAUNCH(nn1_merge_kernel<<<ceil_div(m, 256), 256, 0, s>>>(pk, pi, m, slices, nearest));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
+template <typename T>
+int nn1_scan_t(const T* X, int64_t n, int d, const T* Q, int64_t m, const unsigned int* mx,
+               int32_t* nearest, Workspace& ws, cudaStream_t s) {
+  switch (d) {
+    case 4: return launch_nn1_scan<T, 4>(X, n, Q, m, mx, nearest, ws, s);
+    case 5: return launch_nn1_scan<T, 5>(X, n, Q, m, mx, nearest, ws, s);
+    case 6: return launch_nn1_scan<T, 6>(X, n, Q, m, mx, nearest, ws, s);
+    case 7: return launch_nn1_scan<T, 7>(X, n, Q, m, mx, nearest, ws, s);
+    case 8: return launch_nn1_scan<T, 8>(X, n, Q, m, mx, nearest, ws, s);
+    case 9: return launch_nn1_scan<T, 9>(X, n, Q, m, mx, nearest, ws, s);
+    case 10: return launch_nn1_scan<T, 10>(X, n, Q, m, mx, nearest, ws, s);
+    case 11: return launch_nn1_scan<T, 11>(X, n, Q, m, mx, nearest, ws, s);
+    case 12: return launch_nn1_scan<T, 12>(X, n, Q, m, mx, nearest, ws, s);
+    case 13: return launch_nn1_scan<T, 13>(X, n, Q, m, mx, nearest, ws, s);
+    case 14: return launch_nn1_scan<T, 14>(X, n, Q, m, mx, nearest, ws, s);
+    case 15: return launch_nn1_scan<T, 15>(X, n, Q, m, mx, nearest, ws, s);
+    default:
+      set_error("nearest-point scan: d = %d outside [4, %d]", d, kNn1ScanMaxD);
+      return FMGP_EUNSUPPORTED;
+  }
 }
 
 }  // namespace
@@ -338,6 +471,43 @@ int knn_query(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, 
     return launch_grid_query<3>(gv, q, m, kq, idx, key, stream);
   }
   return knn_query_brute(X, dtype, n, d, Q, m, kq, idx, key, ws, stream);
+}
+
+int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaStream_t s) {
+  if (count <= 0) return FMGP_OK;
+  const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), (int64_t)num_sms() * 8);
+  FMGP_LAUNCH(maxabs_kernel<<<blocks, 256, 0, s>>>(X, f64, count, mx));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
+int knn_query_brute_mx(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q,
+                       int64_t m, int kq, const unsigned int* mx, int32_t* idx, double* key,
+                       cudaStream_t stream) {
+  if (m == 0) return FMGP_OK;
+  if (dtype == FMGP_F64)
+    return launch_brute_mx<double>((const double*)X, n, d, (const double*)Q, m, kq, 0, mx, idx,
+                                   key, stream);
+  return launch_brute_mx<float>((const float*)X, n, d, (const float*)Q, m, kq, 0, mx, idx, key,
+                                stream);
+}
+
+int nearest_scan(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
+                 const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t stream) {
+  if (m == 0) return FMGP_OK;
+  if (!mx) {
+    unsigned int* own = ws.get<unsigned int>(1);
+    if (!own) return FMGP_ENOMEM;
+    FMGP_CUDA_TRY(cudaMemsetAsync(own, 0, sizeof(unsigned int), stream));
+    int rc = maxabs_into(X, dtype == FMGP_F64, n * d, own, stream);
+    if (!rc) rc = maxabs_into(Q, dtype == FMGP_F64, m * d, own, stream);
+    if (rc) return rc;
+    mx = own;
+  }
+  if (dtype == FMGP_F64)
+    return nn1_scan_t<double>((const double*)X, n, d, (const double*)Q, m, mx, nearest, ws,
+                              stream);
+  return nn1_scan_t<float>((const float*)X, n, d, (const float*)Q, m, mx, nearest, ws, stream);
 }
 
 int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,

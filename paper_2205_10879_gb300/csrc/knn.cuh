@@ -42,4 +42,21 @@ int tc_knn(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int
 int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
                     int kq, int32_t* idx, double* key, Workspace& ws, cudaStream_t stream);
 
+// atomicMax of max |X[i]| (FP32 bits, i < count) into *mx: the magnitude bound
+// whose rounding slack the exhaustive scan's FP32 lower bounds include.
+int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaStream_t s);
+
+// Exhaustive scan with the magnitude bound supplied: *mx must be at least
+// max |coordinate| over X and all of Q (FP32 bits, rounded up).
+int knn_query_brute_mx(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q,
+                       int64_t m, int kq, const unsigned int* mx, int32_t* idx, double* key,
+                       cudaStream_t stream);
+
+// Nearest training point (kq = 1) of each query by a thread-per-query scan,
+// for 4 <= d <= kNn1ScanMaxD.  mx: magnitude bound as for knn_query_brute_mx,
+// or null to compute it from X and Q.
+constexpr int kNn1ScanMaxD = 15;
+int nearest_scan(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
+                 const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t stream);
+
 }  // namespace fmgp

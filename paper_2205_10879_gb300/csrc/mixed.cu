@@ -228,7 +228,7 @@ __device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* 
 }
 
 template <int MODE, int NS, int CB>
-__global__ void __launch_bounds__(256, 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
+__global__ void __launch_bounds__(256, NS >= 5 ? 1 : 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
                                                           MixedLayout lay) {
   constexpr bool LOO = MODE == kModeLoocv;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -599,7 +599,8 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   auto kern_fn = S == 1 ? pick(std::integral_constant<int, 1>{})
                : S == 2 ? pick(std::integral_constant<int, 2>{})
                : S == 3 ? pick(std::integral_constant<int, 3>{})
-                        : pick(std::integral_constant<int, 4>{});
+               : S == 4 ? pick(std::integral_constant<int, 4>{})
+                        : pick(std::integral_constant<int, 5>{});
   FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
   FMGP_LAUNCH(kern_fn<<<blocks, warps * 32, smem, s>>>(a, mx, lay));
   FMGP_CUDA_TRY(cudaGetLastError());

@@ -80,27 +80,23 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
     // Cholesky, Crout order: step j forms column j of L
     for (int j = 0; j < k; ++j) {
       const double* lj = L + j * ldl;
-      const int r0 = lane, r1 = lane + 32, r2 = lane + 64, r3 = lane + 96;
-      double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
-      if (r0 >= j && r0 < k) {
-        const double* lr = L + r0 * ldl;
-        for (int p = 0; p < j; ++p) d0 = fma(lr[p], lj[p], d0);
-      }
-      if (r1 >= j && r1 < k) {
-        const double* lr = L + r1 * ldl;
-        for (int p = 0; p < j; ++p) d1 = fma(lr[p], lj[p], d1);
-      }
-      if (r2 >= j && r2 < k) {
-        const double* lr = L + r2 * ldl;
-        for (int p = 0; p < j; ++p) d2 = fma(lr[p], lj[p], d2);
-      }
-      if (r3 >= j && r3 < k) {
-        const double* lr = L + r3 * ldl;
-        for (int p = 0; p < j; ++p) d3 = fma(lr[p], lj[p], d3);
+      // rows lane + 32 s of column j: dot of the finished part of the row
+      double dd[kMaxSlots];
+#pragma unroll
+      for (int s = 0; s < kMaxSlots; ++s) {
+        const int row = lane + 32 * s;
+        dd[s] = 0.0;
+        if (row >= j && row < k) {
+          const double* lr = L + row * ldl;
+          for (int p = 0; p < j; ++p) dd[s] = fma(lr[p], lj[p], dd[s]);
+        }
       }
       if (lane == (j & 31)) {
         const int sj = j >> 5;
-        const double dj = sj == 0 ? d0 : (sj == 1 ? d1 : (sj == 2 ? d2 : d3));
+        double dj = dd[0];
+#pragma unroll
+        for (int s = 1; s < kMaxSlots; ++s)
+          if (s == sj) dj = dd[s];
         const double v = L[j * ldl + j] - dj;
         if (!(v > 0.0)) {
           *flag = 1;
@@ -113,10 +109,11 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
       __syncwarp();
       if (*flag) break;
       const double inv = invd[j];
-      if (r0 > j && r0 < k) L[r0 * ldl + j] = (L[r0 * ldl + j] - d0) * inv;
-      if (r1 > j && r1 < k) L[r1 * ldl + j] = (L[r1 * ldl + j] - d1) * inv;
-      if (r2 > j && r2 < k) L[r2 * ldl + j] = (L[r2 * ldl + j] - d2) * inv;
-      if (r3 > j && r3 < k) L[r3 * ldl + j] = (L[r3 * ldl + j] - d3) * inv;
+#pragma unroll
+      for (int s = 0; s < kMaxSlots; ++s) {
+        const int row = lane + 32 * s;
+        if (row > j && row < k) L[row * ldl + j] = (L[row * ldl + j] - dd[s]) * inv;
+      }
       __syncwarp();
     }
     const bool fail = (*flag != 0) || bad;

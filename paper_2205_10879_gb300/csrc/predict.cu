@@ -142,6 +142,7 @@ int nearest_train(const void* X, fmgp_dtype dtype, int64_t n, int d, const void*
     if (d == 2) return launch_nn1_grid<2>(gv, Z, dtype, m, nearest, stream);
     return launch_nn1_grid<3>(gv, Z, dtype, m, nearest, stream);
   }
+  if (d <= kNn1ScanMaxD) return nearest_scan(X, dtype, n, d, Z, m, nullptr, nearest, ws, stream);
   return knn_query_brute(X, dtype, n, d, Z, m, 1, nearest, nullptr, ws, stream);
 }
 

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("prec", [fb.PREC_FP64, fb.PREC_MIXED])
-@pytest.mark.parametrize("name", ["tiny", "spatial", "large", "d16"])
+@pytest.mark.parametrize("name", ["tiny", "spatial", "large", "d16", "borehole"])
 def test_muygps_matches_oracle(cuda, prec, name):
     if name == "tiny":
         W = wl.tiny(m=400)
@@ -22,6 +22,8 @@ def test_muygps_matches_oracle(cuda, prec, name):
         W = wl.spatial(n=20_000, m=1_500, nu=0.5)
     elif name == "large":
         W = wl.large(n=200_000, m=800)
+    elif name == "borehole":
+        W = wl.borehole(n=5_000, m=200, k=150, nugget=1e-5)
     else:
         rng = np.random.default_rng(4)
         X = rng.random((6000, 16))

@@ -45,7 +45,7 @@ def test_knn_tiny_bitexact(cuda):
     np.testing.assert_array_equal(dist.cpu().numpy(), ref_k)
 
 
-@pytest.mark.parametrize("kq", [1, 49, 127])
+@pytest.mark.parametrize("kq", [1, 49, 127, 150, 160])
 def test_knn_spatial_sample_bitexact(cuda, kq):
     W = wl.spatial(n=40_000, m=10)
     nbr, dist = fb.fmgp_build_knn(dev(W.X), kq, with_dist=True)
@@ -63,11 +63,32 @@ def test_knn_bruteforce_bitexact(cuda, d, dtype):
     X = rng.random((n, d)).astype(dtype)
     X[rng.random((n, d)) < 0.8] = 0
     X[10] = X[20]  # exact duplicate
-    for kq in [1, 29]:
+    for kq in [1, 29, 150]:
         nbr, dist = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
         ref_i, ref_k = oracle.self_knn(X.astype(np.float64), kq)
         np.testing.assert_array_equal(nbr.cpu().numpy(), ref_i)
         np.testing.assert_array_equal(dist.cpu().numpy(), ref_k)
+
+
+@pytest.mark.parametrize("d,dtype", [(4, np.float64), (8, np.float64), (8, np.float32),
+                                     (15, np.float64)])
+def test_nearest_scan_bitexact(cuda, d, dtype):
+    """The thread-per-query nearest-point scan (4 <= d <= 15): integer grid
+    coordinates make many exact ties, which must go to the lowest index
+    across the scan's slices; half the rows get a small jitter."""
+    rng = np.random.default_rng(300 + d)
+    n, m = 9000, 700
+    X = rng.integers(0, 4, (n, d)).astype(dtype)
+    X[: n // 2] += (rng.random((n // 2, d)) * 0.01).astype(dtype)
+    Z = rng.integers(0, 4, (m, d)).astype(dtype)
+    Z[::3] += (rng.random((len(Z[::3]), d)) * 0.02).astype(dtype)
+    Y = rng.normal(size=(n, 1))
+    gk = fb.make_kernel("matern", 1.5, 1.0, 1.0, 1e-2)
+    nbr, _ = fb.fmgp_build_knn(dev(X), 4)
+    C, _ = fb.fmgp_precompute(dev(X), dev(Y), nbr, 5, gk, fb.PREC_FP64)
+    _, near = fb.fmgp_predict(dev(X), nbr, C, 5, gk, dev(Z), fb.PREC_FP64)
+    ref, _ = oracle.knn(X.astype(np.float64), Z.astype(np.float64), 1)
+    np.testing.assert_array_equal(near.cpu().numpy(), ref[:, 0])
 
 
 def test_nearest_test_point_bitexact(cuda):
@@ -132,7 +153,7 @@ def test_fp64_multi_response_highdim_small(cuda):
     assert rel_rms(yh.cpu().numpy(), yr) < FP64_TOL
 
 
-@pytest.mark.parametrize("k", [1, 2, 33, 64, 128])
+@pytest.mark.parametrize("k", [1, 2, 33, 64, 128, 129, 150])
 def test_fp64_precompute_k_range(cuda, k):
     W = wl.spatial(n=3_000, m=200, nu=1.5)
     ok, gk = kern_pair(W.kernel)
@@ -145,6 +166,19 @@ def test_fp64_precompute_k_range(cuda, k):
     yh, _ = fb.fmgp_predict(dev(W.X), nbr, C, k, gk, dev(W.Z), fb.PREC_FP64)
     yr, _ = oracle.predict(W.X, nb, Cr, ok, W.Z)
     assert rel_rms(yh.cpu().numpy(), yr) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision", [fb.PREC_FP64, fb.PREC_MIXED])
+def test_k_beyond_shared_memory_is_refused(cuda, precision):
+    """k = 160 needs more than 200 KB of shared memory per warp for the FP64
+    factor (the mixed form keeps it for its fallback): the call fails with
+    FMGP_EUNSUPPORTED instead of launching."""
+    W = wl.spatial(n=2_000, m=10, nu=1.5)
+    _, gk = kern_pair(W.kernel)
+    nbr, _ = fb.fmgp_build_knn(dev(W.X), 159)
+    with pytest.raises(fb.FmgpError) as ei:
+        fb.fmgp_precompute(dev(W.X), dev(W.Y), nbr, 160, gk, precision)
+    assert ei.value.code == fb.FMGP_EUNSUPPORTED
 
 
 def test_k_equals_n_small(cuda):
@@ -247,6 +281,12 @@ def test_mixed_ill_conditioned_large_like(cuda):
     several steps and some blocks may go to the FP64 fallback."""
     W = wl.large(n=1_000_000, m=3_000)
     _mixed_check(W, 64, 63)
+
+
+@pytest.mark.parametrize("k", [129, 150])
+def test_mixed_k_beyond_128(cuda, k):
+    W = wl.spatial(n=6_000, m=500, nu=1.5)
+    _mixed_check(W, k, k - 1)
 
 
 def test_mixed_highdim_multiresponse(cuda):
