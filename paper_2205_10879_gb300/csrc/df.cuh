@@ -90,15 +90,19 @@ __device__ __forceinline__ dfl df_fma(dfl x, dfl y, dfl acc) { return df_add(acc
 
 // Square root by one Newton (Karp-Markstein) correction of an FP32 root:
 // s ~ sqrt(hi), result s + (x - s^2) / (2 s) with x - s^2 formed exactly.
+// Written without an early return (0 for x <= 0 by selection) so that
+// several independent evaluations can interleave.
 __device__ __forceinline__ dfl df_sqrt(dfl x) {
-  if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+  const bool pos = x.hi > 0.0f;
+  const float xh = pos ? x.hi : 1.0f;
   // s needs only FP32-level accuracy: the correction below restores ~2^-46
-  const float rs = rsqrtf(x.hi);
-  const float s = __fmul_rn(x.hi, rs);
+  const float rs = rsqrtf(xh);
+  const float s = __fmul_rn(xh, rs);
   const dfl p = df_two_prod(s, s);
-  const float e = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);
+  const float e = __fadd_rn(__fsub_rn(__fsub_rn(xh, p.hi), p.lo), pos ? x.lo : 0.0f);
   const float c = e * (0.5f * rs);
-  return df_quick(s, c);
+  const dfl r = df_quick(s, c);
+  return {pos ? r.hi : 0.0f, pos ? r.lo : 0.0f};
 }
 
 // Constants of the DF exponential, filled on the host from FP64 values:
@@ -117,8 +121,11 @@ struct DfConsts {
 //   exp(-a) = 2^-n exp(-j/64) exp(-s),
 //   exp(-s) = 1 - s + s^2/2 in DF + s^3 (-1/6 + s/24 - s^2/120 + s^3/720) in
 //   FP32 (that tail is below 1e-7, so FP32 keeps it to ~1e-14).
+// Arguments at or above 87 (and NaN) give 0, by selection rather than an
+// early return; 2^-n is applied as an exact multiplication by a power of two.
 __device__ __forceinline__ dfl df_exp_neg(dfl a, const DfConsts& K) {
-  if (!(a.hi < 87.0f)) return {0.0f, 0.0f};
+  const bool in_range = a.hi < 87.0f;
+  if (!in_range) a = {87.0f, 0.0f};
   const float nf = rintf(__fmul_rn(a.hi, 1.4426950408889634f));
   const float r1 = __fsub_rn(a.hi, __fmul_rn(nf, K.ln2_1));  // exact
   const dfl p2 = df_two_prod(nf, K.ln2_2);                    // n ln2_2 exactly
@@ -140,8 +147,9 @@ __device__ __forceinline__ dfl df_exp_neg(dfl a, const DfConsts& K) {
                                        __fmul_rn(0.5f, s2.lo)), tail);
   const dfl e = df_quick(h2.hi, lo);
   dfl v = df_mul(dfl{K.e_hi[j + 24], K.e_lo[j + 24]}, e);
-  const int ni = (int)nf;
-  return {ldexpf(v.hi, -ni), ldexpf(v.lo, -ni)};
+  const int ni = (int)nf;  // 0 <= ni <= 126
+  const float sc = __int_as_float((127 - ni) << 23);
+  return {in_range ? __fmul_rn(v.hi, sc) : 0.0f, in_range ? __fmul_rn(v.lo, sc) : 0.0f};
 }
 
 __device__ __forceinline__ double df_to_double(dfl x) { return (double)x.hi + (double)x.lo; }

@@ -101,6 +101,44 @@ __device__ __forceinline__ dfl sqdist_df(const float2* a, const float2* b, int d
   return s;
 }
 
+// U kernel entries at once (pairs aa[u], bb[u] of the staged rows), the
+// kernel-kind switch hoisted so that the U evaluations interleave.
+template <int U>
+__device__ __forceinline__ void corr_df_multi(const KParamsDF& p, const float2* XS, int d,
+                                              const int* aa, const int* bb, const DfConsts& K,
+                                              dfl* out) {
+  dfl D[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) D[u] = {0.0f, 0.0f};
+  for (int t = 0; t < d; ++t) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float2 x = XS[aa[u] * d + t], y = XS[bb[u] * d + t];
+      const dfl diff = df_add_fast(dfl{x.x, x.y}, dfl{-y.x, -y.y});
+      D[u] = df_add_fast(D[u], df_sqr(diff));
+    }
+  }
+  if (p.kind == FMGP_KERNEL_RBF) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) out[u] = df_exp_neg(df_mul(D[u], p.scale), K);
+  } else if (p.nu2 == 1) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) out[u] = df_exp_neg(df_mul(df_sqrt(D[u]), p.scale), K);
+  } else if (p.nu2 == 3) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const dfl a = df_mul(df_sqrt(D[u]), p.scale);
+      out[u] = df_mul(df_add_f(a, 1.0f), df_exp_neg(a, K));
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const dfl a = df_mul(df_sqrt(D[u]), p.scale);
+      out[u] = df_mul(df_add(df_add_f(a, 1.0f), df_mul(df_sqr(a), p.third)), df_exp_neg(a, K));
+    }
+  }
+}
+
 struct MixedArgs {
   const float2* Xdf;  // n x d
   const float2* Ydf;  // n x r
@@ -228,7 +266,7 @@ __device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* 
 }
 
 template <int MODE, int NS, int CB>
-__global__ void __launch_bounds__(256, NS >= 5 ? 1 : 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
+__global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
                                                           MixedLayout lay) {
   constexpr bool LOO = MODE == kModeLoocv;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -275,26 +313,29 @@ __global__ void __launch_bounds__(256, NS >= 5 ? 1 : 2) block_mixed_kernel(Block
       const int npairs = k * (k - 1) / 2;
       int a = 1, b = lane;
       while (b >= a) { b -= a; ++a; }
-      // two entries per iteration (p and p + 32) for instruction-level parallelism
-      for (int p = lane; p < npairs; p += 64) {
-        const int a0 = a, b0 = b;
-        b += 32;
-        while (b >= a) { b -= a; ++a; }
-        const int a1 = a, b1 = b;
-        const bool two = p + 32 < npairs;
-        const dfl k0 = corr_df(kp, sqdist_df(XS + a0 * d, XS + b0 * d, d), mx.K);
-        dfl k1 = {0.0f, 0.0f};
-        if (two) k1 = corr_df(kp, sqdist_df(XS + a1 * d, XS + b1 * d, d), mx.K);
-        M[a0 * ldl + b0] = k0.hi;
-        M[b0 * ldl + a0] = k0.hi;
-        LO[p] = k0.lo;
-        if (two) {
-          M[a1 * ldl + b1] = k1.hi;
-          M[b1 * ldl + a1] = k1.hi;
-          LO[p + 32] = k1.lo;
+      // two entries per iteration, evaluated together for instruction-level
+      // parallelism (out-of-range slots evaluate a dummy pair and are dropped)
+      constexpr int U = 2;
+      for (int p = lane; p < npairs; p += 32 * U) {
+        int aa[U], bb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const bool v = p + 32 * u < npairs;
+          aa[u] = v ? a : 1;
+          bb[u] = v ? b : 0;
+          b += 32;
+          while (b >= a) { b -= a; ++a; }
         }
-        b += 32;
-        while (b >= a) { b -= a; ++a; }
+        dfl kv[U];
+        corr_df_multi<U>(kp, XS, d, aa, bb, mx.K, kv);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (p + 32 * u < npairs) {
+            M[aa[u] * ldl + bb[u]] = kv[u].hi;
+            M[bb[u] * ldl + aa[u]] = kv[u].hi;
+            LO[p + 32 * u] = kv[u].lo;
+          }
+        }
       }
     }
     for (int a = lane; a < k; a += 32) M[a * ldl + a] = kp.diag.hi;
@@ -400,26 +441,35 @@ __global__ void __launch_bounds__(256, NS >= 5 ? 1 : 2) block_mixed_kernel(Block
       bool conv = false;
       for (int step = 1; step <= kMaxRefine; ++step) {
         // residual y - K x in DF; lane owns rows; K_ab = (upper hi, packed lo)
+        for (int c = 0; c < r; ++c) {
+          dfl acc[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          const int row = lane + 32 * s;
-          if (row < k) {
-            const int rb = row * (row - 1) / 2;
-            for (int c = 0; c < r; ++c) {
-              dfl acc = YS[row * r + c];
-              acc = df_add(acc, df_neg(df_mul(kp.diag, XV[row * r + c])));
-              for (int b = 0; b < row; ++b) {  // K_row,b = (M[b][row], LO[row(row-1)/2 + b])
-                const dfl kab = {M[b * ldl + row], LO[rb + b]};
-                acc = df_add(acc, df_neg(df_mul(kab, XV[b * r + c])));
+          for (int s = 0; s < NS; ++s) {
+            const int row = lane + 32 * s;
+            acc[s] = dfl{0.0f, 0.0f};
+            if (row < k) acc[s] = df_add(YS[row * r + c], df_neg(df_mul(kp.diag, XV[row * r + c])));
+          }
+          int cb = 0;  // b(b-1)/2
+          for (int b = 0; b < k; ++b) {
+            const dfl xb = XV[b * r + c];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              const int row = lane + 32 * s;
+              if (row < k && b != row) {
+                // K_row,b = (M[b][row], LO[row(row-1)/2 + b]) below the diagonal,
+                // (M[row][b], LO[b(b-1)/2 + row]) above it
+                const bool below = b < row;
+                const float hi = below ? M[b * ldl + row] : M[row * ldl + b];
+                const float lo = below ? LO[row * (row - 1) / 2 + b] : LO[cb + row];
+                acc[s] = df_add(acc[s], df_neg(df_mul(dfl{hi, lo}, xb)));
               }
-              int cb = row * (row + 1) / 2;  // b(b-1)/2 at b = row + 1
-              for (int b = row + 1; b < k; ++b) {  // K_b,row = (M[row][b], LO[b(b-1)/2 + row])
-                const dfl kab = {M[row * ldl + b], LO[cb + row]};
-                acc = df_add(acc, df_neg(df_mul(kab, XV[b * r + c])));
-                cb += b;
-              }
-              RV[row * r + c] = acc.hi;
             }
+            cb += b;
+          }
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            const int row = lane + 32 * s;
+            if (row < k) RV[row * r + c] = acc[s].hi;
           }
         }
         __syncwarp();
@@ -584,9 +634,6 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   mx.K = df_consts();
   mx.kdf = make_kparams_df(a.kp, kern);
   const MixedLayout lay = mixed_layout(a.k, a.d, a.r);
-  const size_t smem = lay.bytes * warps;
-  const int64_t need = (a.count + warps - 1) / warps;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
   // rows per lane (k <= 32 S) and Cholesky block width are compile-time
   auto pick = [&](auto sconst) {
     constexpr int SS = decltype(sconst)::value;
@@ -601,6 +648,15 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
                : S == 3 ? pick(std::integral_constant<int, 3>{})
                : S == 4 ? pick(std::integral_constant<int, 4>{})
                         : pick(std::integral_constant<int, 5>{});
+  {
+    // the 2-slot instantiation is compiled for at most 192 threads (6 warps)
+    cudaFuncAttributes fa;
+    FMGP_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)kern_fn));
+    if (warps * 32 > fa.maxThreadsPerBlock) warps = fa.maxThreadsPerBlock / 32;
+  }
+  const size_t smem = lay.bytes * warps;
+  const int64_t need = (a.count + warps - 1) / warps;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
   FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
   FMGP_LAUNCH(kern_fn<<<blocks, warps * 32, smem, s>>>(a, mx, lay));
   FMGP_CUDA_TRY(cudaGetLastError());
