@@ -26,6 +26,8 @@ namespace {
 
 constexpr int kMaxSlots = kMaxK / 32;
 constexpr int kMaxRefine = 6;
+constexpr size_t kMixedHead = 512;  // per-CTA shared memory before the warps' areas
+static_assert(sizeof(DfConsts) <= kMixedHead, "the staged exponential table must fit the head");
 
 // The mixed kernels work with correlations phi (sigma^2 factored out): the
 // block solved is M = K / sigma^2 (diagonal 1 + tau^2), so C = M^{-1} Y / sigma^2,
@@ -272,7 +274,20 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
   extern __shared__ __align__(16) unsigned char smem[];
   const int wpb = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = smem + (size_t)wid * lay.bytes;
+  // the exponential's constants, staged once per CTA: lanes index the table
+  // with different j, which the constant bank would serialise
+  DfConsts& Ks = *reinterpret_cast<DfConsts*>(smem);
+  if (threadIdx.x == 0) {
+    Ks.ln2_1 = mx.K.ln2_1;
+    Ks.ln2_2 = mx.K.ln2_2;
+    Ks.ln2_3 = mx.K.ln2_3;
+  }
+  for (int t = threadIdx.x; t < 49; t += blockDim.x) {
+    Ks.e_hi[t] = mx.K.e_hi[t];
+    Ks.e_lo[t] = mx.K.e_lo[t];
+  }
+  __syncthreads();
+  unsigned char* base = smem + kMixedHead + (size_t)wid * lay.bytes;
   float* M = (float*)(base + lay.off_L);
   float* LO = (float*)(base + lay.off_LO);
   float2* XS = (float2*)(base + lay.off_X);
@@ -327,7 +342,7 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
           while (b >= a) { b -= a; ++a; }
         }
         dfl kv[U];
-        corr_df_multi<U>(kp, XS, d, aa, bb, mx.K, kv);
+        corr_df_multi<U>(kp, XS, d, aa, bb, Ks, kv);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (p + 32 * u < npairs) {
@@ -514,7 +529,7 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
       for (int s = 0; s < NS; ++s) {
         const int a = lane + 32 * s;
         kx[s] = dfl{0.0f, 0.0f};
-        if (a < k) kx[s] = corr_df(kp, sqdist_df(xi, XS + a * d, d), mx.K);
+        if (a < k) kx[s] = corr_df(kp, sqdist_df(xi, XS + a * d, d), Ks);
       }
       dfl e2 = {0.0f, 0.0f};
       for (int c = 0; c < r; ++c) {
@@ -550,6 +565,19 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
     const float2* Xdf, int64_t n, int d, const int32_t* nbr, int ld, const float2* C, int k,
     int r, KParamsDF kp, DfConsts K, const float2* Zdf, int64_t m, const int32_t* nearest,
     double* Yhat) {
+  // the exponential's constants in shared memory (lanes index the table
+  // with different j, which the constant bank would serialise)
+  __shared__ DfConsts Ks;
+  if (threadIdx.x == 0) {
+    Ks.ln2_1 = K.ln2_1;
+    Ks.ln2_2 = K.ln2_2;
+    Ks.ln2_3 = K.ln2_3;
+  }
+  for (int t = threadIdx.x; t < 49; t += blockDim.x) {
+    Ks.e_hi[t] = K.e_hi[t];
+    Ks.e_lo[t] = K.e_lo[t];
+  }
+  __syncthreads();
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= m) return;
@@ -569,7 +597,7 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
     if (s < nslots && a < k) {
       int64_t idx = (a == 0) ? j : (int64_t)nbr[j * ld + a - 1];
       if (idx < 0 || idx >= n) idx = j;
-      kz[s] = corr_df(kp, sqdist_df(z, Xdf + idx * d, d), K);
+      kz[s] = corr_df(kp, sqdist_df(z, Xdf + idx * d, d), Ks);
     }
   }
   for (int c = 0; c < r; ++c) {
@@ -637,7 +665,7 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   // rows per lane (k <= 32 S) and Cholesky block width are compile-time
   auto pick = [&](auto sconst) {
     constexpr int SS = decltype(sconst)::value;
-    constexpr int CB = SS <= 2 ? 8 : 4;
+    constexpr int CB = SS <= 1 ? 8 : 4;
     return mode == kModeLoocv    ? block_mixed_kernel<kModeLoocv, SS, CB>
            : mode == kModeMuygps ? block_mixed_kernel<kModeMuygps, SS, CB>
                                  : block_mixed_kernel<kModePrecompute, SS, CB>;
@@ -654,7 +682,7 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
     FMGP_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)kern_fn));
     if (warps * 32 > fa.maxThreadsPerBlock) warps = fa.maxThreadsPerBlock / 32;
   }
-  const size_t smem = lay.bytes * warps;
+  const size_t smem = kMixedHead + lay.bytes * warps;
   const int64_t need = (a.count + warps - 1) / warps;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
   FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
