@@ -92,7 +92,7 @@ enum {
  * index i itself is excluded; a duplicate of x_i stored at another index is a
  * neighbour at distance 0.
  *   X        n x d, FP64 or FP32 per `dtype`.
- *   kq       neighbours per row, 1 <= kq <= n-1.  A table with
+ *   kq       neighbours per row, 1 <= kq <= min(n-1, 160).  A table with
  *            kq = max(k-1, k_loocv) serves both fmgp_precompute (k-1 columns)
  *            and fmgp_loocv_objective (k columns) through nbr_ld = kq.
  *   nbr_out  n x kq int32 (row-major, leading dimension kq).
@@ -113,7 +113,11 @@ int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_
  *   Y        n x r FP64.
  *   nbr      n x nbr_ld int32 neighbour table (first k-1 columns are used),
  *            normally the output of fmgp_build_knn; entries must lie in [0, n).
- *   k        neighbourhood size |S_i|, 1 <= k <= min(n, 128), nbr_ld >= k-1.
+ *   k        neighbourhood size |S_i|, 1 <= k <= min(n, 160), nbr_ld >= k-1.
+ *            A block's FP64 factor must fit one warp's shared memory (about
+ *            k <= 157 at d = 2, less for large d); larger requests return
+ *            FMGP_EUNSUPPORTED (the mixed form keeps the FP64 layout for its
+ *            fallback, so the same limit applies).
  *   C_out    n x k x r coefficients, C_out[(i*k + a)*r + c] pairs with point
  *            S_i[a].  FMGP_PREC_FP64: double.  FMGP_PREC_MIXED: double-float
  *            pairs (float hi, float lo; value = hi + lo), i.e. n*k*r*2 floats.
@@ -155,7 +159,8 @@ int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const in
  * yhat_i = K(x_i, X_Ni) K(X_Ni, X_Ni)^{-1} Y(X_Ni) and
  * Q = (1/b) sum_{i in B} sum_c (Y[i][c] - yhat_i[c])^2.
  *   batch      b int64 training indices in [0, n) (device).
- *   k          1 <= k <= min(n-1, 128), nbr_ld >= k.
+ *   k          1 <= k <= min(n-1, 160), nbr_ld >= k (same shared-memory limit
+ *              as fmgp_precompute).
  *   Q_out      HOST pointer to one double.
  *   resid_out  b FP64 per-point squared residuals (device), or NULL.
  * The per-point residuals are summed in batch order by one deterministic
@@ -175,7 +180,8 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
  * neighbourhood solve, Yhat[t] = K(z_t, X_N*) K(X_N*, X_N*)^{-1} Y(X_N*)
  * (nugget on the block diagonal only).  O(k^3) per test point instead of
  * FastMuyGPs' O(k).
- *   X n x d, Y n x r (FP64), Z m x d (X's dtype), 1 <= k <= min(n, 128).
+ *   X n x d, Y n x r (FP64), Z m x d (X's dtype), 1 <= k <= min(n, 160) (same
+ *   shared-memory limit as fmgp_precompute).
  *   Yhat_out m x r FP64; nbr_out m x k int32 neighbour table or NULL.
  * A block that is not positive definite yields NaN predictions for its test
  * point.  Asynchronous on `stream`.
@@ -197,7 +203,8 @@ typedef struct fmgp_model fmgp_model;
  * X, nbr and C (as produced by fmgp_build_knn / fmgp_precompute with the same
  * k, kernel and precision) are BORROWED: they must stay valid and unchanged
  * until fmgp_model_destroy.  The model builds and OWNS the nearest-point
- * search grid (d <= 3) and, for FMGP_PREC_MIXED, a double-float copy of X.
+ * search grid (d <= 3), an FP32 copy of an FP64 X for the nearest-point scan
+ * (4 <= d <= 15) and, for FMGP_PREC_MIXED, a double-float copy of X.
  * Synchronises `stream` before returning.  *out receives the handle.
  */
 int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
@@ -214,7 +221,7 @@ int fmgp_model_predict(fmgp_model* model, const void* Z, int64_t m, double* Yhat
 /* Free the model's own buffers (waits for the device to go idle first). */
 int fmgp_model_destroy(fmgp_model* model);
 
-/* Device bytes owned by the model (grid + double-float copy), -1 for NULL. */
+/* Device bytes owned by the model (grid and copies of X), -1 for NULL. */
 int64_t fmgp_model_device_bytes(const fmgp_model* model);
 
 /*

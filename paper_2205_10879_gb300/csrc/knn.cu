@@ -300,17 +300,68 @@ int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, in
 // ------------------------------------------- nearest point, 4 <= d < 16 --
 // One thread per query keeps the query in registers; CTA (x, y) scans slice
 // y of the training points, staged kNnTile rows at a time in shared memory as
-// FP32 and read by all threads at the same address.  The FP32 lower bound is
-// the exhaustive scan's; a candidate whose bound does not exceed the current
-// best gets its canonical FP64 key.  Each slice's exact (key, index) minimum
-// goes to part; nn1_merge_kernel takes the minimum over slices.
+// FP32 and read by all threads at the same address.  A candidate whose plain
+// FP32 squared distance is within a rounding-safe threshold of the current
+// best (nn1_threshold) gets its canonical FP64 key.  Lanes pass that test at
+// different rows, and a warp would run the FP64 key path once for every such
+// row; so the threshold is first seeded with the key of each lane's nearest
+// candidate (by FP32 distance) in the first tile, one round for all lanes, and
+// then passing candidates are queued per lane and keyed together at the end
+// of each tile.  Every passing candidate is keyed and compared by (key,
+// index), so the result is the exact minimum.  Each slice's minimum goes to
+// part; nn1_merge_kernel takes the minimum over slices.
 constexpr int kNnThreads = 128;
 constexpr int kNnTile = 256;
+constexpr int kNnQueue = 4;
+
+// Pass threshold on the plain FP32 squared distance a = sum_j (qf_j - xf_j)^2
+// (FP32 copies of the query and the candidate).  With e = qf - xf and
+// delta = (q - x) - e the FP64->FP32 conversion error (|delta_j| <= cerr, so
+// ||delta|| <= cvec = cerr sqrt(D)), ||q - x|| >= ||e|| - cvec, and the FMA
+// chain gives ||e||^2 >= a * rel.  A candidate can reach the current best
+// (whose key is at most bup) only if sqrt(a * rel) <= sqrt(bup) + cvec, i.e.
+// a <= (sqrt(bup) + cvec)^2 / rel; the factors below round that bound up.
+__device__ __forceinline__ float nn1_threshold(float bup, float cvec, float rel) {
+  if (!(bup < __int_as_float(0x7f800000))) return __int_as_float(0x7f800000);
+  const float s = sqrtf(bup) * (1.0f + 16.0f * kU) + cvec;
+  return s * s * (1.0f + 16.0f * kU) / rel;
+}
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kNnThreads) nn1_scan_kernel(
-    const T* __restrict__ X, int64_t n, const T* __restrict__ Q, int64_t m,
-    const unsigned int* maxabs_bits, int64_t slice, unsigned long long* part_key,
+__device__ __forceinline__ void nn1_key(const T* __restrict__ X, const T* __restrict__ qg,
+                                        int cand, unsigned long long& best, int& bi, float& thr,
+                                        float cvec, float rel) {
+  const T* xg = X + (int64_t)cand * D;
+  double t = __dsub_rn((double)qg[0], (double)xg[0]);
+  double sum = __dmul_rn(t, t);
+#pragma unroll
+  for (int j = 1; j < D; ++j) {
+    t = __dsub_rn((double)qg[j], (double)xg[j]);
+    sum = __dadd_rn(sum, __dmul_rn(t, t));
+  }
+  const unsigned long long ck = dbits(sum);
+  if (key_less(ck, cand, best, bi)) {
+    best = ck;
+    bi = cand;
+    thr = nn1_threshold(key_bits_to_float_up(best), cvec, rel);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ float nn1_approx(const float* qf, const float* xr) {
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const float t = qf[j] - xr[j];
+    acc = fmaf(t, t, acc);
+  }
+  return acc;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kNnThreads, 8) nn1_scan_kernel(
+    const T* __restrict__ X, const float* __restrict__ Xf, int64_t n, const T* __restrict__ Q,
+    int64_t m, const unsigned int* maxabs_bits, int64_t slice, unsigned long long* part_key,
     int* part_idx) {
   __shared__ __align__(16) float tile[kNnTile * D];
   const int64_t q = blockIdx.x * (int64_t)kNnThreads + threadIdx.x;
@@ -319,47 +370,59 @@ __global__ void __launch_bounds__(kNnThreads) nn1_scan_kernel(
   const int64_t c1 = min(n, c0 + slice);
   const float M = __uint_as_float(*maxabs_bits);
   const float cerr = (sizeof(T) == 8) ? 2.5f * kU * M : 0.f;
+  const float cvec = cerr * (sqrtf((float)D) * (1.0f + 16.0f * kU));
   const float rel = 1.0f - (2.0f * D + 8.0f) * kU;
+  const T* qg = Q + (qv ? q : 0) * D;
   float qf[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) qf[j] = qv ? (float)Q[q * D + j] : 0.f;
+  for (int j = 0; j < D; ++j) qf[j] = qv ? (float)qg[j] : 0.f;
   unsigned long long best = ~0ull;
   int bi = INT_MAX;
-  float bup = __int_as_float(0x7f800000);
+  float thr = __int_as_float(0x7f800000);
+  int qi[kNnQueue];
+  int qn = 0;
   for (int64_t base = c0; base < c1; base += kNnTile) {
     const int rows = (int)min((int64_t)kNnTile, c1 - base);
     __syncthreads();
-    for (int e = threadIdx.x; e < rows * D; e += kNnThreads) tile[e] = (float)X[base * D + e];
+    for (int e = threadIdx.x; e < rows * D; e += kNnThreads) tile[e] = Xf[base * D + e];
     __syncthreads();
     if (!qv) continue;
-    for (int rr = 0; rr < rows; ++rr) {
-      const float* xr = tile + rr * D;
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        float t = fabsf(qf[j] - xr[j]) * (1.0f - 2.0f * kU) - cerr;
-        t = fmaxf(t, 0.f);
-        acc = fmaf(t, t, acc);
-      }
-      if (acc * rel <= bup) {
-        const int64_t cand = base + rr;
-        const T* xg = X + cand * D;
-        const T* qg = Q + q * D;
-        double t = __dsub_rn((double)qg[0], (double)xg[0]);
-        double sum = __dmul_rn(t, t);
-#pragma unroll
-        for (int j = 1; j < D; ++j) {
-          t = __dsub_rn((double)qg[j], (double)xg[j]);
-          sum = __dadd_rn(sum, __dmul_rn(t, t));
+    if (base == c0) {
+      // seed the threshold: key the first tile's nearest candidate by the
+      // FP32 distance (one round for all lanes)
+      float amin = __int_as_float(0x7f800000);
+      int rmin = 0;
+      for (int rr = 0; rr < rows; ++rr) {
+        const float a = nn1_approx<D>(qf, tile + rr * D);
+        if (a < amin) {
+          amin = a;
+          rmin = rr;
         }
-        const unsigned long long ck = dbits(sum);
-        if (key_less(ck, (int)cand, best, bi)) {
-          best = ck;
-          bi = (int)cand;
-          bup = key_bits_to_float_up(best);
+      }
+      nn1_key<T, D>(X, qg, (int)(base + rmin), best, bi, thr, cvec, rel);
+    }
+    for (int rr = 0; rr < rows; ++rr) {
+      if (nn1_approx<D>(qf, tile + rr * D) <= thr) {
+        const int cand = (int)(base + rr);
+        if (qn < kNnQueue) {
+#pragma unroll
+          for (int s = 0; s < kNnQueue; ++s)
+            if (s == qn) qi[s] = cand;
+          ++qn;
+        } else {  // this lane's queue is full: drain it alone (rare)
+#pragma unroll
+          for (int s = 0; s < kNnQueue; ++s)
+            nn1_key<T, D>(X, qg, qi[s], best, bi, thr, cvec, rel);
+          qi[0] = cand;
+          qn = 1;
         }
       }
     }
+    // key the queued candidates of all lanes together
+#pragma unroll
+    for (int s = 0; s < kNnQueue; ++s)
+      if (s < qn) nn1_key<T, D>(X, qg, qi[s], best, bi, thr, cvec, rel);
+    qn = 0;
   }
   if (qv) {
     part_key[q * gridDim.y + blockIdx.y] = best;
@@ -382,8 +445,8 @@ __global__ void nn1_merge_kernel(const unsigned long long* part_key, const int* 
 }
 
 template <typename T, int D>
-int launch_nn1_scan(const T* X, int64_t n, const T* Q, int64_t m, const unsigned int* mx,
-                    int32_t* nearest, Workspace& ws, cudaStream_t s) {
+int launch_nn1_scan(const T* X, const float* Xf, int64_t n, const T* Q, int64_t m,
+                    const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t s) {
   const int qblocks = ceil_div(m, kNnThreads);
   // about eight CTAs per SM in total, slices of at least 2048 rows
   int slices = (int)std::max<int64_t>(1, ((int64_t)num_sms() * 8 + qblocks - 1) / qblocks);
@@ -393,28 +456,28 @@ int launch_nn1_scan(const T* X, int64_t n, const T* Q, int64_t m, const unsigned
   int* pi = ws.get<int>((size_t)m * slices);
   if (!pk || !pi) return FMGP_ENOMEM;
   FMGP_LAUNCH((nn1_scan_kernel<T, D><<<dim3((unsigned)qblocks, (unsigned)slices), kNnThreads, 0, s>>>(
-      X, n, Q, m, mx, slice, pk, pi)));
+      X, Xf, n, Q, m, mx, slice, pk, pi)));
   FMGP_LAUNCH(nn1_merge_kernel<<<ceil_div(m, 256), 256, 0, s>>>(pk, pi, m, slices, nearest));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
 
 template <typename T>
-int nn1_scan_t(const T* X, int64_t n, int d, const T* Q, int64_t m, const unsigned int* mx,
-               int32_t* nearest, Workspace& ws, cudaStream_t s) {
+int nn1_scan_t(const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_t m,
+               const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t s) {
   switch (d) {
-    case 4: return launch_nn1_scan<T, 4>(X, n, Q, m, mx, nearest, ws, s);
-    case 5: return launch_nn1_scan<T, 5>(X, n, Q, m, mx, nearest, ws, s);
-    case 6: return launch_nn1_scan<T, 6>(X, n, Q, m, mx, nearest, ws, s);
-    case 7: return launch_nn1_scan<T, 7>(X, n, Q, m, mx, nearest, ws, s);
-    case 8: return launch_nn1_scan<T, 8>(X, n, Q, m, mx, nearest, ws, s);
-    case 9: return launch_nn1_scan<T, 9>(X, n, Q, m, mx, nearest, ws, s);
-    case 10: return launch_nn1_scan<T, 10>(X, n, Q, m, mx, nearest, ws, s);
-    case 11: return launch_nn1_scan<T, 11>(X, n, Q, m, mx, nearest, ws, s);
-    case 12: return launch_nn1_scan<T, 12>(X, n, Q, m, mx, nearest, ws, s);
-    case 13: return launch_nn1_scan<T, 13>(X, n, Q, m, mx, nearest, ws, s);
-    case 14: return launch_nn1_scan<T, 14>(X, n, Q, m, mx, nearest, ws, s);
-    case 15: return launch_nn1_scan<T, 15>(X, n, Q, m, mx, nearest, ws, s);
+    case 4: return launch_nn1_scan<T, 4>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 5: return launch_nn1_scan<T, 5>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 6: return launch_nn1_scan<T, 6>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 7: return launch_nn1_scan<T, 7>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 8: return launch_nn1_scan<T, 8>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 9: return launch_nn1_scan<T, 9>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 10: return launch_nn1_scan<T, 10>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 11: return launch_nn1_scan<T, 11>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 12: return launch_nn1_scan<T, 12>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 13: return launch_nn1_scan<T, 13>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 14: return launch_nn1_scan<T, 14>(X, Xf, n, Q, m, mx, nearest, ws, s);
+    case 15: return launch_nn1_scan<T, 15>(X, Xf, n, Q, m, mx, nearest, ws, s);
     default:
       set_error("nearest-point scan: d = %d outside [4, %d]", d, kNn1ScanMaxD);
       return FMGP_EUNSUPPORTED;
@@ -492,8 +555,23 @@ int knn_query_brute_mx(const void* X, fmgp_dtype dtype, int64_t n, int d, const 
                                 stream);
 }
 
+__global__ void to_f32_kernel(const double* in, int64_t count, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+int to_f32(const double* in, int64_t count, float* out, cudaStream_t s) {
+  if (count <= 0) return FMGP_OK;
+  const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), (int64_t)num_sms() * 8);
+  FMGP_LAUNCH(to_f32_kernel<<<blocks, 256, 0, s>>>(in, count, out));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
 int nearest_scan(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
-                 const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t stream) {
+                 const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t stream,
+                 const float* Xf32) {
   if (m == 0) return FMGP_OK;
   if (!mx) {
     unsigned int* own = ws.get<unsigned int>(1);
@@ -504,10 +582,21 @@ int nearest_scan(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* 
     if (rc) return rc;
     mx = own;
   }
-  if (dtype == FMGP_F64)
-    return nn1_scan_t<double>((const double*)X, n, d, (const double*)Q, m, mx, nearest, ws,
-                              stream);
-  return nn1_scan_t<float>((const float*)X, n, d, (const float*)Q, m, mx, nearest, ws, stream);
+  if (dtype == FMGP_F64) {
+    // the candidate tiles are staged from an FP32 copy (converted once here
+    // unless the caller keeps one): converting per tile would load the FP64 pipe
+    if (!Xf32) {
+      float* own = ws.get<float>((size_t)n * d);
+      if (!own) return FMGP_ENOMEM;
+      const int rc = to_f32((const double*)X, n * d, own, stream);
+      if (rc) return rc;
+      Xf32 = own;
+    }
+    return nn1_scan_t<double>((const double*)X, Xf32, n, d, (const double*)Q, m, mx, nearest,
+                              ws, stream);
+  }
+  return nn1_scan_t<float>((const float*)X, (const float*)X, n, d, (const float*)Q, m, mx,
+                           nearest, ws, stream);
 }
 
 int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,

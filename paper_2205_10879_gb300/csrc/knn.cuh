@@ -54,9 +54,14 @@ int knn_query_brute_mx(const void* X, fmgp_dtype dtype, int64_t n, int d, const 
 
 // Nearest training point (kq = 1) of each query by a thread-per-query scan,
 // for 4 <= d <= kNn1ScanMaxD.  mx: magnitude bound as for knn_query_brute_mx,
-// or null to compute it from X and Q.
+// or null to compute it from X and Q.  Xf32: an FP32 copy of an FP64 X
+// (round to nearest), or null to make one for the call.
 constexpr int kNn1ScanMaxD = 15;
 int nearest_scan(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
-                 const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t stream);
+                 const unsigned int* mx, int32_t* nearest, Workspace& ws, cudaStream_t stream,
+                 const float* Xf32 = nullptr);
+
+// FP32 copy (round to nearest) of count FP64 values.
+int to_f32(const double* in, int64_t count, float* out, cudaStream_t s);
 
 }  // namespace fmgp

@@ -91,7 +91,7 @@ int emulate(const Model& md, const void* Zp, int64_t m, const unsigned int* mx, 
   if (md.has_grid)
     rc = nearest_on_grid(md.grid, Zp, md.dtype, m, near, s);
   else if (md.d <= kNn1ScanMaxD)
-    rc = nearest_scan(md.X, md.dtype, md.n, md.d, Zp, m, mx, near, ws, s);
+    rc = nearest_scan(md.X, md.dtype, md.n, md.d, Zp, m, mx, near, ws, s, md.Xf32);
   else if (tune_params().use_tensor_cores && tc_knn_eligible(md.n, md.d, m, 1))
     rc = knn_query_brute(md.X, md.dtype, md.n, md.d, Zp, m, 1, near, nullptr, ws, s);
   else

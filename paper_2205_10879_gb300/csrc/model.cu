@@ -1,7 +1,8 @@
 // Resident fitted models: a model borrows the caller's X, neighbour table and
 // coefficients and owns what prediction would otherwise rebuild per call (the
-// search grid over X for d <= 3, the double-float copy of X for the mixed
-// form), so repeated prediction batches (the serving loop) only run the
+// search grid over X for d <= 3, an FP32 copy of an FP64 X for the
+// nearest-point scan at 4 <= d <= 15, the double-float copy of X for the
+// mixed form), so repeated prediction batches (the serving loop) only run the
 // nearest-point lookup and the gather-dot.
 #include "model.cuh"
 #include "predict.cuh"
@@ -54,6 +55,11 @@ extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int
   if (d <= kGridMaxD) {
     rc = build_grid(X, dtype, n, d, tune_params().grid_target, ws, s, &m->grid);
     m->has_grid = (rc == FMGP_OK);
+  }
+  if (!rc && d > kGridMaxD && d <= kNn1ScanMaxD && dtype == FMGP_F64) {
+    m->Xf32 = ws.get<float>((size_t)n * d);
+    if (!m->Xf32) rc = FMGP_ENOMEM;
+    else rc = to_f32((const double*)X, n * d, m->Xf32, s);
   }
   if (!rc && precision == FMGP_PREC_MIXED) {
     m->Xdf = ws.get<float2>((size_t)n * d);
@@ -108,7 +114,9 @@ int model_predict(const Model& md, const void* Z, int64_t m, double* Yhat, int32
     if (!near) return FMGP_ENOMEM;
   }
   int rc = md.has_grid ? nearest_on_grid(md.grid, Z, md.dtype, m, near, s)
-                       : nearest_train(md.X, md.dtype, md.n, md.d, Z, m, near, tune_params(), ws, s);
+           : md.d <= kNn1ScanMaxD
+               ? nearest_scan(md.X, md.dtype, md.n, md.d, Z, m, nullptr, near, ws, s, md.Xf32)
+               : nearest_train(md.X, md.dtype, md.n, md.d, Z, m, near, tune_params(), ws, s);
   if (rc) return rc;
   const KParams kp = make_kparams(md.kern);
   if (md.prec == FMGP_PREC_MIXED)

@@ -20,6 +20,7 @@ struct Model {
   bool has_grid = false;
   GridView grid{};
   float2* Xdf = nullptr;
+  float* Xf32 = nullptr;  // FP32 copy of an FP64 X for the nearest-point scan (4 <= d <= 15)
   void* bufs[kMaxBufs];
   int nbufs = 0;
   size_t bytes = 0;

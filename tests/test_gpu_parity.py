@@ -91,6 +91,23 @@ def test_nearest_scan_bitexact(cuda, d, dtype):
     np.testing.assert_array_equal(near.cpu().numpy(), ref[:, 0])
 
 
+def test_nearest_scan_fp64_near_ties_bitexact(cuda):
+    """FP64 points that differ by ~1e-10 collapse onto the same FP32 values:
+    the scan's FP32 threshold must let all of them through to the exact key."""
+    rng = np.random.default_rng(321)
+    n, m, d = 6000, 500, 8
+    centres = rng.integers(0, 3, (n // 6, d)).astype(np.float64)
+    X = np.repeat(centres, 6, axis=0) + rng.random((n, d)) * 1e-10
+    Z = centres[rng.integers(0, len(centres), m)] + rng.random((m, d)) * 1e-10
+    Y = rng.normal(size=(n, 1))
+    gk = fb.make_kernel("matern", 1.5, 1.0, 1.0, 1e-2)
+    nbr, _ = fb.fmgp_build_knn(dev(X), 4)
+    C, _ = fb.fmgp_precompute(dev(X), dev(Y), nbr, 5, gk, fb.PREC_FP64)
+    _, near = fb.fmgp_predict(dev(X), nbr, C, 5, gk, dev(Z), fb.PREC_FP64)
+    ref, _ = oracle.knn(X, Z, 1)
+    np.testing.assert_array_equal(near.cpu().numpy(), ref[:, 0])
+
+
 def test_nearest_test_point_bitexact(cuda):
     W = wl.spatial(n=30_000, m=5_000)
     X = dev(W.X)
