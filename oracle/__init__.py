@@ -260,6 +260,23 @@ def loocv(X, Y, nbr, k, batch, kern, long_double=False):
     return float(Q[0]), res
 
 
+def predict_rows(X, nbr, rows, C, kern, Z):
+    """Prediction from a subsampled precompute (the subsampling of the
+    precomputed coefficients proposed in Sec. 5): C (s x k x r) holds Eq. 6
+    for the training points rows[0..s) only (oracle.precompute(..., rows=rows)).
+    Each test point takes its nearest centre x_rows[p] (canonical key, ties to
+    the lower position p) and Eq. 7 with S_rows[p] and C[p].
+    Returns (Yhat m x r, the chosen centres' training indices m)."""
+    X = _c(X, np.float64)
+    rows = np.asarray(rows, np.int64)
+    C = _c(C, np.float64)
+    pos, _ = knn(X[rows], Z, 1)
+    centre = rows[pos[:, 0]]
+    Cfull = np.zeros((X.shape[0],) + C.shape[1:], np.float64)
+    Cfull[rows[::-1]] = C[::-1]  # a repeated row keeps its first position's coefficients
+    return predict_given(X, nbr, Cfull, kern, Z, centre.astype(np.int32)), centre.astype(np.int32)
+
+
 def mcmc(X, nbr, C, kern, z0, dim, lo, hi, f_obs, sigma, step, x0, noise, expo, col=0):
     """Metropolis calibration of input coordinate `dim` (Sec. 4.2).  noise and
     expo are (steps x chains) N(0,1) and Exp(1) draws.  Returns (samples

@@ -16,6 +16,9 @@ Each pin is chosen so that a plausible slip in the oracle fails it:
    precomputed C (Eq. 6).
  - sigma^2 invariance of the mean and 1/sigma^2 scaling of C.
  - Long-double re-evaluation bounds the FP64 rounding error.
+ - Subsampled precompute (Sec. 5): with every training point as a centre it is
+   the full method; at a test point whose nearest training point is a centre
+   it agrees with the full method; at a centre it interpolates (as Eq. 7 does).
  - Metropolis calibration (Sec. 4.2): with a linear response the posterior of
    the calibrated input is a (truncated) Gaussian in closed form, which the
    chains must reproduce (sign, factor 1/2, prior rejection); with Exp(1)
@@ -339,3 +342,49 @@ def test_mcmc_with_infinite_expo_takes_every_in_range_proposal():
         np.testing.assert_array_equal(S[t], x)
         assert np.all(np.isneginf(margin[t][~ok]))
     assert np.array_equal(acc, (S != np.vstack([x0[None, :], S[:-1]])).sum(axis=0))
+
+
+# --------------------------------------------------- subsampled precompute --
+def _subsample_setup():
+    W = wl.tiny(n=1500, m=400)
+    kern = oracle.kernel("matern", 1.5, 0.1, 1.0, 1e-4)
+    nbr, _ = oracle.self_knn(W.X, 29)
+    C, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern)
+    return W, kern, nbr, C
+
+
+def test_subsample_with_every_row_is_the_full_method():
+    W, kern, nbr, C = _subsample_setup()
+    rows = np.arange(W.n)
+    Cs, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern, rows=rows)
+    yr, cr = oracle.predict_rows(W.X, nbr, rows, Cs, kern, W.Z)
+    yf, nf = oracle.predict(W.X, nbr, C, kern, W.Z)
+    np.testing.assert_array_equal(cr, nf)
+    np.testing.assert_array_equal(yr, yf)
+
+
+def test_subsample_agrees_where_the_nearest_point_is_a_centre():
+    """Half the training points as centres: test points whose global nearest
+    training point is a centre use the same S and C row as the full method;
+    the others use another centre and differ."""
+    W, kern, nbr, C = _subsample_setup()
+    rows = np.sort(np.random.default_rng(5).choice(W.n, W.n // 2, replace=False))
+    Cs, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern, rows=rows)
+    yr, cr = oracle.predict_rows(W.X, nbr, rows, Cs, kern, W.Z)
+    yf, nf = oracle.predict(W.X, nbr, C, kern, W.Z)
+    same = np.isin(nf, rows)
+    assert 0 < same.sum() < W.m
+    np.testing.assert_array_equal(cr[same], nf[same])
+    np.testing.assert_array_equal(yr[same], yf[same])
+    assert np.all(np.isin(cr, rows))
+    assert np.all(cr[~same] != nf[~same])
+
+
+def test_subsample_interpolates_at_centres():
+    """At z = x_c (c a centre) the prediction is y_c - sigma^2 tau^2 C_c[0]."""
+    W, kern, nbr, _ = _subsample_setup()
+    rows = np.arange(0, W.n, 3)
+    Cs, _ = oracle.precompute(W.X, W.Y, nbr, 30, kern, rows=rows)
+    yr, cr = oracle.predict_rows(W.X, nbr, rows, Cs, kern, W.X[rows])
+    np.testing.assert_array_equal(cr, rows)
+    np.testing.assert_allclose(yr, W.Y[rows] - 1e-4 * Cs[:, 0, :], rtol=0, atol=1e-9)
