@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-muygps", action="store_true")
     p.add_argument("--no-highdim", action="store_true")
     p.add_argument("--no-borehole", action="store_true")
+    p.add_argument("--no-subsample", action="store_true")
     p.add_argument("--mcmc-chains", type=int, default=8192)
     p.add_argument("--mcmc-steps", type=int, default=1221)
     return p.parse_args()
@@ -387,6 +388,8 @@ def run_ours(a):
     }
     if not a.no_highdim:
         line["highdim_knn"] = highdim_knn_bench(a, dev, steps=a.steps, warmup=1)
+    if not a.no_subsample and a.workload == "spatial":
+        line["subsampled"] = subsample_bench(W, X, Y, Z, nbr, k, gk, prec, rmse, dev)
     if not a.no_borehole:
         line["borehole"] = borehole_bench(a, dev)
     if not a.no_serving:
@@ -436,6 +439,30 @@ def highdim_knn_bench(a, dev, steps, warmup):
             "uncertified_queries": fb.diag_counter(2),
             "roofline_call": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                               "frac": ach / peak, "note": "whole call incl. pack/select/re-rank"}}
+
+
+# ------------------------------------------------ subsampled precompute ----
+def subsample_bench(W, X, Y, Z, nbr, k, gk, prec, rmse_full, dev):
+    """The subsampling of precomputed coefficients proposed in Sec. 5, on the
+    step's workload and precision: C for a random fraction of the training
+    points (the centres), prediction from the nearest centre.  Coefficient
+    memory, precompute and prediction time, RMSE against the full method's."""
+    import torch
+    from paper_2205_10879_gb300 import _binding as fb
+    out = {"rmse_full": rmse_full, "centres": []}
+    for frac in (0.5, 0.25):
+        s = int(W.n * frac)
+        rows = torch.from_numpy(np.sort(np.random.default_rng(9).choice(W.n, s, replace=False))
+                                .astype(np.int32)).to(dev)
+        fb.fmgp_precompute_rows(X, Y, nbr, k, gk, rows, prec)
+        (C, _), ms_pre = _timed(lambda: fb.fmgp_precompute_rows(X, Y, nbr, k, gk, rows, prec), dev)
+        fb.fmgp_predict_rows(X, nbr, rows, C, k, gk, Z, prec)
+        (yh, _), ms_pred = _timed(lambda: fb.fmgp_predict_rows(X, nbr, rows, C, k, gk, Z, prec), dev)
+        rmse = float(np.sqrt(np.mean((yh.cpu().numpy() - W.Ztrue) ** 2)))
+        out["centres"].append({"fraction": frac, "s": s, "coeff_bytes": int(C.numel() * C.element_size()),
+                               "precompute_ms": ms_pre, "predict_ms": ms_pred, "rmse": rmse,
+                               "rmse_vs_full": rmse / rmse_full})
+    return out
 
 
 # ------------------------------------------------- borehole + MCMC (4.2) ----

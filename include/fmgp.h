@@ -191,6 +191,48 @@ int fmgp_muygps_predict(const void* X, fmgp_dtype dtype, const double* Y, int64_
                         fmgp_precision precision, double* Yhat_out, int32_t* nbr_out,
                         void* stream);
 
+/*
+ * fmgp_precompute_rows -- Eq. 6 for a subset of the training points (the
+ * "centres"): the subsampling of the precomputed coefficients that Sec. 5
+ * proposes to reduce the O(nk) memory of C.  For p < s, the block of training
+ * point i = rows[p] is formed and solved exactly as fmgp_precompute does
+ * (S_i = [i, nbr[i][0..k-2]]) and stored as row p of C_out.
+ *   rows       s int32 training indices (device; any order, repeats allowed).
+ *              An index outside [0, n) gives FMGP_BLOCK_BAD_INDEX and a zero
+ *              row (counted like a non-SPD block in the return value).
+ *   s          number of centres, 0 <= s < 2^31 (s = 0 is a no-op).
+ *   C_out      s x k x r coefficients, element format as fmgp_precompute.
+ *   status_out s int8 FMGP_BLOCK_* codes, or NULL.
+ * nbr is the full table of fmgp_build_knn (rows index into it).  Other
+ * arguments, precision, synchronisation and return values as fmgp_precompute.
+ */
+int fmgp_precompute_rows(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                         int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                         const int32_t* rows, int64_t s, const fmgp_kernel* kernel,
+                         fmgp_precision precision, void* C_out, int8_t* status_out,
+                         void* stream);
+
+/*
+ * fmgp_predict_rows -- prediction from fmgp_precompute_rows.  Each test point
+ * z_t takes the nearest centre x_{rows[p]} (canonical key; ties to the lower
+ * position p) and Eq. 7 with S_{rows[p]} and row p of C:
+ *   Yhat[t][c] = sum_a sigma^2 phi(||z_t - x_{S[a]}||) C[p][a][c].
+ * With every training point as a centre (rows = 0..n-1) this is fmgp_predict.
+ *   rows, s    as given to fmgp_precompute_rows, 1 <= s <= n.
+ *   C          s x k x r from fmgp_precompute_rows (same k, kernel, precision).
+ *   nearest_out m int32 training index rows[p] of each test point's centre,
+ *              or NULL.
+ * The rows are checked on the device before anything else runs (the call
+ * synchronises `stream` once for that): an index outside [0, n) returns
+ * FMGP_EINVAL with nothing written.  Otherwise asynchronous; returns FMGP_OK,
+ * FMGP_EINVAL, FMGP_ENOMEM or FMGP_ECUDA.
+ */
+int fmgp_predict_rows(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
+                      int32_t nbr_ld, const int32_t* rows, int64_t s, const void* C, int32_t k,
+                      int32_t r, const fmgp_kernel* kernel, fmgp_precision precision,
+                      const void* Z, int64_t m, double* Yhat_out, int32_t* nearest_out,
+                      void* stream);
+
 /* ------------------------------------------------------------------------
  * Resident models and the serving loop (the paper's online phase run as a
  * service: Sec. 1 motivates FastMuyGPs by applications that need many fast

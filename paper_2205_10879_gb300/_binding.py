@@ -72,6 +72,10 @@ def load(build_if_missing=True):
     lib.fmgp_build_knn.argtypes = [P, I32, I64, I32, I32, P, P, I32, P]
     lib.fmgp_precompute.argtypes = [P, I32, P, I64, I32, I32, P, I32, I32, KP, I32, P, P, P]
     lib.fmgp_predict.argtypes = [P, I32, I64, I32, P, I32, P, I32, I32, KP, I32, P, I64, P, P, P]
+    lib.fmgp_precompute_rows.argtypes = [P, I32, P, I64, I32, I32, P, I32, I32, P, I64, KP, I32,
+                                         P, P, P]
+    lib.fmgp_predict_rows.argtypes = [P, I32, I64, I32, P, I32, P, I64, P, I32, I32, KP, I32, P,
+                                      I64, P, P, P]
     lib.fmgp_loocv_objective.argtypes = [P, I32, P, I64, I32, I32, P, I32, I32, P, I64, KP, I32,
                                          P, P, P]
     for f in ("fmgp_build_knn", "fmgp_precompute", "fmgp_predict", "fmgp_loocv_objective"):
@@ -198,6 +202,49 @@ def fmgp_predict(X, nbr, C, k, kernel, Z, precision=PREC_FP64, Yhat_out=None, ne
     _check(load().fmgp_predict(_ptr(X), _dtype_code(X), n, d, _ptr(nbr), nbr.shape[1], _ptr(C),
                                int(k), r, ctypes.byref(kernel), int(precision), _ptr(Z), m,
                                _ptr(Yhat_out), _ptr(nearest_out), _stream(stream)))
+    return Yhat_out, nearest_out
+
+
+def fmgp_precompute_rows(X, Y, nbr, k, kernel, rows, precision=PREC_FP64, C_out=None,
+                         status_out=None, with_status=True, stream=None):
+    """Eq. 6 for the centres rows (int32 CUDA tensor of s training indices):
+    (C s x k x r [x 2 for PREC_MIXED], status s int8)."""
+    _dev(X, "X"); _dev(Y, "Y"); _dev(nbr, "nbr"); _dev(rows, "rows")
+    if rows.dtype != torch.int32:
+        raise TypeError("rows must be int32")
+    n, d = X.shape
+    r = Y.shape[1]
+    s = rows.shape[0]
+    if C_out is None:
+        C_out = torch.empty(coeff_shape(s, k, r, precision),
+                            dtype=torch.float64 if precision == PREC_FP64 else torch.float32,
+                            device=X.device)
+    if with_status and status_out is None:
+        status_out = torch.empty(s, dtype=torch.int8, device=X.device)
+    _check(load().fmgp_precompute_rows(_ptr(X), _dtype_code(X), _ptr(Y), n, d, r, _ptr(nbr),
+                                       nbr.shape[1], int(k), _ptr(rows), s, ctypes.byref(kernel),
+                                       int(precision), _ptr(C_out), _ptr(status_out),
+                                       _stream(stream)))
+    return C_out, status_out
+
+
+def fmgp_predict_rows(X, nbr, rows, C, k, kernel, Z, precision=PREC_FP64, Yhat_out=None,
+                      nearest_out=None, with_nearest=True, stream=None):
+    """Prediction from fmgp_precompute_rows: (Yhat m x r, centre index m int32)."""
+    _dev(X, "X"); _dev(nbr, "nbr"); _dev(rows, "rows"); _dev(C, "C"); _dev(Z, "Z")
+    if rows.dtype != torch.int32:
+        raise TypeError("rows must be int32")
+    n, d = X.shape
+    r = C.shape[2]
+    m = Z.shape[0]
+    if Yhat_out is None:
+        Yhat_out = torch.empty((m, r), dtype=torch.float64, device=X.device)
+    if with_nearest and nearest_out is None:
+        nearest_out = torch.empty(m, dtype=torch.int32, device=X.device)
+    _check(load().fmgp_predict_rows(_ptr(X), _dtype_code(X), n, d, _ptr(nbr), nbr.shape[1],
+                                    _ptr(rows), rows.shape[0], _ptr(C), int(k), r,
+                                    ctypes.byref(kernel), int(precision), _ptr(Z), m,
+                                    _ptr(Yhat_out), _ptr(nearest_out), _stream(stream)))
     return Yhat_out, nearest_out
 
 

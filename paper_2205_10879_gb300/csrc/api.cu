@@ -217,6 +217,40 @@ __global__ void __launch_bounds__(1024) loocv_reduce(const double* resid, int64_
 
 using namespace fmgp;
 
+// ------------------------------------------------ subsampled precompute --
+namespace {
+
+// flag = 1 if some rows[p] lies outside [0, n).
+__global__ void check_rows_kernel(const int32_t* rows, int64_t s, int64_t n, int* flag) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < s;
+       p += (int64_t)gridDim.x * blockDim.x)
+    if (rows[p] < 0 || rows[p] >= n) *flag = 1;
+}
+
+// Xc[p] = X[rows[p]] (rows checked beforehand).
+template <typename T>
+__global__ void gather_rows_kernel(const T* X, int d, const int32_t* rows, int64_t s, T* Xc) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / d;
+    Xc[e] = X[(int64_t)rows[p] * d + (e - p * d)];
+  }
+}
+
+// nearest[t] = rows[pos[t]]: the training index of the chosen centre.
+__global__ void centre_index_kernel(const int32_t* rows, const int32_t* pos, int64_t m,
+                                    int32_t* nearest) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x)
+    nearest[t] = rows[pos[t]];
+}
+
+int grid_for(int64_t count) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(count, 256), (int64_t)num_sms() * 8));
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* fmgp_last_error(void) { return g_err; }
@@ -452,6 +486,98 @@ int fmgp_muygps_predict(const void* X, fmgp_dtype dtype, const double* Y, int64_
     a.Zdf = Zdf;
   }
   return run_blocks(a, X, dtype, kModeMuygps, *kernel, precision, ws, s);
+}
+
+int fmgp_precompute_rows(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                         int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                         const int32_t* rows, int64_t s_rows, const fmgp_kernel* kernel,
+                         fmgp_precision precision, void* C_out, int8_t* status_out,
+                         void* stream) {
+  g_err[0] = 0;
+  int rc = validate_block_args(X, dtype, Y, n, d, r, k > 1 ? nbr : (const int32_t*)X, nbr_ld,
+                               kernel, precision);
+  if (rc) return rc;
+  FMGP_REQUIRE(s_rows >= 0 && s_rows < INT32_MAX, "s = %lld out of range [0, 2^31)",
+               (long long)s_rows);
+  if (s_rows == 0) return FMGP_OK;
+  FMGP_REQUIRE(rows && C_out, "rows and C_out must be non-NULL");
+  FMGP_REQUIRE(k >= 1 && k <= n && k <= kMaxK, "k = %d must be in [1, min(n, %d)]", k, kMaxK);
+  FMGP_REQUIRE(nbr_ld >= k - 1 && nbr_ld >= 0, "nbr_ld = %d must be >= k-1 = %d", nbr_ld, k - 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  int* fails = ws.get<int>(1);
+  if (!fails) return FMGP_ENOMEM;
+  FMGP_CUDA_TRY(cudaMemsetAsync(fails, 0, sizeof(int), s));
+  BlockArgs a{};
+  a.Y = Y;
+  a.nbr = nbr;
+  a.C = C_out;
+  a.status = status_out;
+  a.fail_count = fails;
+  a.rows = rows;
+  a.n = n;
+  a.count = s_rows;
+  a.d = d;
+  a.r = r;
+  a.ld = nbr_ld;
+  a.k = k;
+  a.kp = make_kparams(*kernel);
+  rc = run_blocks(a, X, dtype, kModePrecompute, *kernel, precision, ws, s);
+  if (rc) return rc;
+  if (!status_out) {
+    int h = 0;
+    FMGP_CUDA_TRY(cudaMemcpyAsync(&h, fails, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FMGP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+      set_error("%d neighbourhood blocks were not positive definite or had a bad index", h);
+      return FMGP_ENOTSPD;
+    }
+  }
+  return FMGP_OK;
+}
+
+int fmgp_predict_rows(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
+                      int32_t nbr_ld, const int32_t* rows, int64_t s_rows, const void* C,
+                      int32_t k, int32_t r, const fmgp_kernel* kernel, fmgp_precision precision,
+                      const void* Z, int64_t m, double* Yhat_out, int32_t* nearest_out,
+                      void* stream) {
+  g_err[0] = 0;
+  if (!dtype_ok(dtype) || !kernel_ok(kernel) || !prec_ok(precision)) return FMGP_EINVAL;
+  FMGP_REQUIRE(m >= 0, "m = %lld must be >= 0", (long long)m);
+  FMGP_REQUIRE(X && C && rows, "X, C and rows must be non-NULL");
+  FMGP_REQUIRE(n >= 1 && n < INT32_MAX, "n = %lld out of range [1, 2^31)", (long long)n);
+  FMGP_REQUIRE(s_rows >= 1 && s_rows <= n, "s = %lld must be in [1, n]", (long long)s_rows);
+  FMGP_REQUIRE(d >= 1 && r >= 1, "d and r must be >= 1");
+  FMGP_REQUIRE(k >= 1 && k <= n && k <= kMaxK, "k = %d must be in [1, min(n, %d)]", k, kMaxK);
+  FMGP_REQUIRE(k == 1 || nbr, "nbr must be non-NULL when k > 1");
+  FMGP_REQUIRE(nbr_ld >= k - 1, "nbr_ld = %d must be >= k-1", nbr_ld);
+  if (m == 0) return FMGP_OK;
+  FMGP_REQUIRE(Z && Yhat_out, "Z and Yhat_out must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace ws(s);
+  int* flag = ws.get<int>(1);
+  const size_t xb = dtype == FMGP_F64 ? 8 : 4;
+  void* Xc = ws.alloc((size_t)s_rows * d * xb);
+  int32_t* pos = ws.get<int32_t>(m);
+  int32_t* near = nearest_out ? nearest_out : ws.get<int32_t>(m);
+  if (!flag || !Xc || !pos || !near) return FMGP_ENOMEM;
+  FMGP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  FMGP_LAUNCH(check_rows_kernel<<<grid_for(s_rows), 256, 0, s>>>(rows, s_rows, n, flag));
+  int h = 0;
+  FMGP_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FMGP_CUDA_TRY(cudaStreamSynchronize(s));
+  FMGP_REQUIRE(h == 0, "rows holds an index outside [0, n)");
+  if (dtype == FMGP_F64)
+    FMGP_LAUNCH(gather_rows_kernel<double><<<grid_for(s_rows * d), 256, 0, s>>>(
+        (const double*)X, d, rows, s_rows, (double*)Xc));
+  else
+    FMGP_LAUNCH(gather_rows_kernel<float><<<grid_for(s_rows * d), 256, 0, s>>>(
+        (const float*)X, d, rows, s_rows, (float*)Xc));
+  int rc = nearest_train(Xc, dtype, s_rows, d, Z, m, pos, tune_params(), ws, s);
+  if (rc) return rc;
+  FMGP_LAUNCH(centre_index_kernel<<<grid_for(m), 256, 0, s>>>(rows, pos, m, near));
+  return gather_dot(X, dtype, n, d, nbr, nbr_ld, C, k, r, make_kparams(*kernel), *kernel,
+                    precision, Z, m, near, Yhat_out, ws, s, pos);
 }
 
 }  // extern "C"

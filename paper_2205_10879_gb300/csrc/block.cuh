@@ -42,6 +42,9 @@ struct BlockArgs {
   const int* list = nullptr;
   const int* list_count = nullptr;
   bool c_df = false;
+  // Precompute over centres (subsampled precompute): item p factors the block
+  // of training point rows[p] and writes C row p and status p.
+  const int32_t* rows = nullptr;
 };
 
 // blocks = 0 picks a grid covering `count`; the list mode needs an explicit grid.

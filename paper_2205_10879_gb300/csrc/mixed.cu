@@ -302,7 +302,9 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
 
   for (int64_t item = (int64_t)blockIdx.x * wpb + wid; item < args.count;
        item += (int64_t)gridDim.x * wpb) {
-    int64_t i = LOO ? args.batch[item] : item;
+    int64_t i = LOO ? args.batch[item]
+                    : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
+    const int64_t orow = MODE == kModePrecompute && args.rows ? item : i;  // row of C / status
     bool bad = false;
     if (MODE != kModeMuygps && (i < 0 || i >= args.n)) { bad = true; i = 0; }
     for (int a = lane; a < k; a += 32) {
@@ -515,12 +517,12 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
         mx.fb_list[pos] = (int)item;
       }
     } else if (MODE == kModePrecompute) {
-      float2* Ci = (float2*)args.C + i * (int64_t)k * r;
+      float2* Ci = (float2*)args.C + orow * (int64_t)k * r;
       for (int e = lane; e < k * r; e += 32) {
         const dfl cv = df_mul(XV[e], kp.inv_var);
         Ci[e] = make_float2(cv.hi, cv.lo);
       }
-      if (args.status && lane == 0) args.status[i] = FMGP_BLOCK_OK;
+      if (args.status && lane == 0) args.status[orow] = FMGP_BLOCK_OK;
     } else {
       // cross-covariance of the query point (x_i for LOOCV, z_t for MuyGPs), in DF
       dfl kx[NS];
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
 __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
     const float2* Xdf, int64_t n, int d, const int32_t* nbr, int ld, const float2* C, int k,
     int r, KParamsDF kp, DfConsts K, const float2* Zdf, int64_t m, const int32_t* nearest,
-    double* Yhat) {
+    double* Yhat, const int32_t* crow) {
   // the exponential's constants in shared memory (lanes index the table
   // with different j, which the constant bank would serialise)
   __shared__ DfConsts Ks;
@@ -587,6 +589,7 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
       for (int c = 0; c < r; ++c) Yhat[w * r + c] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
+  const int64_t cj = crow ? (int64_t)crow[w] : j;  // row of C (a position for centre subsets)
   const float2* z = Zdf + w * d;
   dfl kz[kMaxSlots];
   const int nslots = (k + 31) / 32;
@@ -606,7 +609,7 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
     for (int s = 0; s < kMaxSlots; ++s) {
       const int a = lane + 32 * s;
       if (s < nslots && a < k) {
-        const float2 cc = C[(j * k + a) * r + c];
+        const float2 cc = C[(cj * k + a) * r + c];
         acc = df_add(acc, df_mul(kz[s], dfl{cc.x, cc.y}));
       }
     }
@@ -702,7 +705,8 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
 int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
                      const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
                      const void* Z, int64_t m, const int32_t* nearest, double* Yhat,
-                     Workspace& ws, cudaStream_t stream, const float2* Xdf_cached) {
+                     Workspace& ws, cudaStream_t stream, const float2* Xdf_cached,
+                     const int32_t* crow) {
   if (m == 0) return FMGP_OK;
   float2* Xdf = Xdf_cached ? nullptr : ws.get<float2>((size_t)n * d);
   float2* Zdf = ws.get<float2>((size_t)m * d);
@@ -714,7 +718,7 @@ int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const in
   const int blocks = ceil_div(m * 32, 256);
   FMGP_LAUNCH(gather_dot_mixed_kernel<<<blocks, 256, 0, stream>>>(
       Xdf, n, d, nbr, ld, (const float2*)C, k, r, make_kparams_df(kp, kern), df_consts(), Zdf, m,
-      nearest, Yhat));
+      nearest, Yhat, crow));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }

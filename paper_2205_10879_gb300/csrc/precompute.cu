@@ -41,7 +41,9 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
   for (int64_t it = (int64_t)blockIdx.x * wpb + wid; it < total;
        it += (int64_t)gridDim.x * wpb) {
     const int64_t item = args.list ? (int64_t)args.list[it] : it;
-    int64_t i = LOO ? args.batch[item] : item;
+    int64_t i = LOO ? args.batch[item]
+                    : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
+    const int64_t orow = MODE == kModePrecompute && args.rows ? item : i;  // row of C / status
     // S: precompute S_i = [i, N_i]; LOOCV N_i (self excluded); MuyGPs N*_t
     bool bad = false;
     if (MODE != kModeMuygps && (i < 0 || i >= args.n)) { bad = true; i = 0; }
@@ -151,18 +153,18 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
     }
     if (MODE == kModePrecompute) {
       if (args.c_df) {
-        float2* Ci = (float2*)args.C + i * (int64_t)k * r;
+        float2* Ci = (float2*)args.C + orow * (int64_t)k * r;
         for (int e = lane; e < k * r; e += 32) {
           const double v = fail ? 0.0 : W[e];
           const float hi = (float)v;
           Ci[e] = make_float2(hi, (float)(v - (double)hi));
         }
       } else {
-        double* Ci = (double*)args.C + i * (int64_t)k * r;
+        double* Ci = (double*)args.C + orow * (int64_t)k * r;
         for (int e = lane; e < k * r; e += 32) Ci[e] = fail ? 0.0 : W[e];
       }
       if (args.status && lane == 0)
-        args.status[i] = bad ? FMGP_BLOCK_BAD_INDEX
+        args.status[orow] = bad ? FMGP_BLOCK_BAD_INDEX
                              : (fail ? FMGP_BLOCK_NOT_SPD
                                      : (args.list ? FMGP_BLOCK_FP64_RETRY : FMGP_BLOCK_OK));
       if (fail && lane == 0) atomicAdd(args.fail_count, 1);

@@ -69,11 +69,13 @@ __global__ void __launch_bounds__(256) nn1_grid_kernel(GridView gv, const T* Z, 
 template <typename T>
 __global__ void __launch_bounds__(256) gather_dot_f64_kernel(
     const T* X, int64_t n, int d, const int32_t* nbr, int ld, const double* C, int k, int r,
-    KParams kp, const T* Z, int64_t m, const int32_t* nearest, double* Yhat) {
+    KParams kp, const T* Z, int64_t m, const int32_t* nearest, double* Yhat,
+    const int32_t* crow) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= m) return;
   const int64_t j = nearest[w];
+  const int64_t cj = crow ? (int64_t)crow[w] : j;  // row of C (a position for centre subsets)
   if (j < 0 || j >= n) {  // no valid nearest point (cannot happen for n >= 1)
     if (lane == 0)
       for (int c = 0; c < r; ++c) Yhat[w * r + c] = __longlong_as_double(0x7ff8000000000000ll);
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(256) gather_dot_f64_kernel(
 #pragma unroll
     for (int s = 0; s < kMaxK / 32; ++s) {
       const int a = lane + 32 * s;
-      if (s < nslots && a < k) acc = fma(kz[s], C[(j * k + a) * r + c], acc);
+      if (s < nslots && a < k) acc = fma(kz[s], C[(cj * k + a) * r + c], acc);
     }
 #pragma unroll
     for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
@@ -149,21 +151,21 @@ int nearest_train(const void* X, fmgp_dtype dtype, int64_t n, int d, const void*
 int gather_dot(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
                const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
                fmgp_precision prec, const void* Z, int64_t m, const int32_t* nearest,
-               double* Yhat, Workspace& ws, cudaStream_t stream) {
+               double* Yhat, Workspace& ws, cudaStream_t stream, const int32_t* crow) {
   if (m == 0) return FMGP_OK;
   const int blocks = ceil_div(m * 32, 256);
   if (prec == FMGP_PREC_FP64) {
     if (dtype == FMGP_F64)
       FMGP_LAUNCH(gather_dot_f64_kernel<double><<<blocks, 256, 0, stream>>>(
           (const double*)X, n, d, nbr, ld, (const double*)C, k, r, kp, (const double*)Z, m,
-          nearest, Yhat));
+          nearest, Yhat, crow));
     else
       FMGP_LAUNCH(gather_dot_f64_kernel<float><<<blocks, 256, 0, stream>>>(
           (const float*)X, n, d, nbr, ld, (const double*)C, k, r, kp, (const float*)Z, m,
-          nearest, Yhat));
+          nearest, Yhat, crow));
   } else {
     return gather_dot_mixed(X, dtype, n, d, nbr, ld, C, k, r, kp, kern, Z, m, nearest, Yhat, ws,
-                            stream);
+                            stream, nullptr, crow);
   }
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;

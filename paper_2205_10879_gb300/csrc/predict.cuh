@@ -16,13 +16,14 @@ int nearest_train(const void* X, fmgp_dtype dtype, int64_t n, int d, const void*
 int gather_dot(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
                const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
                fmgp_precision prec, const void* Z, int64_t m, const int32_t* nearest,
-               double* Yhat, Workspace& ws, cudaStream_t stream);
+               double* Yhat, Workspace& ws, cudaStream_t stream, const int32_t* crow = nullptr);
 
 // A5 with double-float coefficients and cross-covariances (mixed precision).
 int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,
                      const void* C, int k, int r, const KParams& kp, const fmgp_kernel& kern,
                      const void* Z, int64_t m, const int32_t* nearest, double* Yhat,
-                     Workspace& ws, cudaStream_t stream, const float2* Xdf_cached = nullptr);
+                     Workspace& ws, cudaStream_t stream, const float2* Xdf_cached = nullptr,
+                     const int32_t* crow = nullptr);
 
 // Double-float copy of count values (FP64 or FP32 input).
 int to_df(const void* in, bool f64, int64_t count, float2* out, cudaStream_t s);
