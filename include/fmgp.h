@@ -85,12 +85,12 @@ enum {
 };
 
 /*
- * fmgp_build_knn -- self k-nearest-neighbour table of the training set.
- * Algorithm 2 "query k-1 nearest neighbors of x_i" and Algorithm 1 "query k
- * nearest neighbors for all i in B": for every training point i, the kq
- * nearest training points j != i, ascending by (canonical key, j).  Only the
- * index i itself is excluded; a duplicate of x_i stored at another index is a
- * neighbour at distance 0.
+ * fmgp_build_knn -- self k-nearest-neighbour table of the training set: the
+ * neighbour queries of Algorithm 2 (the k-1 nearest neighbours of every
+ * training point) and of Algorithm 1 (the k nearest neighbours of every batch
+ * point).  For every training point i, the kq nearest training points j != i,
+ * ascending by (canonical key, j).  Only the index i itself is excluded; a
+ * duplicate of x_i stored at another index is a neighbour at distance 0.
  *   X        n x d, FP64 or FP32 per `dtype`.
  *   kq       neighbours per row, 1 <= kq <= min(n-1, 160).  A table with
  *            kq = max(k-1, k_loocv) serves both fmgp_precompute (k-1 columns)

@@ -85,9 +85,8 @@ double fmgp_oracle_key(const double* a, const double* b, int d) {
   return s;
 }
 
-/* Brute-force k-nearest-neighbour query (Algorithm 1 "query k nearest
- * neighbors", Algorithm 2 "query k-1 nearest neighbors" and the test-point
- * lookup).  For each query q, every training j (j != exclude[q] when an
+/* Brute-force k-nearest-neighbour query (the neighbour queries of
+ * Algorithms 1 and 2 and the test-point lookup).  For each query q, every training j (j != exclude[q] when an
  * exclusion list is given: the query's own index for self-queries) is
  * scanned in index order and kept in a sorted list of the kq smallest
  * (key, j); a later j never displaces an equal key, so ties go to the lowest
