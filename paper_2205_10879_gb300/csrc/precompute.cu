@@ -1,9 +1,11 @@
-// A2 + A3 (Eq. 6) and A6 (Eqs. 4-5) in FP64: one warp per neighbourhood.
-// The warp stages the neighbourhood's features and responses in shared
-// memory, assembles the lower triangle of K_S there, factors it by a
-// row-per-lane Crout Cholesky, solves L L^T W = Y_S by column sweeps, and
-// either stores W as the row C_i (precompute) or dots it with the
-// cross-covariance of x_i to form the leave-one-out residual (LOOCV).
+// A2 + A3 (Eq. 6) and A6 (Eqs. 4-5) in FP64: one warp per neighbourhood
+// (one CTA per neighbourhood when the neighbourhood's shared memory is too
+// large for several to share an SM).  The warp stages the neighbourhood's
+// features and responses in shared memory, assembles the lower triangle of
+// K_S there, factors it by a row-per-lane Crout Cholesky, solves
+// L L^T W = Y_S by column sweeps, and either stores W as the row C_i
+// (precompute) or dots it with the cross-covariance of x_i to form the
+// leave-one-out residual (LOOCV) or the prediction (MuyGPs).
 #include "block.cuh"
 #include "knn.cuh"
 
@@ -212,6 +214,172 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
   }
 }
 
+// The same computation with one CTA per neighbourhood, for neighbourhoods
+// too large for several warps' worth of them to share an SM (an FP64 factor
+// of k = 150 needs ~190 KB): one resident warp could only use one of the
+// SM's four FP64 units.  kCtaThreads threads split the work (thread t owns
+// row t, so k <= kCtaThreads) with a barrier per column; every dot product
+// and every update runs in the same order as in block_f64_kernel, so
+// coefficients are identical to it.
+constexpr int kCtaThreads = 256;
+static_assert(kMaxK <= kCtaThreads, "one row per thread");
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kCtaThreads, 1) block_f64_cta_kernel(BlockArgs args,
+                                                                       const T* X) {
+  constexpr bool LOO = MODE == kModeLoocv;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[kCtaThreads / 32];
+  const BlockLayout lay = args.layout;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double* L = (double*)(smem + lay.off_L);
+  double* W = (double*)(smem + lay.off_W);
+  double* invd = (double*)(smem + lay.off_inv);
+  T* XS = (T*)(smem + lay.off_X);
+  int* S = (int*)(smem + lay.off_S);
+  volatile int* flag = (int*)(smem + lay.off_flag);
+  const int k = args.k, d = args.d, r = args.r, ldl = lay.ldl;
+  const KParams kp = args.kp;
+
+  const int64_t total = args.list ? (int64_t)*args.list_count : args.count;
+  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+    __syncthreads();  // the previous neighbourhood is finished with shared memory
+    const int64_t item = args.list ? (int64_t)args.list[it] : it;
+    int64_t i = LOO ? args.batch[item]
+                    : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
+    const int64_t orow = MODE == kModePrecompute && args.rows ? item : i;  // row of C / status
+    bool bad = false;
+    if (MODE != kModeMuygps && (i < 0 || i >= args.n)) { bad = true; i = 0; }
+    if (tid < k) {
+      int64_t idx = MODE != kModePrecompute ? (int64_t)args.nbr[i * args.ld + tid]
+                                            : (tid == 0 ? i : (int64_t)args.nbr[i * args.ld + tid - 1]);
+      if (idx < 0 || idx >= args.n) { bad = true; idx = 0; }
+      S[tid] = (int)idx;
+    }
+    if (tid == 0) *flag = 0;
+    bad = __syncthreads_or(bad) != 0;
+    for (int e = tid; e < k * d; e += kCtaThreads) {
+      const int a = e / d, t = e - a * d;
+      XS[e] = X[(int64_t)S[a] * d + t];
+    }
+    for (int e = tid; e < k * r; e += kCtaThreads) {
+      const int a = e / r, c = e - a * r;
+      W[e] = args.Y[(int64_t)S[a] * r + c];
+    }
+    __syncthreads();
+    const int npairs = k * (k - 1) / 2;
+    for (int p = tid; p < npairs; p += kCtaThreads) {
+      int a, b;
+      pair_of(p, a, b);
+      double D = 0.0;
+      for (int t = 0; t < d; ++t) {
+        const double diff = (double)XS[a * d + t] - (double)XS[b * d + t];
+        D = fma(diff, diff, D);
+      }
+      L[a * ldl + b] = kp.var * phi64(kp, D);
+    }
+    if (tid < k) L[tid * ldl + tid] = kp.diag;
+    __syncthreads();
+    // Cholesky, Crout order: thread t forms row t of column j
+    for (int j = 0; j < k; ++j) {
+      double dd = 0.0;
+      if (tid >= j && tid < k) {
+        const double* lr = L + tid * ldl;
+        const double* lj = L + j * ldl;
+        for (int p = 0; p < j; ++p) dd = fma(lr[p], lj[p], dd);
+      }
+      if (tid == j) {
+        const double v = L[j * ldl + j] - dd;
+        if (!(v > 0.0)) {
+          *flag = 1;
+        } else {
+          const double ljj = sqrt(v);
+          L[j * ldl + j] = ljj;
+          invd[j] = 1.0 / ljj;
+        }
+      }
+      __syncthreads();
+      if (*flag) break;
+      if (tid > j && tid < k) L[tid * ldl + j] = (L[tid * ldl + j] - dd) * invd[j];
+      __syncthreads();
+    }
+    const bool fail = (*flag != 0) || bad;
+    if (!fail) {
+      for (int p = 0; p < k; ++p) {  // forward sweep: L v = y
+        for (int c = tid; c < r; c += kCtaThreads) W[p * r + c] *= invd[p];
+        __syncthreads();
+        if (tid > p && tid < k) {
+          const double l = L[tid * ldl + p];
+          for (int c = 0; c < r; ++c) W[tid * r + c] = fma(-l, W[p * r + c], W[tid * r + c]);
+        }
+        __syncthreads();
+      }
+      for (int p = k - 1; p >= 0; --p) {  // back sweep: L^T w = v
+        for (int c = tid; c < r; c += kCtaThreads) W[p * r + c] *= invd[p];
+        __syncthreads();
+        if (tid < p) {
+          const double l = L[p * ldl + tid];
+          for (int c = 0; c < r; ++c) W[tid * r + c] = fma(-l, W[p * r + c], W[tid * r + c]);
+        }
+        __syncthreads();
+      }
+    }
+    if (MODE == kModePrecompute) {
+      if (args.c_df) {
+        float2* Ci = (float2*)args.C + orow * (int64_t)k * r;
+        for (int e = tid; e < k * r; e += kCtaThreads) {
+          const double v = fail ? 0.0 : W[e];
+          const float hi = (float)v;
+          Ci[e] = make_float2(hi, (float)(v - (double)hi));
+        }
+      } else {
+        double* Ci = (double*)args.C + orow * (int64_t)k * r;
+        for (int e = tid; e < k * r; e += kCtaThreads) Ci[e] = fail ? 0.0 : W[e];
+      }
+      if (args.status && tid == 0)
+        args.status[orow] = bad ? FMGP_BLOCK_BAD_INDEX
+                                : (fail ? FMGP_BLOCK_NOT_SPD
+                                        : (args.list ? FMGP_BLOCK_FP64_RETRY : FMGP_BLOCK_OK));
+      if (fail && tid == 0) atomicAdd(args.fail_count, 1);
+    } else {
+      // cross-covariance of the query point (x_i for LOOCV, z_t for MuyGPs)
+      double kx = 0.0;
+      const T* xi = MODE == kModeMuygps ? (const T*)args.Zq + i * d : X + i * d;
+      if (!fail && tid < k) {
+        double D = 0.0;
+        for (int t = 0; t < d; ++t) {
+          const double diff = (double)xi[t] - (double)XS[tid * d + t];
+          D = fma(diff, diff, D);
+        }
+        kx = kp.var * phi64(kp, D);
+      }
+      double e2 = 0.0;
+      for (int c = 0; c < r; ++c) {
+        double acc = tid < k ? kx * W[tid * r + c] : 0.0;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+        if (lane == 0) red[wid] = acc;
+        __syncthreads();
+        if (tid == 0) {
+          double sum = red[0];
+          for (int w = 1; w < kCtaThreads / 32; ++w) sum += red[w];
+          if (MODE == kModeMuygps) {
+            args.yhat[i * r + c] = fail ? __longlong_as_double(0x7ff8000000000000ll) : sum;
+          } else {
+            const double e = args.Y[i * r + c] - sum;
+            e2 = fma(e, e, e2);
+          }
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        if (MODE == kModeLoocv) args.resid[item] = fail ? __longlong_as_double(0x7ff8000000000000ll) : e2;
+        if (fail) atomicAdd(args.fail_count, 1);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 BlockLayout block_layout(int k, int d, int r, int xbytes, bool f32_factor) {
@@ -231,8 +399,34 @@ BlockLayout block_layout(int k, int d, int r, int xbytes, bool f32_factor) {
   return l;
 }
 
+// Neighbourhoods larger than this (bytes of shared memory) take one CTA each:
+// fewer than four of them would fit on an SM as one-warp blocks.
+constexpr size_t kCtaBlockBytes = 56 * 1024;
+
 int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mode, int warps,
                      cudaStream_t stream, int blocks) {
+  if (a.layout.bytes_per_warp > kCtaBlockBytes) {
+    const size_t smem = a.layout.bytes_per_warp;
+    // persistent: as many CTAs as fit on the SMs at once
+    const int fit = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+    const int grid = blocks > 0 ? blocks
+                                : (int)std::max<int64_t>(1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit));
+    if (dtype == FMGP_F64) {
+      auto kern = mode == kModeLoocv    ? block_f64_cta_kernel<double, kModeLoocv>
+                  : mode == kModeMuygps ? block_f64_cta_kernel<double, kModeMuygps>
+                                        : block_f64_cta_kernel<double, kModePrecompute>;
+      FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
+      FMGP_LAUNCH(kern<<<grid, kCtaThreads, smem, stream>>>(a, (const double*)X));
+    } else {
+      auto kern = mode == kModeLoocv    ? block_f64_cta_kernel<float, kModeLoocv>
+                  : mode == kModeMuygps ? block_f64_cta_kernel<float, kModeMuygps>
+                                        : block_f64_cta_kernel<float, kModePrecompute>;
+      FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
+      FMGP_LAUNCH(kern<<<grid, kCtaThreads, smem, stream>>>(a, (const float*)X));
+    }
+    FMGP_CUDA_TRY(cudaGetLastError());
+    return FMGP_OK;
+  }
   const size_t smem = a.layout.bytes_per_warp * warps;
   const int sms = num_sms();
   const int64_t need = (a.count + warps - 1) / warps;

@@ -257,6 +257,22 @@ def test_loocv_tiny(cuda, precision):
     assert rel_rms(res.cpu().numpy(), resr) < tol
 
 
+@pytest.mark.parametrize("precision", [fb.PREC_FP64, fb.PREC_MIXED])
+def test_loocv_large_k(cuda, precision):
+    """k = 140: the FP64 blocks take one CTA each (and so does the mixed
+    path's FP64 fallback)."""
+    W = wl.spatial(n=4000, m=10, nu=1.5, b=300)
+    ok, gk = kern_pair(W.kernel)
+    X = dev(W.X)
+    nbr, _ = fb.fmgp_build_knn(X, 140)
+    Q, res = fb.fmgp_loocv_objective(X, dev(W.Y), nbr, 140, dev(W.batch), gk, precision)
+    nb, _ = oracle.self_knn(W.X, 140)
+    Qr, resr = oracle.loocv(W.X, W.Y, nb, 140, W.batch, ok)
+    tol = FP64_TOL if precision == fb.PREC_FP64 else MIXED_TOL
+    assert abs(Q - Qr) / abs(Qr) < tol
+    assert rel_rms(res.cpu().numpy(), resr) < tol
+
+
 # ------------------------------------------------------------ mixed path --
 def _mixed_check(W, k, kq, n_rows=None, tol=MIXED_TOL):
     ok, gk = kern_pair(W.kernel)
