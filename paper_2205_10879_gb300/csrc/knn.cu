@@ -2,7 +2,7 @@
 //   d <= 3 : uniform grid, one warp per query, rings of cells in order of
 //            Chebyshev distance with box pruning and an exact stop test.
 //   d >= 4 : tiled scan of all training points; a CTA of 8 warps (8 queries)
-//            stages 32 candidate rows at a time in shared memory as FP32.
+//            stages 256 candidate rows at a time in shared memory as FP32.
 //   nearest point only, 4 <= d <= 15: one thread per query over slices of
 //            the training points, then a minimum over the slices.
 // Both rank on the canonical FP64 key; FP32 is used only for lower bounds.
@@ -144,8 +144,9 @@ __global__ void __launch_bounds__(256) knn_grid_query_kernel(GridView gv, const 
 
 // ---------------------------------------------------------- brute force ----
 constexpr int kBfWarps = 8;
-constexpr int kBfTile = 32;
-constexpr int kBfChunk = 256;  // feature columns staged per pass
+constexpr int kBfTile = 256;   // candidate rows staged per pass (8 per lane)
+constexpr int kBfSub = kBfTile / 32;
+constexpr int kBfChunk = 64;   // feature columns staged per pass
 
 __global__ void maxabs_kernel(const void* X, int f64, int64_t count, unsigned int* out_bits) {
   float m = 0.f;
@@ -158,20 +159,26 @@ __global__ void maxabs_kernel(const void* X, int f64, int64_t count, unsigned in
   if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));
 }
 
-// Each warp owns one query; each lane owns one candidate of the staged tile.
-// The FP32 partial distances over feature chunks give a lower bound
+// Each warp owns one query; the CTA stages kBfTile candidate rows at a time
+// (FP32 copy of X, kBfChunk feature columns per pass) and lane l bounds rows
+// l, l + 32, ... of the tile.  The FP32 partial distances give a lower bound
 // (relative rounding of d non-negative terms plus the FP64->FP32 conversion
-// slack); only candidates whose bound does not exceed the current k-th key
-// get their canonical FP64 key.
+// slack).  Each lane marks its rows whose bound does not exceed the current
+// k-th key; then, round by round, every lane takes its next marked row,
+// checks it against the k-th key as it stands, and the warp forms the
+// canonical FP64 keys of those rows together and offers them to the list.
+// So the FP64 key path runs once per round (not once for every row that any
+// lane passes), and the result is the exact top kq by (key, index).
 template <typename T, int L>
 __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
-    const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int exclude_self,
-    const unsigned int* maxabs_bits, int32_t* idx_out, double* key_out, const int* qlist,
-    const int* qcount) {
+    const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_t m, int kq,
+    int exclude_self, const unsigned int* maxabs_bits, int32_t* idx_out, double* key_out,
+    const int* qlist, const int* qcount) {
   extern __shared__ float sm[];
-  const int ld = d | 1;  // odd stride: conflict-free column reads
-  float* tile = sm;                          // kBfTile x ld (chunk of columns)
-  float* qs = sm + kBfTile * ld;             // kBfWarps x ld
+  const int ld = d | 1;                      // query rows
+  const int tld = min(d, kBfChunk) | 1;      // tile rows: odd stride, conflict-free
+  float* tile = sm;                          // kBfTile x tld (chunk of columns)
+  float* qs = sm + kBfTile * tld;            // kBfWarps x ld
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // query of this warp: position p of the (optional) list
   const int64_t count = qlist ? (int64_t)*qcount : m;
@@ -192,41 +199,66 @@ __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
   WarpTopK<L> top;
   top.init(kq);
   const float* myq = qs + wid * ld;
+  const T* qr = Q + q * d;
   for (int64_t base = 0; base < n; base += kBfTile) {
-    float acc = 0.f;
+    float acc[kBfSub];
+#pragma unroll
+    for (int u = 0; u < kBfSub; ++u) acc[u] = 0.f;
     for (int c0 = 0; c0 < d; c0 += kBfChunk) {
       const int cw = min(kBfChunk, d - c0);
       __syncthreads();
       for (int e = threadIdx.x; e < kBfTile * cw; e += blockDim.x) {
-        const int rr = e / cw, j = e % cw;
+        const int rr = e / cw, j = e - rr * cw;
         const int64_t row = base + rr;
-        tile[rr * ld + j] = row < n ? (float)X[row * d + c0 + j] : 0.f;
+        tile[rr * tld + j] = row < n ? Xf[row * d + c0 + j] : 0.f;
       }
       __syncthreads();
-      const float* trow = tile + lane * ld;
       for (int j = 0; j < cw; ++j) {
-        float t = fabsf(myq[c0 + j] - trow[j]) * (1.0f - 2.0f * kU) - cerr;
-        t = fmaxf(t, 0.f);
-        acc = fmaf(t, t, acc);
+        const float qj = myq[c0 + j];
+#pragma unroll
+        for (int u = 0; u < kBfSub; ++u) {
+          float t = fabsf(qj - tile[(u * 32 + lane) * tld + j]) * (1.0f - 2.0f * kU) - cerr;
+          t = fmaxf(t, 0.f);
+          acc[u] = fmaf(t, t, acc[u]);
+        }
       }
     }
-    const int64_t cand = base + lane;
-    unsigned long long ck = ~0ull;
-    int ci = INT_MAX;
-    if (qvalid && cand < n && !(exclude_self && cand == q) && acc * rel <= top.t_up) {
-      // canonical FP64 key from the original rows
-      const T* xr = X + cand * d;
-      const T* qr = Q + q * d;
-      double t = __dsub_rn((double)qr[0], (double)xr[0]);
-      double s = __dmul_rn(t, t);
-      for (int j = 1; j < d; ++j) {
-        t = __dsub_rn((double)qr[j], (double)xr[j]);
-        s = __dadd_rn(s, __dmul_rn(t, t));
-      }
-      ck = dbits(s);
-      ci = (int)cand;
+    if (!qvalid) continue;
+    unsigned pm = 0;  // rows of this lane still to consider
+#pragma unroll
+    for (int u = 0; u < kBfSub; ++u) {
+      const int64_t cand = base + u * 32 + lane;
+      if (cand < n && !(exclude_self && cand == q)) pm |= 1u << u;
     }
-    top.offer(ck, ci, lane);
+    while (true) {
+      // next marked row of each lane whose bound passes the current k-th key
+      int ci = INT_MAX;
+      while (pm) {
+        const int u = __ffs(pm) - 1;
+        pm &= pm - 1;
+        float a = acc[0];
+#pragma unroll
+        for (int v = 1; v < kBfSub; ++v)
+          if (v == u) a = acc[v];
+        if (a * rel <= top.t_up) {
+          ci = (int)(base + u * 32 + lane);
+          break;
+        }
+      }
+      if (!__any_sync(kFull, ci != INT_MAX)) break;
+      unsigned long long ck = ~0ull;
+      if (ci != INT_MAX) {
+        const T* xr = X + (int64_t)ci * d;
+        double t = __dsub_rn((double)qr[0], (double)xr[0]);
+        double sum = __dmul_rn(t, t);
+        for (int j = 1; j < d; ++j) {
+          t = __dsub_rn((double)qr[j], (double)xr[j]);
+          sum = __dadd_rn(sum, __dmul_rn(t, t));
+        }
+        ck = dbits(sum);
+      }
+      top.offer(ck, ci, lane);
+    }
   }
   if (qvalid) top.store(kq, lane, idx_out + q * kq, key_out ? key_out + q * kq : nullptr);
 }
@@ -257,31 +289,43 @@ int launch_grid_query(const GridView& gv, const T* Q, int64_t m, int kq, int32_t
 }
 
 template <typename T, int L>
-int launch_brute_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
-                   const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
+int launch_brute_t(const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_t m, int kq,
+                   int excl, const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
                    const int* qlist = nullptr, const int* qcount = nullptr) {
   const int ld = d | 1;
-  const size_t smem = sizeof(float) * (size_t)(kBfTile + kBfWarps) * ld;
+  const int tld = std::min(d, kBfChunk) | 1;
+  const size_t smem = sizeof(float) * ((size_t)kBfTile * tld + (size_t)kBfWarps * ld);
   if (smem > 200 * 1024) {
     set_error("brute-force kNN: d = %d needs %zu bytes of shared memory", d, smem);
     return FMGP_EUNSUPPORTED;
   }
   auto kern = knn_brute_kernel<T, L>;
   FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
-  FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(X, n, d, Q, m, kq, excl, mx, idx, key, qlist, qcount));
+  FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, qlist, qcount));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
 
 template <typename T>
-int launch_brute_mx(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
-                    const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
+int launch_brute_mx(const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_t m, int kq,
+                    int excl, const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
                     const int* qlist = nullptr, const int* qcount = nullptr) {
-  if (kq <= 32) return launch_brute_t<T, 1>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 64) return launch_brute_t<T, 2>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 96) return launch_brute_t<T, 3>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 128) return launch_brute_t<T, 4>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  return launch_brute_t<T, 5>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 32) return launch_brute_t<T, 1>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 64) return launch_brute_t<T, 2>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 96) return launch_brute_t<T, 3>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  if (kq <= 128) return launch_brute_t<T, 4>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  return launch_brute_t<T, 5>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+}
+
+// FP32 rows the exhaustive scan stages: X itself, or a copy of an FP64 X.
+template <typename T>
+const float* brute_rows(const T* X, int64_t n, int d, Workspace& ws, cudaStream_t s, int* rc) {
+  *rc = FMGP_OK;
+  if (sizeof(T) == 4) return (const float*)X;
+  float* f = ws.get<float>((size_t)n * d);
+  if (!f) { *rc = FMGP_ENOMEM; return nullptr; }
+  *rc = to_f32((const double*)X, n * d, f, s);
+  return f;
 }
 
 template <typename T>
@@ -294,7 +338,9 @@ int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, in
   int rc = maxabs_into(X, sizeof(T) == 8, n * d, mx, s);
   if (!rc && Q != X) rc = maxabs_into(Q, sizeof(T) == 8, m * d, mx, s);
   if (rc) return rc;
-  return launch_brute_mx<T>(X, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  const float* Xf = brute_rows(X, n, d, ws, s, &rc);
+  if (rc) return rc;
+  return launch_brute_mx<T>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
 }
 
 // ------------------------------------------- nearest point, 4 <= d < 16 --
@@ -546,13 +592,17 @@ int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaSt
 
 int knn_query_brute_mx(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q,
                        int64_t m, int kq, const unsigned int* mx, int32_t* idx, double* key,
-                       cudaStream_t stream) {
+                       Workspace& ws, cudaStream_t stream) {
   if (m == 0) return FMGP_OK;
-  if (dtype == FMGP_F64)
-    return launch_brute_mx<double>((const double*)X, n, d, (const double*)Q, m, kq, 0, mx, idx,
-                                   key, stream);
-  return launch_brute_mx<float>((const float*)X, n, d, (const float*)Q, m, kq, 0, mx, idx, key,
-                                stream);
+  int rc;
+  if (dtype == FMGP_F64) {
+    const float* Xf = brute_rows((const double*)X, n, d, ws, stream, &rc);
+    if (rc) return rc;
+    return launch_brute_mx<double>((const double*)X, Xf, n, d, (const double*)Q, m, kq, 0, mx,
+                                   idx, key, stream);
+  }
+  return launch_brute_mx<float>((const float*)X, (const float*)X, n, d, (const float*)Q, m, kq,
+                                0, mx, idx, key, stream);
 }
 
 __global__ void to_f32_kernel(const double* in, int64_t count, float* out) {

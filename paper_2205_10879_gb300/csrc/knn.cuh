@@ -50,7 +50,7 @@ int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaSt
 // max |coordinate| over X and all of Q (FP32 bits, rounded up).
 int knn_query_brute_mx(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q,
                        int64_t m, int kq, const unsigned int* mx, int32_t* idx, double* key,
-                       cudaStream_t stream);
+                       Workspace& ws, cudaStream_t stream);
 
 // Nearest training point (kq = 1) of each query by a thread-per-query scan,
 // for 4 <= d <= kNn1ScanMaxD.  mx: magnitude bound as for knn_query_brute_mx,

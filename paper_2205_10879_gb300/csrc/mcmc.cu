@@ -95,7 +95,7 @@ int emulate(const Model& md, const void* Zp, int64_t m, const unsigned int* mx, 
   else if (tune_params().use_tensor_cores && tc_knn_eligible(md.n, md.d, m, 1))
     rc = knn_query_brute(md.X, md.dtype, md.n, md.d, Zp, m, 1, near, nullptr, ws, s);
   else
-    rc = knn_query_brute_mx(md.X, md.dtype, md.n, md.d, Zp, m, 1, mx, near, nullptr, s);
+    rc = knn_query_brute_mx(md.X, md.dtype, md.n, md.d, Zp, m, 1, mx, near, nullptr, ws, s);
   if (rc) return rc;
   const KParams kp = make_kparams(md.kern);
   if (md.prec == FMGP_PREC_MIXED)
