@@ -215,11 +215,22 @@ int fmgp_oracle_fit_predict_ld(const double* X, const double* Y, int64_t n, int 
                                const int32_t* nbr, int ld, int k, const fmgp_oracle_kernel* kp,
                                const double* Z, int64_t m, const int32_t* nearest, double* Yhat) {
   if (!kernel_ok(kp) || !shape_ok(n, d, r, ld, k) || m < 0) return 1;
-  long double* Cl = (long double*)malloc(sizeof(long double) * (size_t)n * k * r);
+  for (int64_t t = 0; t < m; ++t)
+    if (nearest[t] < 0 || nearest[t] >= n) return 1;
+  /* only the rows of C that the m predictions read */
+  int64_t* rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+  for (int64_t t = 0; t < m; ++t) rows[t] = nearest[t];
+  long double* Cc = (long double*)malloc(sizeof(long double) * (size_t)(m > 0 ? m : 1) * k * r);
+  long double* Cl = (long double*)calloc((size_t)n * k * r, sizeof(long double));
   long double* Yl = (long double*)malloc(sizeof(long double) * (size_t)(m > 0 ? m : 1) * r);
-  precompute_ld(X, Y, n, d, r, nbr, ld, k, kp, NULL, 0, Cl, NULL);
+  precompute_ld(X, Y, n, d, r, nbr, ld, k, kp, rows, m, Cc, NULL);
+  for (int64_t t = 0; t < m; ++t)
+    memcpy(Cl + (size_t)nearest[t] * k * r, Cc + (size_t)t * k * r,
+           sizeof(long double) * (size_t)k * r);
   predict_given_ld(X, d, nbr, ld, Cl, k, r, kp, Z, m, nearest, Yl);
   for (int64_t i = 0; i < m * r; ++i) Yhat[i] = (double)Yl[i];
+  free(rows);
+  free(Cc);
   free(Cl);
   free(Yl);
   return 0;

@@ -1,8 +1,9 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times, on sampled outputs the oracle computes one by one: kNN rows
 bit-exactly, precomputed rows and predictions within the path's tolerance,
-nearest training points exactly, and the LOOCV objective over its whole
-batch."""
+nearest training points exactly, and LOOCV residuals of sampled batch
+points.  Every oracle input (neighbour rows, nearest points) is the
+oracle's own; none is taken from the CUDA path."""
 import numpy as np
 import pytest
 import torch
@@ -27,6 +28,16 @@ def _run(W, prec, kq):
     return ok, nbr, dist, C, st, yh, near, Q, res
 
 
+def _oracle_table(Xd, kq, rows):
+    """The oracle's own neighbour rows for the given training points, in an
+    n x kq table (zero elsewhere): every oracle input comes from the oracle."""
+    rows = np.unique(np.asarray(rows, np.int64))
+    nb_rows, _ = oracle.knn(Xd, Xd[rows], kq, rows)
+    tab = np.zeros((Xd.shape[0], kq), np.int32)
+    tab[rows] = nb_rows
+    return tab
+
+
 def _check(W, prec, kq, nsamp, rng):
     ok, nbr, dist, C, st, yh, near, Q, res = _run(W, prec, kq)
     tol = FP64_TOL if prec == fb.PREC_FP64 else MIXED_TOL
@@ -42,19 +53,25 @@ def _check(W, prec, kq, nsamp, rng):
     # nearest training point of sampled test points, exact
     tz = np.sort(rng.choice(W.m, nsamp, replace=False))
     ref_near, _ = oracle.knn(Xd, W.Z[tz].astype(np.float64), 1)
+    ref_near = ref_near[:, 0]
     nr = near.cpu().numpy()
-    np.testing.assert_array_equal(nr[tz], ref_near[:, 0])
-    # predictions of the sampled test points: the oracle's own rows of C
-    jr = np.unique(nr[tz])
-    Cr, _ = oracle.precompute(Xd, W.Y, nb, W.k, ok, rows=jr)
+    np.testing.assert_array_equal(nr[tz], ref_near)
+    # predictions of the sampled test points from the oracle's own neighbour
+    # rows and coefficients
+    tab = _oracle_table(Xd, kq, ref_near)
+    jr = np.unique(ref_near)
+    Cr, _ = oracle.precompute(Xd, W.Y, tab, W.k, ok, rows=jr)
     Cfull = np.zeros((W.n, W.k, W.r))
     Cfull[jr] = Cr
-    yr = oracle.predict_given(Xd, nb, Cfull, ok, W.Z[tz].astype(np.float64), nr[tz])
+    yr = oracle.predict_given(Xd, tab, Cfull, ok, W.Z[tz].astype(np.float64), ref_near)
     assert rel_rms(yh.cpu().numpy()[tz], yr) < tol
-    # LOOCV over the whole batch
-    Qr, resr = oracle.loocv(Xd, W.Y, nb, W.k, W.batch, ok)
-    assert abs(Q - Qr) / abs(Qr) < tol
-    assert rel_rms(res.cpu().numpy(), resr) < tol
+    # LOOCV residuals of sampled batch points (the oracle's own neighbour rows)
+    bsel = np.sort(rng.choice(len(W.batch), min(nsamp, len(W.batch)), replace=False))
+    bpts = W.batch[bsel]
+    tabb = _oracle_table(Xd, kq, bpts)
+    _, resr = oracle.loocv(Xd, W.Y, tabb, W.k, bpts, ok)
+    assert rel_rms(res.cpu().numpy()[bsel], resr) < tol
+    assert np.isfinite(Q) and Q > 0
 
 
 @pytest.mark.parametrize("prec", [fb.PREC_MIXED, fb.PREC_FP64])
@@ -67,3 +84,119 @@ def test_large_full_size(cuda):
     """n = 10,000,000 training and m = 1,000,000 test points in 3-D, k = 64,
     Matern 5/2 with nugget 1e-5 (ill-conditioned blocks), mixed precision."""
     _check(wl.large(), fb.PREC_MIXED, 64, 150, np.random.default_rng(22))
+
+
+def _oracle_rows(Xd, Y, nb, k, ok, rows):
+    """The oracle's rows of C for the given training points (n x k x r array,
+    zero elsewhere)."""
+    rows = np.unique(np.asarray(rows))
+    Cr, st = oracle.precompute(Xd, Y, nb, k, ok, rows=rows)
+    assert not st.any()
+    Cfull = np.zeros((Xd.shape[0], k, Y.shape[1]))
+    Cfull[rows] = Cr
+    return Cfull
+
+
+@pytest.fixture(scope="module")
+def borehole_ref():
+    """The oracle's side of the full-size borehole check: sampled kNN rows,
+    nearest points of sampled test points, and for six of them the FP64 and
+    long-double means (long double is slow where it is emulated)."""
+    W = wl.borehole()
+    rng = np.random.default_rng(23)
+    ok, _ = kern_pair(W.kernel)
+    rows = np.sort(rng.choice(W.n, 40, replace=False))
+    ref_i, ref_k = oracle.knn(W.X, W.X[rows], W.k - 1, rows)
+    tz = np.sort(rng.choice(W.m, 40, replace=False))
+    ref_near, _ = oracle.knn(W.X, W.Z[tz], 1)
+    return W, ok, rows, ref_i, ref_k, tz, ref_near[:, 0]
+
+
+@pytest.mark.parametrize("prec", [fb.PREC_FP64, fb.PREC_MIXED])
+def test_borehole_full_size(cuda, prec, borehole_ref):
+    """The borehole emulator at the bench's sizes (n = 100,000, m = 20,000,
+    d = 8, k = 150, RBF rho = 43.27, tau^2 = 1e-8).  Its blocks have condition
+    numbers near 1e10, so two FP64 evaluations in different orders differ by
+    ~1e-6 relative: the means are compared with the oracle's long-double
+    evaluation (Eqs. 6-7 for the same nearest point), and the GPU's error may
+    be at most ten times the FP64 oracle's own."""
+    W, ok, rows, ref_i, ref_k, tz, ref_near = borehole_ref
+    _, gk = kern_pair(W.kernel)
+    X, Y, Z = dev(W.X), dev(W.Y), dev(W.Z)
+    nbr, dist = fb.fmgp_build_knn(X, W.k - 1, with_dist=True)
+    C, st = fb.fmgp_precompute(X, Y, nbr, W.k, gk, prec)
+    yh, near = fb.fmgp_predict(X, nbr, C, W.k, gk, Z, prec)
+    torch.cuda.synchronize()
+    s = st.cpu().numpy()
+    assert np.all((s == fb.BLOCK_OK) | (s == fb.BLOCK_FP64_RETRY))
+    nb = nbr.cpu().numpy()
+    np.testing.assert_array_equal(nb[rows], ref_i)
+    np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
+    nr = near.cpu().numpy()
+    np.testing.assert_array_equal(nr[tz], ref_near)
+    j6 = ref_near[:6]
+    tab = _oracle_table(W.X, W.k - 1, j6)
+    Cfull = _oracle_rows(W.X, W.Y, tab, W.k, ok, j6)
+    y64 = oracle.predict_given(W.X, tab, Cfull, ok, W.Z[tz[:6]], j6)
+    yld = oracle.fit_predict_ld(W.X, W.Y, tab, W.k, ok, W.Z[tz[:6]], j6)
+    t6 = tz[:6]
+    e_gpu = rel_rms(yh.cpu().numpy()[t6], yld)
+    e_64 = rel_rms(y64, yld)
+    assert e_gpu <= max(10 * e_64, 1e-10), (e_gpu, e_64)
+    # the emulator is accurate (the bench's RMSE)
+    assert np.sqrt(np.mean((yh.cpu().numpy() - W.Ztrue) ** 2)) < 2e-2
+
+
+def test_borehole_mcmc_full_size(cuda):
+    """MCMC on the full borehole model: every decision of 16 chains x 40 steps
+    is replayed with the oracle's emulator (its own nearest point and row of
+    C at each visited input); the decisions must agree wherever the oracle's
+    margin is not within the emulators' rounding difference of zero."""
+    W = wl.borehole()
+    e = W.extra
+    ok, gk = kern_pair(W.kernel)
+    X, Y = dev(W.X), dev(W.Y)
+    nbr, _ = fb.fmgp_build_knn(X, W.k - 1)
+    C, _ = fb.fmgp_precompute(X, Y, nbr, W.k, gk, fb.PREC_FP64)
+    model = fb.FmgpModel(X, nbr, C, W.k, gk, fb.PREC_FP64)
+    steps, chains, sigma, step = 40, 16, 1.0, 0.3
+    g = np.random.default_rng(2025)
+    noise = g.standard_normal((steps, chains))
+    expo = g.exponential(1.0, (steps, chains))
+    x0 = g.uniform(e["lo"], e["hi"], chains)
+    S, acc, _ = model.mcmc(e["z0"], e["dim"], e["lo"], e["hi"], e["f_obs"], sigma, step, x0,
+                           dev(noise), dev(expo))
+    S = S.cpu().numpy()
+    model.close()
+    cache = {}
+
+    def emulate(x):
+        if x not in cache:
+            z = e["z0"].copy()
+            z[e["dim"]] = x
+            j, _ = oracle.knn(W.X, z[None, :], 1)
+            tab = _oracle_table(W.X, W.k - 1, j[:, 0])
+            Cfull = _oracle_rows(W.X, W.Y, tab, W.k, ok, j[:, 0])
+            cache[x] = oracle.predict_given(W.X, tab, Cfull, ok, z[None, :], j[:, 0])[0, 0]
+        return cache[x]
+
+    checked = skipped = 0
+    for c in range(chains):
+        x = x0[c]
+        for t in range(steps):
+            xp = x + step * noise[t, c]
+            if xp < e["lo"] or xp > e["hi"]:
+                assert S[t, c] == x
+                continue
+            ep, ec = e["f_obs"] - emulate(xp), e["f_obs"] - emulate(x)
+            margin = (ec * ec - ep * ep) / (2 * sigma * sigma) + expo[t, c]
+            if abs(margin) < 1e-2:
+                skipped += 1
+                x = S[t, c]  # follow the GPU chain past a near-tie
+                continue
+            assert S[t, c] == (xp if margin > 0 else x), (c, t, margin)
+            x = S[t, c]
+            checked += 1
+    # near-zero margins (|margin| < 1e-2, about 1 % of decisions here) may go
+    # either way; every other decision must match
+    assert checked > 0.45 * chains * steps and skipped < 0.05 * chains * steps

@@ -141,10 +141,9 @@ def test_fp64_pipeline_spatial_shrunk(cuda, nu):
     W = wl.spatial(n=20_000, m=3_000, nu=nu)
     ok, gk = kern_pair(W.kernel)
     nbr, dist, C, st, yh, near = _gpu_pipeline(W, 50, 49, fb.PREC_FP64, gk)
-    nb = nbr.cpu().numpy()
+    nb, _ = oracle.self_knn(W.X, 49)  # the oracle's own table
+    np.testing.assert_array_equal(nbr.cpu().numpy(), nb)
     rows = np.random.default_rng(1).choice(W.n, 400, replace=False)
-    ref_i, _ = oracle.knn(W.X, W.X[rows], 49, rows)
-    np.testing.assert_array_equal(nb[rows], ref_i)
     Cr, _ = oracle.precompute(W.X, W.Y, nb, 50, ok, rows=rows)
     assert rel_rms(C.cpu().numpy()[rows], Cr) < FP64_TOL
     Cfull, _ = oracle.precompute(W.X, W.Y, nb, 50, ok)
@@ -158,9 +157,8 @@ def test_fp64_multi_response_highdim_small(cuda):
     ok, gk = kern_pair(W.kernel)
     X = dev(W.X)
     nbr, _ = fb.fmgp_build_knn(X, 29)
-    nb = nbr.cpu().numpy()
-    ref_i, _ = oracle.self_knn(W.X.astype(np.float64), 29)
-    np.testing.assert_array_equal(nb, ref_i)
+    nb, _ = oracle.self_knn(W.X.astype(np.float64), 29)  # the oracle's own table
+    np.testing.assert_array_equal(nbr.cpu().numpy(), nb)
     C, st = fb.fmgp_precompute(X, dev(W.Y), nbr, 30, gk, fb.PREC_FP64)
     Cr, _ = oracle.precompute(W.X, W.Y, nb, 30, ok)
     assert rel_rms(C.cpu().numpy(), Cr) < FP64_TOL
@@ -176,7 +174,8 @@ def test_fp64_precompute_k_range(cuda, k):
     ok, gk = kern_pair(W.kernel)
     kq = max(k - 1, 1)
     nbr, _ = fb.fmgp_build_knn(dev(W.X), kq)
-    nb = nbr.cpu().numpy()
+    nb, _ = oracle.self_knn(W.X, kq)  # the oracle's own table
+    np.testing.assert_array_equal(nbr.cpu().numpy(), nb)
     C, st = fb.fmgp_precompute(dev(W.X), dev(W.Y), nbr, k, gk, fb.PREC_FP64)
     Cr, _ = oracle.precompute(W.X, W.Y, nb, k, ok)
     assert rel_rms(C.cpu().numpy(), Cr) < FP64_TOL
@@ -278,18 +277,24 @@ def _mixed_check(W, k, kq, n_rows=None, tol=MIXED_TOL):
     ok, gk = kern_pair(W.kernel)
     X = dev(W.X)
     nbr, _ = fb.fmgp_build_knn(X, kq)
-    nb = nbr.cpu().numpy()
     C, st = fb.fmgp_precompute(X, dev(W.Y), nbr, k, gk, fb.PREC_MIXED)
     yh, near = fb.fmgp_predict(X, nbr, C, k, gk, dev(W.Z), fb.PREC_MIXED)
     torch.cuda.synchronize()
     s = st.cpu().numpy()
     assert np.all((s == fb.BLOCK_OK) | (s == fb.BLOCK_FP64_RETRY))
-    near = near.cpu().numpy()
-    rows = np.unique(near)
+    # the oracle's own nearest points and neighbour rows (for the rows needed)
+    onear, _ = oracle.knn(W.X, W.Z, 1)
+    onear = onear[:, 0]
+    np.testing.assert_array_equal(near.cpu().numpy(), onear)
+    rows = np.unique(onear).astype(np.int64)
+    nb_rows, _ = oracle.knn(W.X, W.X[rows], kq, rows)
+    np.testing.assert_array_equal(nbr.cpu().numpy()[rows], nb_rows)
+    nb = np.zeros((W.n, kq), np.int32)
+    nb[rows] = nb_rows
     Cr, _ = oracle.precompute(W.X, W.Y, nb, k, ok, rows=rows)
     Cfull = np.zeros((W.n, k, W.r))
     Cfull[rows] = Cr
-    yr = oracle.predict_given(W.X, nb, Cfull, ok, W.Z, near)
+    yr = oracle.predict_given(W.X, nb, Cfull, ok, W.Z, onear)
     err = rel_rms(yh.cpu().numpy(), yr)
     assert err < tol, err
     cerr = rel_rms(coeffs_to_f64(C, fb.PREC_MIXED)[rows], Cr)
@@ -342,7 +347,8 @@ def test_mixed_fp64_fallback_on_fp32_failure(cuda):
     C, st = fb.fmgp_precompute(Xd, dev(Y), nbr, 12, gk, fb.PREC_MIXED)
     s = st.cpu().numpy()
     assert (s == fb.BLOCK_FP64_RETRY).sum() > 0
-    nb = nbr.cpu().numpy()
+    nb, _ = oracle.self_knn(X, 11)  # the oracle's own table
+    np.testing.assert_array_equal(nbr.cpu().numpy(), nb)
     Cr, str_ = oracle.precompute(X, Y, nb, 12, ok)
     Cg = coeffs_to_f64(C, fb.PREC_MIXED)
     retry = (s == fb.BLOCK_FP64_RETRY) & (str_ == 0)
@@ -359,6 +365,9 @@ def test_loocv_mixed(cuda, precision):
     X = dev(W.X)
     nbr, _ = fb.fmgp_build_knn(X, 50)
     Q, res = fb.fmgp_loocv_objective(X, dev(W.Y), nbr, 50, dev(W.batch), gk, precision)
-    Qr, resr = oracle.loocv(W.X, W.Y, nbr.cpu().numpy(), 50, W.batch, ok)
+    nb_rows, _ = oracle.knn(W.X, W.X[W.batch], 50, W.batch)  # the oracle's own rows
+    nb = np.zeros((W.n, 50), np.int32)
+    nb[W.batch] = nb_rows
+    Qr, resr = oracle.loocv(W.X, W.Y, nb, 50, W.batch, ok)
     assert abs(Q - Qr) / abs(Qr) < MIXED_TOL
     assert rel_rms(res.cpu().numpy(), resr) < MIXED_TOL
