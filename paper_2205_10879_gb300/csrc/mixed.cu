@@ -271,6 +271,7 @@ template <int MODE, int NS, int CB>
 __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mixed_kernel(BlockArgs args, MixedArgs mx,
                                                           MixedLayout lay) {
   constexpr bool LOO = MODE == kModeLoocv;
+  static_assert(CB % 4 == 0, "panels start at multiples of 4 (float4 reads of finished columns)");
   extern __shared__ __align__(16) unsigned char smem[];
   const int wpb = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -467,6 +468,7 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
             if (row < k) acc[s] = df_add(YS[row * r + c], df_neg(df_mul(kp.diag, XV[row * r + c])));
           }
           int cb = 0;  // b(b-1)/2
+#pragma unroll 2
           for (int b = 0; b < k; ++b) {
             const dfl xb = XV[b * r + c];
 #pragma unroll
