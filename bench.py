@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-highdim", action="store_true")
     p.add_argument("--no-borehole", action="store_true")
     p.add_argument("--no-subsample", action="store_true")
+    p.add_argument("--no-graph", action="store_true")
     p.add_argument("--mcmc-chains", type=int, default=8192)
     p.add_argument("--mcmc-steps", type=int, default=1221)
     return p.parse_args()
@@ -388,6 +389,8 @@ def run_ours(a):
     }
     if not a.no_highdim:
         line["highdim_knn"] = highdim_knn_bench(a, dev, steps=a.steps, warmup=1)
+    if not a.no_graph and a.workload == "spatial":
+        line["cuda_graph"] = graph_bench(X, Y, Z, k, kq, gk, prec, nbr, C, st, yh, near)
     if not a.no_subsample and a.workload == "spatial":
         line["subsampled"] = subsample_bench(W, X, Y, Z, nbr, k, gk, prec, rmse, dev)
     if not a.no_borehole:
@@ -439,6 +442,53 @@ def highdim_knn_bench(a, dev, steps, warmup):
             "uncertified_queries": fb.diag_counter(2),
             "roofline_call": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                               "frac": ach / peak, "note": "whole call incl. pack/select/re-rank"}}
+
+
+# ------------------------------------------------------------ CUDA graph ----
+def graph_bench(X, Y, Z, k, kq, gk, prec, nbr, C, st, yh, near, reps=5):
+    """kNN table + precompute + prediction of the step captured once in a CUDA
+    graph and replayed, against the same three calls launched eagerly (LOOCV
+    returns its objective to the host and stays outside the graph)."""
+    import torch
+    from paper_2205_10879_gb300 import _binding as fb
+
+    def three():
+        fb.fmgp_build_knn(X, kq, nbr_out=nbr)
+        fb.fmgp_precompute(X, Y, nbr, k, gk, prec, C_out=C, status_out=st)
+        fb.fmgp_predict(X, nbr, C, k, gk, Z, prec, Yhat_out=yh, nearest_out=near)
+
+    def timed(f):
+        f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    eager_ms = timed(three)
+    ref = yh.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        three()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    l0 = fb.kernel_launches()
+    with torch.cuda.graph(g):
+        three()
+    launches = fb.kernel_launches() - l0
+    graph_ms = timed(g.replay)
+    same = bool(torch.equal(yh, ref))
+    del g
+    return {"phases": "knn + precompute + predict", "eager_ms": eager_ms, "graph_replay_ms": graph_ms,
+            "kernels_in_graph": int(launches), "replay_equals_eager": same}
 
 
 # ------------------------------------------------ subsampled precompute ----
