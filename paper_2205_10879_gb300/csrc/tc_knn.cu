@@ -308,23 +308,17 @@ __global__ void __launch_bounds__(256) select_merge_kernel(
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= m) return;
-  WarpTopK<S> top;
+  WarpTopK32<S> top;
   top.init(L);
   if (!first) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int g = lane * S + s;
       const int j = cand[q * L + g];
-      top.k[s] = j == INT_MAX ? ~0ull : (unsigned long long)__float_as_uint(ckey[q * L + g]);
+      top.k[s] = j == INT_MAX ? ~0u : __float_as_uint(ckey[q * L + g]);
       top.i[s] = j;
     }
-    unsigned long long mk = top.k[0];
-    int mi = top.i[0];
-#pragma unroll
-    for (int s = 1; s < S; ++s)
-      if (s == top.ts) { mk = top.k[s]; mi = top.i[s]; }
-    top.tk = __shfl_sync(kFull, mk, top.tl);
-    top.ti = __shfl_sync(kFull, mi, top.tl);
+    top.refresh_threshold();
   }
   const float* row = Dc + q * ld;
   const int64_t cols = min(ncols, n - col0);
@@ -341,10 +335,10 @@ __global__ void __launch_bounds__(256) select_merge_kernel(
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int64_t j = col0 + c + e;
-      unsigned long long ck = ~0ull;
+      unsigned int ck = ~0u;
       int ci = INT_MAX;
       if (c + e < cols && !(exclude_self && j == q)) {
-        const unsigned long long v = (unsigned long long)__float_as_uint(fmaxf(v4[e], 0.0f));
+        const unsigned int v = __float_as_uint(fmaxf(v4[e], 0.0f));
         if (v <= top.tk) { ck = v; ci = (int)j; }
       }
       top.offer(ck, ci, lane);
@@ -355,12 +349,12 @@ __global__ void __launch_bounds__(256) select_merge_kernel(
     const int g = lane * S + s;
     if (g < L) {
       cand[q * L + g] = top.i[s];
-      ckey[q * L + g] = top.i[s] == INT_MAX ? 0.f : __uint_as_float((unsigned int)top.k[s]);
+      ckey[q * L + g] = top.i[s] == INT_MAX ? 0.f : __uint_as_float(top.k[s]);
     }
   }
   // largest approximate distance in the list (position L-1); +inf if not full
   if (lane == 0)
-    dL[q] = top.full() ? __uint_as_float((unsigned int)top.tk) : __int_as_float(0x7f800000);
+    dL[q] = top.full() ? __uint_as_float(top.tk) : __int_as_float(0x7f800000);
 }
 
 // Exact re-rank with certificate; uncertified queries go to the fallback list.

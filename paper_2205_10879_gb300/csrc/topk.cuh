@@ -86,6 +86,77 @@ struct WarpTopK {
   }
 };
 
+// The same list with 32-bit keys (the bits of non-negative FP32 values, whose
+// order as unsigned integers is their numeric order): half the compare and
+// shuffle work of the 64-bit list, for searches that rank FP32 distances.
+template <int L>
+struct WarpTopK32 {
+  unsigned int k[L];
+  int i[L];
+  unsigned int tk;  // key of position kq-1, ~0 while not full
+  int ti;
+  int tl, ts;
+
+  __device__ __forceinline__ static bool less(unsigned int ka, int ia, unsigned int kb, int ib) {
+    return ka < kb || (ka == kb && ia < ib);
+  }
+
+  __device__ __forceinline__ void init(int kq) {
+#pragma unroll
+    for (int s = 0; s < L; ++s) { k[s] = ~0u; i[s] = INT_MAX; }
+    tk = ~0u;
+    ti = INT_MAX;
+    tl = (kq - 1) / L;
+    ts = (kq - 1) % L;
+  }
+
+  __device__ __forceinline__ bool full() const { return tk != ~0u; }
+
+  __device__ __forceinline__ void refresh_threshold() {
+    unsigned int mk = k[0];
+    int mi = i[0];
+#pragma unroll
+    for (int s = 1; s < L; ++s)
+      if (s == ts) { mk = k[s]; mi = i[s]; }
+    tk = __shfl_sync(kFull, mk, tl);
+    ti = __shfl_sync(kFull, mi, tl);
+  }
+
+  __device__ __forceinline__ void insert(unsigned int bk, int bi, int lane) {
+    int cnt = 0;
+#pragma unroll
+    for (int s = 0; s < L; ++s) cnt += less(k[s], i[s], bk, bi) ? 1 : 0;
+    const int pos = __reduce_add_sync(kFull, cnt);
+    const unsigned int pk = __shfl_up_sync(kFull, k[L - 1], 1);
+    const int pi = __shfl_up_sync(kFull, i[L - 1], 1);
+#pragma unroll
+    for (int s = L - 1; s >= 0; --s) {
+      const int g = lane * L + s;
+      if (g > pos) {
+        if (s > 0) { k[s] = k[s - 1]; i[s] = i[s - 1]; }
+        else { k[s] = pk; i[s] = pi; }
+      } else if (g == pos) {
+        k[s] = bk;
+        i[s] = bi;
+      }
+    }
+    refresh_threshold();
+  }
+
+  // Offer one candidate per lane (ck = ~0 for none).
+  __device__ __forceinline__ void offer(unsigned int ck, int ci, int lane) {
+    unsigned hits = __ballot_sync(kFull, less(ck, ci, tk, ti));
+    while (hits) {
+      const int src = __ffs(hits) - 1;
+      const unsigned int bk = __shfl_sync(kFull, ck, src);
+      const int bi = __shfl_sync(kFull, ci, src);
+      insert(bk, bi, lane);
+      hits &= ~(1u << src);
+      hits &= __ballot_sync(kFull, less(ck, ci, tk, ti));
+    }
+  }
+};
+
 // Warp argmin of (key, index) pairs.
 __device__ __forceinline__ void warp_argmin(unsigned long long& bk, int& bi) {
 #pragma unroll
