@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-borehole", action="store_true")
     p.add_argument("--no-subsample", action="store_true")
     p.add_argument("--no-graph", action="store_true")
+    p.add_argument("--no-training", action="store_true")
     p.add_argument("--mcmc-chains", type=int, default=8192)
     p.add_argument("--mcmc-steps", type=int, default=1221)
     return p.parse_args()
@@ -389,6 +390,8 @@ def run_ours(a):
     }
     if not a.no_highdim:
         line["highdim_knn"] = highdim_knn_bench(a, dev, steps=a.steps, warmup=1)
+    if not a.no_training and a.workload == "spatial":
+        line["training"] = training_bench(X, Y, batch, k, nbr, gk, prec)
     if not a.no_graph and a.workload == "spatial":
         line["cuda_graph"] = graph_bench(X, Y, Z, k, kq, gk, prec, nbr, C, st, yh, near)
     if not a.no_subsample and a.workload == "spatial":
@@ -442,6 +445,27 @@ def highdim_knn_bench(a, dev, steps, warmup):
             "uncertified_queries": fb.diag_counter(2),
             "roofline_call": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                               "frac": ach / peak, "note": "whole call incl. pack/select/re-rank"}}
+
+
+# -------------------------------------------------------------- training ----
+def training_bench(X, Y, batch, k, nbr, gk, prec):
+    """Hyperparameter training (Algorithm 1): L-BFGS-B on log rho over the
+    LOOCV objective of the step's batch (each evaluation on the GPU), started
+    from half the workload's length scale."""
+    import torch
+    from paper_2205_10879_gb300 import _binding as fb
+    from paper_2205_10879_gb300 import training
+    start = fb.Kernel(gk.kind, gk.nu, gk.length_scale * 0.5, gk.variance, gk.nugget)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = training.optimize_hyperparameters(X, Y, batch, k, start, params=("length_scale",),
+                                            precision=prec, nbr=nbr)
+    wall = time.perf_counter() - t0
+    return {"params": "length_scale", "start": start.length_scale,
+            "found": res["theta"]["length_scale"], "workload_value": gk.length_scale,
+            "q_start": res["q_start"], "q_best": res["q_best"], "evaluations": res["evaluations"],
+            "seconds": wall, "evaluations_per_s": res["evaluations"] / wall,
+            "batch": int(batch.numel()), "k": k}
 
 
 # ------------------------------------------------------------ CUDA graph ----
