@@ -5,6 +5,7 @@
 #include <math.h>
 #include <atomic>
 #include <map>
+#include <tuple>
 #include <string>
 #include <mutex>
 #include "block.cuh"
@@ -41,6 +42,27 @@ cudaError_t ensure_smem(const void* func, size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) cur = bytes;
   return e;
+}
+
+int active_ctas(const void* func, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find({dev, func, threads, smem});
+    if (it != cache.end()) return it->second;
+  }
+  int nb = 0;
+  if (smem > 227 * 1024 || ensure_smem(func, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 0;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[{dev, func, threads, smem}] = nb;
+  return nb;
 }
 
 int num_sms() {
@@ -139,23 +161,6 @@ static bool prec_ok(fmgp_precision p) {
     }                                 \
   } while (0)
 
-// Warps per CTA for a block kernel: the choice that keeps the most warps
-// resident per SM given bytes_per_warp of shared memory (227 KB per SM, 1 KB
-// reserved per CTA); ties go to the larger CTA.
-static int pick_warps(size_t bytes_per_warp, int requested) {
-  if (requested > 0) return requested;
-  const size_t sm_bytes = 227 * 1024;
-  int best = 1, best_total = 0;
-  for (int w : {8, 6, 4, 2, 1}) {
-    const size_t cta = (size_t)w * bytes_per_warp + 1024;
-    if ((size_t)w * bytes_per_warp > 200 * 1024) continue;
-    const int ctas = (int)(sm_bytes / cta);
-    const int total = w * std::min(ctas, 32 / w);
-    if (total > best_total) { best_total = total; best = w; }
-  }
-  return best;
-}
-
 TuneParams& tune_params() {
   static TuneParams tp;
   return tp;
@@ -191,11 +196,12 @@ static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, int mode,
               a.r, std::max(bytes, a.layout.bytes_per_warp));
     return FMGP_EUNSUPPORTED;
   }
+  // warps per CTA: the user's or the autotuner's choice, else (0) the
+  // launchers pick the one with the most resident warps per SM
   int req = tune_params().block_warps;
   if (req == 0) req = tuned_block_warps((int)precision, a.k, a.d, a.r, (int)dtype);
-  const int warps = pick_warps(bytes, req);
-  if (precision == FMGP_PREC_FP64) return launch_block_f64(a, X, dtype, mode, warps, s);
-  return run_block_mixed(a, X, dtype, mode, warps, kern, ws, s);
+  if (precision == FMGP_PREC_FP64) return launch_block_f64(a, X, dtype, mode, req, s);
+  return run_block_mixed(a, X, dtype, mode, req, kern, ws, s);
 }
 
 // Deterministic single-CTA sum of the LOOCV residuals: thread t adds

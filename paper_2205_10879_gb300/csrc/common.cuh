@@ -127,6 +127,11 @@ int cuda_fail(cudaError_t e, const char* what);
 // graphs after a warm-up call) make no attribute calls.
 cudaError_t ensure_smem(const void* func, size_t bytes);
 
+// CTAs of `func` (threads per CTA, dynamic shared memory bytes) resident per
+// SM, from the CUDA occupancy calculator (raises the function's dynamic
+// shared-memory limit first; cached per device).  0 if it cannot run.
+int active_ctas(const void* func, int threads, size_t smem);
+
 #define FMGP_CUDA_TRY(call)                                  \
   do {                                                       \
     cudaError_t _e = (call);                                 \

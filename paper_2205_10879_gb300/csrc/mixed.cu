@@ -681,15 +681,33 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
                : S == 3 ? pick(std::integral_constant<int, 3>{})
                : S == 4 ? pick(std::integral_constant<int, 4>{})
                         : pick(std::integral_constant<int, 5>{});
+  int nb = 0;
   {
     // the 2-slot instantiation is compiled for at most 192 threads (6 warps)
     cudaFuncAttributes fa;
     FMGP_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)kern_fn));
-    if (warps * 32 > fa.maxThreadsPerBlock) warps = fa.maxThreadsPerBlock / 32;
+    const int maxw = fa.maxThreadsPerBlock / 32;
+    if (warps > maxw) warps = maxw;
+    if (warps <= 0) {  // the CTA size with the most resident warps per SM (ties: larger)
+      int best = 0;
+      for (int w : {8, 6, 4, 3, 2, 1}) {
+        if (w > maxw) continue;
+        const int c = active_ctas((const void*)kern_fn, w * 32, kMixedHead + lay.bytes * w);
+        if (c * w > best) { best = c * w; warps = w; nb = c; }
+      }
+      if (!best) {
+        set_error("neighbourhood blocks of %zu bytes do not fit an SM", lay.bytes);
+        return FMGP_EUNSUPPORTED;
+      }
+    } else {
+      nb = active_ctas((const void*)kern_fn, warps * 32, kMixedHead + lay.bytes * warps);
+    }
   }
   const size_t smem = kMixedHead + lay.bytes * warps;
   const int64_t need = (a.count + warps - 1) / warps;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * 16));
+  // a whole number of waves (8) of the CTAs the SMs hold at once: no partial
+  // last wave, and CTAs that finish early are replaced
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * std::max(nb, 1) * 8));
   FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
   FMGP_LAUNCH(kern_fn<<<blocks, warps * 32, smem, s>>>(a, mx, lay));
   FMGP_CUDA_TRY(cudaGetLastError());

@@ -427,23 +427,41 @@ int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mo
     FMGP_CUDA_TRY(cudaGetLastError());
     return FMGP_OK;
   }
-  const size_t smem = a.layout.bytes_per_warp * warps;
-  const int sms = num_sms();
-  const int64_t need = (a.count + warps - 1) / warps;
-  if (blocks <= 0) blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 16));
-  if (dtype == FMGP_F64) {
-    auto kern = mode == kModeLoocv    ? block_f64_kernel<double, kModeLoocv>
-                : mode == kModeMuygps ? block_f64_kernel<double, kModeMuygps>
-                                      : block_f64_kernel<double, kModePrecompute>;
-    FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
-    FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const double*)X));
+  const void* kern;
+  if (dtype == FMGP_F64)
+    kern = mode == kModeLoocv    ? (const void*)block_f64_kernel<double, kModeLoocv>
+           : mode == kModeMuygps ? (const void*)block_f64_kernel<double, kModeMuygps>
+                                 : (const void*)block_f64_kernel<double, kModePrecompute>;
+  else
+    kern = mode == kModeLoocv    ? (const void*)block_f64_kernel<float, kModeLoocv>
+           : mode == kModeMuygps ? (const void*)block_f64_kernel<float, kModeMuygps>
+                                 : (const void*)block_f64_kernel<float, kModePrecompute>;
+  const size_t per_warp = a.layout.bytes_per_warp;
+  int nb = 0;
+  if (warps <= 0) {  // the CTA size with the most resident warps per SM (ties: larger)
+    int best = 0;
+    for (int w : {8, 6, 4, 3, 2, 1}) {
+      const int c = active_ctas(kern, w * 32, (size_t)w * per_warp);
+      if (c * w > best) { best = c * w; warps = w; nb = c; }
+    }
+    if (!best) {
+      set_error("neighbourhood blocks of %zu bytes do not fit an SM", per_warp);
+      return FMGP_EUNSUPPORTED;
+    }
   } else {
-    auto kern = mode == kModeLoocv    ? block_f64_kernel<float, kModeLoocv>
-                : mode == kModeMuygps ? block_f64_kernel<float, kModeMuygps>
-                                      : block_f64_kernel<float, kModePrecompute>;
-    FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
-    FMGP_LAUNCH(kern<<<blocks, warps * 32, smem, stream>>>(a, (const float*)X));
+    nb = active_ctas(kern, warps * 32, (size_t)warps * per_warp);
   }
+  const size_t smem = per_warp * warps;
+  const int64_t need = (a.count + warps - 1) / warps;
+  // a whole number of waves (8) of the CTAs the SMs hold at once: no partial
+  // last wave, and CTAs that finish early are replaced
+  if (blocks <= 0)
+    blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * std::max(nb, 1) * 8));
+  FMGP_CUDA_TRY(ensure_smem(kern, smem));
+  if (dtype == FMGP_F64)
+    FMGP_LAUNCH(((void (*)(BlockArgs, const double*))kern)<<<blocks, warps * 32, smem, stream>>>(a, (const double*)X));
+  else
+    FMGP_LAUNCH(((void (*)(BlockArgs, const float*))kern)<<<blocks, warps * 32, smem, stream>>>(a, (const float*)X));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
