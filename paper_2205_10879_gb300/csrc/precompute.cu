@@ -407,10 +407,17 @@ int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mo
                      cudaStream_t stream, int blocks) {
   if (a.layout.bytes_per_warp > kCtaBlockBytes) {
     const size_t smem = a.layout.bytes_per_warp;
-    // persistent: as many CTAs as fit on the SMs at once
-    const int fit = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+    // eight whole waves of the CTAs the SMs hold at once
+    const void* fk = dtype == FMGP_F64
+                         ? (mode == kModeLoocv    ? (const void*)block_f64_cta_kernel<double, kModeLoocv>
+                            : mode == kModeMuygps ? (const void*)block_f64_cta_kernel<double, kModeMuygps>
+                                                  : (const void*)block_f64_cta_kernel<double, kModePrecompute>)
+                         : (mode == kModeLoocv    ? (const void*)block_f64_cta_kernel<float, kModeLoocv>
+                            : mode == kModeMuygps ? (const void*)block_f64_cta_kernel<float, kModeMuygps>
+                                                  : (const void*)block_f64_cta_kernel<float, kModePrecompute>);
+    const int fit = std::max(1, active_ctas(fk, kCtaThreads, smem));
     const int grid = blocks > 0 ? blocks
-                                : (int)std::max<int64_t>(1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit));
+                                : (int)std::max<int64_t>(1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit * 8));
     if (dtype == FMGP_F64) {
       auto kern = mode == kModeLoocv    ? block_f64_cta_kernel<double, kModeLoocv>
                   : mode == kModeMuygps ? block_f64_cta_kernel<double, kModeMuygps>
