@@ -731,10 +731,23 @@ def oracle_sample(W, a, samples):
 
 def oracle_baseline(W, a):
     """The spatial workload is timed whole (a few seconds on 16 cores); the
-    10^7-point workload on a sample of about the same cost, extrapolated."""
+    10^7-point workload on a sample of about the same cost, extrapolated.
+    A one-thread run of a small sample is reported beside it."""
+    import oracle
     if a.workload == "large":
-        return oracle_sample(W, a, samples=(6000, 6000, 2000))
-    return oracle_full(W)
+        r = oracle_sample(W, a, samples=(6000, 6000, 2000))
+    else:
+        r = oracle_full(W)
+    cores = oracle.max_threads()
+    oracle.set_threads(1)
+    try:
+        one = oracle_sample(W, a, samples=(300, 300, 100) if a.workload == "large"
+                            else (2000, 2000, 500))
+    finally:
+        oracle.set_threads(cores)
+    r["single_thread"] = {"value": one["value"], "unit": "points/s", "cores": 1,
+                          "sample": one["sample"], "sample_seconds": one["sample_seconds"]}
+    return r
 
 
 def run_reference(a):
