@@ -398,6 +398,9 @@ const char* fmgp_version(void);
  *   "grid_target"  mean training points per grid cell of the d <= 3 search (default 12)
  *   "block_warps"  warps per CTA of the neighbourhood kernels, 0 = automatic
  *   "tensor_cores" 1 = tcgen05 candidate search for kNN at d >= 16 (default), 0 = off
+ *   "tc_fused_select" 1 = for kq <= 32 the candidates are selected inside the
+ *                  tcgen05 distance kernel (default), 0 = distances go through
+ *                  a pass buffer in HBM and a separate selection kernel
  * Process-wide; returns FMGP_EINVAL for an unknown key or a value out of range.
  */
 int fmgp_tune_set(const char* key, double value);

@@ -282,6 +282,8 @@ int fmgp_tune_set(const char* key, double value) {
     tp.block_warps = (int)value;
   } else if (k == "tensor_cores") {
     tp.use_tensor_cores = value != 0.0;
+  } else if (k == "tc_fused_select") {
+    tp.tc_fused_select = value != 0.0;
   } else {
     set_error("unknown tuning key '%s'", key);
     return FMGP_EINVAL;
@@ -296,6 +298,7 @@ double fmgp_tune_get(const char* key) {
   if (k == "grid_target") return tp.grid_target;
   if (k == "block_warps") return tp.block_warps;
   if (k == "tensor_cores") return tp.use_tensor_cores ? 1.0 : 0.0;
+  if (k == "tc_fused_select") return tp.tc_fused_select ? 1.0 : 0.0;
   return -1.0;
 }
 

@@ -9,6 +9,7 @@ struct TuneParams {
   double grid_target = 12.0;     // mean training points per grid cell
   int block_warps = 0;           // warps per CTA for block kernels (0 = automatic)
   bool use_tensor_cores = true;  // tcgen05 candidate search for d >= 16
+  bool tc_fused_select = true;   // candidate selection inside the tcgen05 epilogue (kq <= 32)
 };
 
 TuneParams& tune_params();

@@ -8,9 +8,16 @@
 //    feature chunks of both operands (128-byte swizzle) through a 4-stage
 //    shared-memory ring, one thread issues tcgen05.mma (kind::f16, BF16 in,
 //    FP32 accumulate in tensor memory, M=128 N=256 K=16), and four epilogue
-//    warps read the double-buffered accumulator with tcgen05.ld and write the
-//    approximate squared distances ||q||^2 + ||x||^2 - 2 q.x to a pass buffer.
-// 3. select: one warp per query keeps the L smallest approximate distances.
+//    warps read the double-buffered accumulator with tcgen05.ld and form the
+//    approximate squared distances ||q||^2 + ||x||^2 - 2 q.x.  For kq <= 32
+//    each epilogue thread (one query) keeps the R smallest of its CTA's
+//    candidate range in registers (the fused form: nothing but R candidates
+//    per query and range reaches HBM); otherwise the distances go to a pass
+//    buffer.
+// 3. select: one warp per query keeps the L smallest approximate distances
+//    (of the per-range lists, or of the pass buffer).  With per-range lists,
+//    every candidate a range dropped is no closer than that range's R-th, so
+//    the smallest such R-th joins the list's L-th in the certificate bound.
 // 4. rerank: the L candidates get their canonical FP64 keys; the kq best are
 //    the result if a certificate holds: every candidate outside the list has
 //    approximate distance >= the list's largest, whose rigorous lower bound
@@ -37,6 +44,10 @@ constexpr int kBBytes = kTN * kTK * 2;   // 32 KB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kTcThreads = 192;          // warps 0-3 epilogue, 4 producer, 5 MMA
 constexpr size_t kTcSmem = (size_t)kStages * kStageBytes + 1024 + 256;
+// fused selection: per epilogue thread a 32-float row (stride 33) of the
+// current chunk's distances, indexed by the bits the thread pops
+constexpr int kScrStride = 33;
+constexpr size_t kTcSelSmem = kTcSmem + (size_t)kTM * kScrStride * sizeof(float);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -130,13 +141,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Insert (dv, col) into the ascending list bk/bi of R entries (static
+// indices only, so the list stays in registers).  Equal keys keep their
+// arrival order: columns arrive in increasing order, so ties go to the lower
+// index.
+template <int R>
+__device__ __forceinline__ void sorted_insert(float (&bk)[R], int (&bi)[R], float dv, int col) {
+#pragma unroll
+  for (int s = R - 1; s > 0; --s) {
+    const bool a = dv < bk[s - 1];
+    const bool b = dv < bk[s];
+    bi[s] = a ? bi[s - 1] : (b ? col : bi[s]);
+    bk[s] = a ? bk[s - 1] : (b ? dv : bk[s]);
+  }
+  if (dv < bk[0]) { bk[0] = dv; bi[0] = col; }
+}
+
 // Approximate squared distances of query block blockIdx.x against candidate
 // tiles tile0 + blockIdx.y*tpc .. (at most tpc tiles, not past tile_end).
-// out row q (query q), column (t - tile0)*256 + j holds candidate t*256 + j.
+// R == 0: out row q (query q), column (t - tile0)*256 + j holds candidate
+//   t*256 + j.
+// R > 0: the R smallest (clamped at 0; candidates >= n_valid and, with self,
+//   the query itself left out) as an ascending list at
+//   pkey/pidx[(q * gridDim.y + blockIdx.y) * R ..], INT_MAX past the end.
+template <int R>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
     const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX,
     const float* __restrict__ qnorm, const float* __restrict__ xnorm, int tile0, int tile_end,
-    int tpc, int k_chunks, int64_t ld_out, float* __restrict__ out, int* __restrict__ err) {
+    int tpc, int k_chunks, int64_t ld_out, float* __restrict__ out, int64_t n_valid, int self,
+    float* __restrict__ pkey, int32_t* __restrict__ pidx, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + (size_t)kStages * kStageBytes);
@@ -215,6 +248,66 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
         mma_commit(&tfull[b]);
       }
     }
+  } else if constexpr (R > 0) {  // epilogue warps 0-3, fused selection
+    const int row = warp * 32 + lane;
+    const int64_t qrow = (int64_t)qb * kTM + row;
+    const float qn = qnorm[qrow];
+    float* scr = reinterpret_cast<float*>(smem + (size_t)kStages * kStageBytes + 256) +
+                 row * kScrStride;
+    float bk[R];
+    int bi[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) { bk[s] = __int_as_float(0x7f800000); bi[s] = INT_MAX; }
+    for (int t = 0; t < n_tiles; ++t) {
+      const int b = t & 1;
+      const uint32_t u = (uint32_t)(t >> 1);
+      const bool ok = mbar_wait(&tfull[b], u & 1u, abort);
+      if (!__all_sync(kFull, ok)) { *abort = 1; break; }
+      tc_fence_after();
+      for (int c = 0; c < kTN / 32; ++c) {
+        uint32_t v[32];
+        __syncwarp();
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kTN + c * 32), v);
+        const int64_t gcol = (int64_t)(t_first + t) * kTN + c * 32;
+        const float4* xn4 = reinterpret_cast<const float4*>(xnorm + gcol);
+        const float thr = bk[R - 1];
+        unsigned int mask = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 x = xn4[q];
+          const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float dv = fmaxf(fmaf(-2.0f, __uint_as_float(v[4 * q + e]), qn + xs[e]), 0.0f);
+            scr[4 * q + e] = dv;
+            mask |= (dv < thr ? 1u : 0u) << (4 * q + e);
+          }
+        }
+        const int64_t lim = n_valid - gcol;
+        if (lim < 32) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
+        if (self) {
+          const int64_t sj = qrow - gcol;
+          if (sj >= 0 && sj < 32) mask &= ~(1u << sj);
+        }
+        // each lane pops its own hits: the warp pays for the busiest lane,
+        // not for the union of all lanes' hits
+        while (__any_sync(kFull, mask != 0u)) {
+          if (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            const float dv = scr[j];
+            if (dv < bk[R - 1]) sorted_insert<R>(bk, bi, dv, (int)(gcol + j));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+    float* okey = pkey + (qrow * gridDim.y + blockIdx.y) * R;
+    int32_t* oidx = pidx + (qrow * gridDim.y + blockIdx.y) * R;
+#pragma unroll
+    for (int s = 0; s < R; ++s) { okey[s] = bk[s]; oidx[s] = bi[s]; }
   } else {  // epilogue warps 0-3: TMEM lanes 32*warp .. 32*warp+31
     const int row = warp * 32 + lane;
     const float qn = qnorm[(int64_t)qb * kTM + row];
@@ -355,6 +448,50 @@ __global__ void __launch_bounds__(256) select_merge_kernel(
   // largest approximate distance in the list (position L-1); +inf if not full
   if (lane == 0)
     dL[q] = top.full() ? __uint_as_float(top.tk) : __int_as_float(0x7f800000);
+}
+
+// One warp per query: the L smallest of the per-range lists of the fused
+// distance pass (nseg ranges of R ascending entries each, INT_MAX past a
+// range's end).  dL = the smaller of the list's L-th key (+inf if not full)
+// and the smallest R-th key of a full range: every candidate outside the
+// list is at least that far.
+template <int S>
+__global__ void __launch_bounds__(256) select_parts_kernel(
+    const float* __restrict__ pkey, const int32_t* __restrict__ pidx, int64_t m, int nseg, int R,
+    int L, int32_t* __restrict__ cand, float* __restrict__ dL) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= m) return;
+  WarpTopK32<S> top;
+  top.init(L);
+  const int tot = nseg * R;
+  const float* kq_ = pkey + q * tot;
+  const int32_t* iq = pidx + q * tot;
+  float bound = __int_as_float(0x7f800000);
+  for (int base = 0; base < tot; base += 32) {
+    const int e = base + lane;
+    unsigned int ck = ~0u;
+    int ci = INT_MAX;
+    if (e < tot) {
+      const int j = iq[e];
+      if (j != INT_MAX) {
+        const float v = kq_[e];
+        ck = __float_as_uint(v);
+        ci = j;
+        if (e % R == R - 1) bound = fminf(bound, v);
+      }
+    }
+    top.offer(ck, ci, lane);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) bound = fminf(bound, __shfl_xor_sync(kFull, bound, o));
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int g = lane * S + s;
+    if (g < L) cand[q * L + g] = top.i[s];
+  }
+  if (lane == 0)
+    dL[q] = fminf(bound, top.full() ? __uint_as_float(top.tk) : __int_as_float(0x7f800000));
 }
 
 // Exact re-rank with certificate; uncertified queries go to the fallback list.
@@ -716,6 +853,13 @@ int pack(const T* X, int64_t rows, int d, int64_t rows_pad, int d_pad, Workspace
   return FMGP_OK;
 }
 
+// Per-range list length of the fused selection for kq neighbours (0 = the
+// pass-buffer form).
+int tc_fused_r(int kq) {
+  if (!tune_params().tc_fused_select) return 0;
+  return kq <= 4 ? 8 : (kq <= 32 ? 32 : 0);
+}
+
 template <typename T>
 int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool self,
              int32_t* idx_out, double* key_out, Workspace& ws, cudaStream_t s) {
@@ -741,38 +885,80 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   if (rc) return rc;
   const int n_tiles = (int)(n_pad / kTN), k_chunks = d_pad / kTK;
   const int64_t qblocks = m_pad / kTM;
-  // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
-  int chunk_tiles = (int)std::max<int64_t>(1, (int64_t)(1ll << 30) / (m_pad * 4 * kTN));
-  chunk_tiles = std::min(chunk_tiles, n_tiles);
-  // tiles per CTA: enough CTAs for two waves over the SMs
-  const int64_t want = 2ll * num_sms();
-  int tpc = chunk_tiles;
-  while (tpc > 1 && qblocks * ((chunk_tiles + tpc - 1) / tpc) < want) tpc = (tpc + 1) / 2;
-  const int ysplit = (chunk_tiles + tpc - 1) / tpc;
-  float* Dc = ws.get<float>((size_t)m_pad * chunk_tiles * kTN);
   int32_t* cand = ws.get<int32_t>((size_t)m * L);
-  float* ckey = ws.get<float>((size_t)m * L);
   float* dL = ws.get<float>(m);
   int* err = ws.get<int>(1);
   int* fb_list = ws.get<int>(m);
   int* fb_count = ws.get<int>(1);
-  if (!Dc || !cand || !ckey || !dL || !err || !fb_list || !fb_count) return FMGP_ENOMEM;
+  if (!cand || !dL || !err || !fb_list || !fb_count) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   FMGP_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(int), s));
-  FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel, kTcSmem));
-  const int64_t ldc = (int64_t)chunk_tiles * kTN;
   const int sblocks = ceil_div(m * 32, 256);
-  for (int t0 = 0; t0 < n_tiles; t0 += chunk_tiles) {
-    const int t1 = std::min(n_tiles, t0 + chunk_tiles);
-    FMGP_LAUNCH(tc_dist_kernel<<<dim3((unsigned)qblocks, (unsigned)ysplit), kTcThreads, kTcSmem, s>>>(
-        tmQ, tmX, qn2, xn2, t0, t1, tpc, k_chunks, ldc, Dc, err));
-    const int64_t col0 = (int64_t)t0 * kTN, ncols = (int64_t)(t1 - t0) * kTN;
-    const int first = t0 == 0 ? 1 : 0;
+  const int R = tc_fused_r(kq);
+  if (R > 0) {
+    // candidate ranges per query block: the split with the shortest
+    // makespan (whole waves of one CTA per SM x tiles per CTA, plus a tile's
+    // worth of start-up), at least 4 ranges for R = 32 and 2 for R = 8 so the
+    // ranges' R-th keys lie well beyond the kq nearest, and at most ~1 GB of
+    // per-range lists
+    const int sms = num_sms();
+    const int ys_lo = std::min(n_tiles, R == 32 ? 4 : 2);
+    const int64_t per_range = m_pad * R * (int64_t)(sizeof(float) + sizeof(int32_t));
+    const int ys_hi = (int)std::max<int64_t>(
+        ys_lo, std::min<int64_t>(std::min(n_tiles, 128), (1ll << 30) / per_range));
+    int nseg = ys_lo;
+    int64_t best = INT64_MAX;
+    for (int ys = ys_lo; ys <= ys_hi; ++ys) {
+      const int tpc = ceil_div(n_tiles, ys);
+      if (ceil_div(n_tiles, tpc) != ys) continue;  // same ranges as a smaller split
+      const int64_t cost = ceil_div(qblocks * ys, sms) * (int64_t)(tpc + 2);
+      if (cost < best) { best = cost; nseg = ys; }
+    }
+    const int tpc = ceil_div(n_tiles, nseg);
+    float* pkey = ws.get<float>((size_t)m_pad * nseg * R);
+    int32_t* pidx = ws.get<int32_t>((size_t)m_pad * nseg * R);
+    if (!pkey || !pidx) return FMGP_ENOMEM;
+    if (R == 8) {
+      FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<8>, kTcSelSmem));
+      FMGP_LAUNCH(tc_dist_kernel<8><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcThreads, kTcSelSmem, s>>>(
+          tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
+    } else {
+      FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<32>, kTcSelSmem));
+      FMGP_LAUNCH(tc_dist_kernel<32><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcThreads, kTcSelSmem, s>>>(
+          tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
+    }
     switch (S) {
-      case 1: FMGP_LAUNCH(select_merge_kernel<1><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
-      case 2: FMGP_LAUNCH(select_merge_kernel<2><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
-      case 3: FMGP_LAUNCH(select_merge_kernel<3><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
-      default: FMGP_LAUNCH(select_merge_kernel<4><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+      case 1: FMGP_LAUNCH(select_parts_kernel<1><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
+      case 2: FMGP_LAUNCH(select_parts_kernel<2><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
+      case 3: FMGP_LAUNCH(select_parts_kernel<3><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
+      default: FMGP_LAUNCH(select_parts_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
+    }
+  } else {
+    // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
+    int chunk_tiles = (int)std::max<int64_t>(1, (int64_t)(1ll << 30) / (m_pad * 4 * kTN));
+    chunk_tiles = std::min(chunk_tiles, n_tiles);
+    // tiles per CTA: enough CTAs for two waves over the SMs
+    const int64_t want = 2ll * num_sms();
+    int tpc = chunk_tiles;
+    while (tpc > 1 && qblocks * ((chunk_tiles + tpc - 1) / tpc) < want) tpc = (tpc + 1) / 2;
+    const int ysplit = (chunk_tiles + tpc - 1) / tpc;
+    float* Dc = ws.get<float>((size_t)m_pad * chunk_tiles * kTN);
+    float* ckey = ws.get<float>((size_t)m * L);
+    if (!Dc || !ckey) return FMGP_ENOMEM;
+    FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<0>, kTcSmem));
+    const int64_t ldc = (int64_t)chunk_tiles * kTN;
+    for (int t0 = 0; t0 < n_tiles; t0 += chunk_tiles) {
+      const int t1 = std::min(n_tiles, t0 + chunk_tiles);
+      FMGP_LAUNCH(tc_dist_kernel<0><<<dim3((unsigned)qblocks, (unsigned)ysplit), kTcThreads, kTcSmem, s>>>(
+          tmQ, tmX, qn2, xn2, t0, t1, tpc, k_chunks, ldc, Dc, n, 0, nullptr, nullptr, err));
+      const int64_t col0 = (int64_t)t0 * kTN, ncols = (int64_t)(t1 - t0) * kTN;
+      const int first = t0 == 0 ? 1 : 0;
+      switch (S) {
+        case 1: FMGP_LAUNCH(select_merge_kernel<1><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+        case 2: FMGP_LAUNCH(select_merge_kernel<2><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+        case 3: FMGP_LAUNCH(select_merge_kernel<3><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+        default: FMGP_LAUNCH(select_merge_kernel<4><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+      }
     }
   }
   FMGP_CUDA_TRY(cudaGetLastError());

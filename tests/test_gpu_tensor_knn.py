@@ -1,7 +1,9 @@
 """Tensor-core (tcgen05, BF16) candidate search for kNN at d >= 16: results
 must equal the oracle bit-exactly, and most queries must be certified
 (i.e. the tensor-core distances were good enough that the exact fallback
-scan was not needed), which shows the tensor-core path actually worked."""
+scan was not needed), which shows the tensor-core path actually worked.
+Both forms of the candidate selection are covered: inside the distance
+kernel (kq <= 32) and through the pass buffer."""
 import numpy as np
 import pytest
 import torch
@@ -25,14 +27,34 @@ def _data(kind, n, d, seed):
     return X if kind == "u64" else X.astype(np.float32)
 
 
+class _Fused:
+    """Select the candidate-selection form for the block's duration."""
+
+    def __init__(self, on):
+        self.on = on
+
+    def __enter__(self):
+        self.prev = fb.tune_get("tc_fused_select")
+        fb.tune_set("tc_fused_select", self.on)
+
+    def __exit__(self, *exc):
+        fb.tune_set("tc_fused_select", self.prev)
+
+
+@pytest.mark.parametrize("fused", [1, 0])
 @pytest.mark.parametrize("kind,n,d,kq", [("sparse32", 6000, 784, 29), ("u64", 5000, 16, 1),
-                                         ("u64", 9000, 64, 31), ("u32", 8000, 64, 63)])
-def test_tensor_core_knn_bitexact_and_certified(cuda, kind, n, d, kq):
+                                         ("u64", 9000, 64, 31), ("u32", 8000, 64, 63),
+                                         ("u32", 4099, 16, 4), ("u64", 4500, 40, 5),
+                                         ("u32", 7001, 24, 32)])
+def test_tensor_core_knn_bitexact_and_certified(cuda, kind, n, d, kq, fused):
     X = _data(kind, n, d, n + d)
     c0 = fb.diag_counter(1)
-    nbr, dist = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
+    with _Fused(fused):
+        nbr, dist = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
+        nbr_i, _ = fb.fmgp_build_knn(dev(X), kq)
     torch.cuda.synchronize()
-    assert fb.diag_counter(1) == c0 + 1, "tensor-core path not taken"
+    assert torch.equal(nbr, nbr_i)
+    assert fb.diag_counter(1) == c0 + 2, "tensor-core path not taken"
     fallbacks = fb.diag_counter(2)
     assert 0 <= fallbacks <= 0.2 * n, fallbacks
     rows = np.random.default_rng(1).choice(n, 300, replace=False)
@@ -61,3 +83,27 @@ def test_tensor_core_nearest_for_prediction(cuda):
     assert fb.diag_counter(2) <= 0.05 * W.m
     ref, _ = oracle.knn(W.X.astype(np.float64), W.Z.astype(np.float64), 1)
     np.testing.assert_array_equal(near.cpu().numpy(), ref[:, 0])
+
+
+@pytest.mark.parametrize("n,d,m", [(4096, 16, 128), (20_011, 64, 129), (30_000, 24, 5_000),
+                                   (9_000, 130, 700)])
+def test_tensor_core_nearest_both_forms(cuda, n, d, m):
+    """Nearest training point of m queries (one query block with many
+    candidate ranges up to many blocks with a ragged last one): both forms
+    of the selection equal the oracle's exact answer."""
+    rng = np.random.default_rng(n + m)
+    X = rng.random((n, d))
+    Z = rng.random((m, d))
+    Z[: m // 8] = X[rng.choice(n, m // 8, replace=False)]  # queries on training points
+    kern = fb.make_kernel("rbf", 0.0, 1.0, 1.0, 1e-2)
+    C = torch.zeros((n, 2, 1), dtype=torch.float64, device="cuda")
+    nbr = torch.zeros((n, 1), dtype=torch.int32, device="cuda")
+    ref, _ = oracle.knn(X, Z, 1)
+    for fused in (1, 0):
+        with _Fused(fused):
+            c0 = fb.diag_counter(1)
+            _, near = fb.fmgp_predict(dev(X), nbr, C, 2, kern, dev(Z))
+            torch.cuda.synchronize()
+            assert fb.diag_counter(1) == c0 + 1
+            assert fb.diag_counter(2) <= 0.05 * m
+        np.testing.assert_array_equal(near.cpu().numpy(), ref[:, 0])
