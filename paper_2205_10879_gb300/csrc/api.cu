@@ -284,6 +284,9 @@ int fmgp_tune_set(const char* key, double value) {
     tp.use_tensor_cores = value != 0.0;
   } else if (k == "tc_fused_select") {
     tp.tc_fused_select = value != 0.0;
+  } else if (k == "tc_oversample") {
+    if (!(value >= 2 && value <= 4)) { set_error("tc_oversample out of range [2, 4]"); return FMGP_EINVAL; }
+    tp.tc_oversample = (int)value;
   } else {
     set_error("unknown tuning key '%s'", key);
     return FMGP_EINVAL;
@@ -299,6 +302,7 @@ double fmgp_tune_get(const char* key) {
   if (k == "block_warps") return tp.block_warps;
   if (k == "tensor_cores") return tp.use_tensor_cores ? 1.0 : 0.0;
   if (k == "tc_fused_select") return tp.tc_fused_select ? 1.0 : 0.0;
+  if (k == "tc_oversample") return tp.tc_oversample;
   return -1.0;
 }
 

@@ -43,11 +43,19 @@ constexpr int kABytes = kTM * kTK * 2;   // 16 KB
 constexpr int kBBytes = kTN * kTK * 2;   // 32 KB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kTcThreads = 192;          // warps 0-3 epilogue, 4 producer, 5 MMA
+// fused selection: a second epilogue warpgroup (warps 6-9) takes the upper
+// half of each tile's columns, so two warps per SM sub-partition hide the
+// latency of the TMEM loads and the per-chunk filtering
+constexpr int kTcSelThreads = 320;
+constexpr int kTcEpiWarps(int R) { return R > 0 ? 8 : 4; }
 constexpr size_t kTcSmem = (size_t)kStages * kStageBytes + 1024 + 256;
-// fused selection: per epilogue thread a 32-float row (stride 33) of the
-// current chunk's distances, indexed by the bits the thread pops
-constexpr int kScrStride = 33;
-constexpr size_t kTcSelSmem = kTcSmem + (size_t)kTM * kScrStride * sizeof(float);
+// fused selection: per epilogue thread a 32-float row of the current chunk's
+// values, written as 16-byte slots swizzled by the row's low 3 bits (slot
+// q at q ^ (row & 7): the 8 rows of a store phase hit distinct banks) and
+// read back at the bits the thread pops
+constexpr int kScrStride = 32;
+constexpr size_t kTcSelSmem = kTcSmem + (size_t)2 * kTM * kScrStride * sizeof(float);
+static_assert(kTcSelSmem <= 232448, "fused tensor-core kernel exceeds 227 KB of shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -161,11 +169,14 @@ __device__ __forceinline__ void sorted_insert(float (&bk)[R], int (&bi)[R], floa
 // tiles tile0 + blockIdx.y*tpc .. (at most tpc tiles, not past tile_end).
 // R == 0: out row q (query q), column (t - tile0)*256 + j holds candidate
 //   t*256 + j.
-// R > 0: the R smallest (clamped at 0; candidates >= n_valid and, with self,
-//   the query itself left out) as an ascending list at
-//   pkey/pidx[(q * gridDim.y + blockIdx.y) * R ..], INT_MAX past the end.
+// R > 0: for each half h of the tile columns, the R smallest (clamped at 0;
+//   candidates >= n_valid and, with self, the query itself left out) as an
+//   ascending list at pkey/pidx[(q * 2 gridDim.y + 2 blockIdx.y + h) * R ..],
+//   INT_MAX past the end.  The thread ranks w = ||x||^2 - 2 q.x (FP32) and
+//   reports ||q||^2 + w: the sum is monotone in w, so the kept set and the
+//   range's R-th value are those of the reported distances.
 template <int R>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
+__global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist_kernel(
     const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX,
     const float* __restrict__ qnorm, const float* __restrict__ xnorm, int tile0, int tile_end,
     int tpc, int k_chunks, int64_t ld_out, float* __restrict__ out, int64_t n_valid, int self,
@@ -190,7 +201,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], kTcEpiWarps(R));
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -248,13 +259,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
         mma_commit(&tfull[b]);
       }
     }
-  } else if constexpr (R > 0) {  // epilogue warps 0-3, fused selection
-    const int row = warp * 32 + lane;
+  } else if constexpr (R > 0) {  // epilogue warps 0-3 and 6-9, fused selection
+    // TMEM lane quarter of a warp = its index mod 4; half h of the columns
+    const int quarter = warp & 3, h = warp >= 6 ? 1 : 0;
+    const int row = quarter * 32 + lane;
     const int64_t qrow = (int64_t)qb * kTM + row;
     const float qn = qnorm[qrow];
     float* scr = reinterpret_cast<float*>(smem + (size_t)kStages * kStageBytes + 256) +
-                 row * kScrStride;
-    float bk[R];
+                 (h * kTM + row) * kScrStride;
+    float4* scr4 = reinterpret_cast<float4*>(scr);
+    const int sw = row & 7;
+    float bk[R];  // ascending w values of the kept candidates
     int bi[R];
 #pragma unroll
     for (int s = 0; s < R; ++s) { bk[s] = __int_as_float(0x7f800000); bi[s] = INT_MAX; }
@@ -264,25 +279,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
       const bool ok = mbar_wait(&tfull[b], u & 1u, abort);
       if (!__all_sync(kFull, ok)) { *abort = 1; break; }
       tc_fence_after();
-      for (int c = 0; c < kTN / 32; ++c) {
+      for (int c = h * (kTN / 64); c < (h + 1) * (kTN / 64); ++c) {
+        const int64_t gcol = (int64_t)(t_first + t) * kTN + c * 32;
+        // the columns' norms are loaded before the TMEM load (which orders
+        // memory after it) so the two latencies overlap; with R = 32 the
+        // registers this holds would spill, so they are loaded after it
+        const float4* xn4 = reinterpret_cast<const float4*>(xnorm + gcol);
+        float4 xv[8];
+        if constexpr (R <= 8) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xv[q] = xn4[q];
+        }
         uint32_t v[32];
         __syncwarp();
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kTN + c * 32), v);
-        const int64_t gcol = (int64_t)(t_first + t) * kTN + c * 32;
-        const float4* xn4 = reinterpret_cast<const float4*>(xnorm + gcol);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN + c * 32), v);
+        if constexpr (R > 8) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xv[q] = xn4[q];
+        }
         const float thr = bk[R - 1];
-        unsigned int mask = 0;
+        float w[32];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float4 x = xn4[q];
-          const float xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float dv = fmaxf(fmaf(-2.0f, __uint_as_float(v[4 * q + e]), qn + xs[e]), 0.0f);
-            scr[4 * q + e] = dv;
-            mask |= (dv < thr ? 1u : 0u) << (4 * q + e);
-          }
+          const float4 x = xv[q];
+          float4 o;
+          o.x = w[4 * q + 0] = fmaf(-2.0f, __uint_as_float(v[4 * q + 0]), x.x);
+          o.y = w[4 * q + 1] = fmaf(-2.0f, __uint_as_float(v[4 * q + 1]), x.y);
+          o.z = w[4 * q + 2] = fmaf(-2.0f, __uint_as_float(v[4 * q + 2]), x.z);
+          o.w = w[4 * q + 3] = fmaf(-2.0f, __uint_as_float(v[4 * q + 3]), x.w);
+          scr4[q ^ sw] = o;
         }
+        // bit j = (w_j < thr) = sign bit of w_j - thr (thr = +inf gives -inf:
+        // set), shifted in from the top column of each 8-column group down
+        unsigned int g8[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          unsigned int mg = 0;
+#pragma unroll
+          for (int e = 7; e >= 0; --e)
+            mg = __funnelshift_l(__float_as_uint(w[8 * g + e] - thr), mg, 1);
+          g8[g] = mg;
+        }
+        unsigned int mask = g8[0] | (g8[1] << 8) | (g8[2] << 16) | (g8[3] << 24);
         const int64_t lim = n_valid - gcol;
         if (lim < 32) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
         if (self) {
@@ -295,8 +333,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
           if (mask) {
             const int j = __ffs(mask) - 1;
             mask &= mask - 1u;
-            const float dv = scr[j];
-            if (dv < bk[R - 1]) sorted_insert<R>(bk, bi, dv, (int)(gcol + j));
+            const float wj = scr[(((j >> 2) ^ sw) << 2) | (j & 3)];
+            if (wj < bk[R - 1]) sorted_insert<R>(bk, bi, wj, (int)(gcol + j));
           }
         }
       }
@@ -304,10 +342,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_dist_kernel(
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[b]);
     }
-    float* okey = pkey + (qrow * gridDim.y + blockIdx.y) * R;
-    int32_t* oidx = pidx + (qrow * gridDim.y + blockIdx.y) * R;
+    const int64_t seg = qrow * 2 * gridDim.y + 2 * blockIdx.y + h;
+    float* okey = pkey + seg * R;
+    int32_t* oidx = pidx + seg * R;
 #pragma unroll
-    for (int s = 0; s < R; ++s) { okey[s] = bk[s]; oidx[s] = bi[s]; }
+    for (int s = 0; s < R; ++s) {
+      okey[s] = bi[s] == INT_MAX ? __int_as_float(0x7f800000) : fmaxf(qn + bk[s], 0.0f);
+      oidx[s] = bi[s];
+    }
   } else {  // epilogue warps 0-3: TMEM lanes 32*warp .. 32*warp+31
     const int row = warp * 32 + lane;
     const float qn = qnorm[(int64_t)qb * kTM + row];
@@ -494,6 +536,92 @@ __global__ void __launch_bounds__(256) select_parts_kernel(
     dL[q] = fminf(bound, top.full() ? __uint_as_float(top.tk) : __int_as_float(0x7f800000));
 }
 
+// As select_parts_kernel for at most 32*PER entries per query, without a
+// running list: the L-th smallest key T is found by bisection on the key
+// bits (warp counts of keys <= mid), the members are the keys < T and, of
+// those equal to T, the lowest indices; they are written unordered (the
+// re-rank needs the set, not its order).
+template <int PER>
+__global__ void __launch_bounds__(256) select_parts_bisect_kernel(
+    const float* __restrict__ pkey, const int32_t* __restrict__ pidx, int64_t m, int nseg, int R,
+    int L, int32_t* __restrict__ cand, float* __restrict__ dL) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= m) return;
+  const int tot = nseg * R;
+  const float* kq_ = pkey + q * tot;
+  const int32_t* iq = pidx + q * tot;
+  unsigned int kk[PER];
+  int ii[PER];
+  float bound = __int_as_float(0x7f800000);
+  int nvalid = 0;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = p * 32 + lane;
+    kk[p] = ~0u;
+    ii[p] = INT_MAX;
+    if (e < tot) {
+      const int j = iq[e];
+      if (j != INT_MAX) {
+        const float v = kq_[e];
+        kk[p] = __float_as_uint(v) & 0x7fffffffu;  // v >= 0; -0 counts as +0
+        ii[p] = j;
+        ++nvalid;
+        if (e % R == R - 1) bound = fminf(bound, v);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) bound = fminf(bound, __shfl_xor_sync(kFull, bound, o));
+  nvalid = __reduce_add_sync(kFull, (unsigned)nvalid);
+  const bool full = nvalid >= L;
+  // T = smallest key with at least L keys <= T (all valid keys if not full)
+  unsigned int T = 0x7f800000u;
+  if (full) {
+    unsigned int lo = 0, hi = 0x7f800000u;
+    while (lo < hi) {
+      const unsigned int mid = lo + ((hi - lo) >> 1);
+      int c = 0;
+#pragma unroll
+      for (int p = 0; p < PER; ++p) c += kk[p] <= mid ? 1 : 0;
+      if ((int)__reduce_add_sync(kFull, (unsigned)c) >= L) hi = mid; else lo = mid + 1;
+    }
+    T = lo;
+  }
+  bool mem[PER];
+  int nlt = 0;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    mem[p] = full ? kk[p] < T : ii[p] != INT_MAX;
+    nlt += mem[p] ? 1 : 0;
+  }
+  if (full) {
+    // keys equal to T by increasing index until the list holds L
+    int need = L - (int)__reduce_add_sync(kFull, (unsigned)nlt);
+    while (need > 0) {
+      unsigned int best = ~0u;
+#pragma unroll
+      for (int p = 0; p < PER; ++p)
+        if (kk[p] == T && !mem[p]) best = min(best, (unsigned int)ii[p]);
+      best = __reduce_min_sync(kFull, best);
+#pragma unroll
+      for (int p = 0; p < PER; ++p)
+        if (kk[p] == T && (unsigned int)ii[p] == best) mem[p] = true;
+      --need;
+    }
+  }
+  int base = 0;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const unsigned int bal = __ballot_sync(kFull, mem[p]);
+    if (mem[p]) cand[q * L + base + __popc(bal & ((1u << lane) - 1u))] = ii[p];
+    base += __popc(bal);
+  }
+  for (int g = base + lane; g < L; g += 32) cand[q * L + g] = INT_MAX;
+  if (lane == 0)
+    dL[q] = fminf(bound, full ? __uint_as_float(T) : __int_as_float(0x7f800000));
+}
+
 // Exact re-rank with certificate; uncertified queries go to the fallback list.
 // One warp per query.  Candidate rows are read through a shared-memory tile
 // (32 rows x 64 features, padded) so every global read is coalesced and each
@@ -534,9 +662,12 @@ __device__ __forceinline__ void load_rows(const T* X, int d, const int* rows, in
   }
 }
 
+// Xa, Qa: FP32 copies of the rows for the bounds pass A (X, Q themselves for
+// FP32 inputs; for FP64 inputs converted once, not per candidate visit).
 template <typename T, int S, int KS>
 __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
-    const T* __restrict__ X, const T* __restrict__ Q, int d, int64_t m, int L, int kq,
+    const T* __restrict__ X, const T* __restrict__ Q, const float* __restrict__ Xa,
+    const float* __restrict__ Qa, int d, int64_t m, int L, int kq,
     const int32_t* __restrict__ cand, const float* __restrict__ dL,
     const float* __restrict__ qnorm2, const float* __restrict__ qdelta,
     const unsigned int* __restrict__ xstats, const int* __restrict__ err,
@@ -568,14 +699,17 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     rowlist[lane] = (j == INT_MAX) ? -1 : j;
     __syncwarp();
     float acc = 0.f;
+    float* tilef = reinterpret_cast<float*>(tile);
+    float* qrowf = tilef + 32 * (kRrChunk + 1);
+    const float* qra = Qa + w * d;
     for (int c0 = 0; c0 < d; c0 += kRrChunk) {
       const int cw = min(kRrChunk, d - c0);
-      load_rows<T>(X, d, rowlist, 32, c0, cw, tile, lane);
-      for (int p = lane; p < cw; p += 32) qrow[p] = qr[c0 + p];
+      load_rows<float>(Xa, d, rowlist, 32, c0, cw, tilef, lane);
+      for (int p = lane; p < cw; p += 32) qrowf[p] = qra[c0 + p];
       __syncwarp();
-      const T* myrow = tile + lane * (kRrChunk + 1);
+      const float* myrow = tilef + lane * (kRrChunk + 1);
       for (int p = 0; p < cw; ++p) {
-        const float t = (float)qrow[p] - (float)myrow[p];
+        const float t = qrowf[p] - myrow[p];
         acc = fmaf(t, t, acc);
       }
       __syncwarp();
@@ -791,15 +925,15 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
 }
 
 template <typename T, int S>
-int launch_rerank(const T* X, const T* Q, int d, int64_t m, int L, int kq, const int32_t* cand,
+int launch_rerank(const T* X, const T* Q, const float* Xa, const float* Qa, int d, int64_t m, int L, int kq, const int32_t* cand,
                   const float* dL, const float* qn2, const float* qdl, const unsigned int* xst,
                   const int* err, int32_t* idx, double* key, int* fbl, int* fbc, cudaStream_t s) {
   const int blocks = ceil_div(m, kRrWarps);
   const int KS = (kq + 31) / 32;
-  if (KS == 1) FMGP_LAUNCH((rerank_kernel<T, S, 1><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else if (KS == 2) FMGP_LAUNCH((rerank_kernel<T, S, 2><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else if (KS == 3) FMGP_LAUNCH((rerank_kernel<T, S, 3><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else FMGP_LAUNCH((rerank_kernel<T, S, 4><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  if (KS == 1) FMGP_LAUNCH((rerank_kernel<T, S, 1><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else if (KS == 2) FMGP_LAUNCH((rerank_kernel<T, S, 2><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else if (KS == 3) FMGP_LAUNCH((rerank_kernel<T, S, 3><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else FMGP_LAUNCH((rerank_kernel<T, S, 4><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
@@ -853,6 +987,12 @@ int pack(const T* X, int64_t rows, int d, int64_t rows_pad, int d_pad, Workspace
   return FMGP_OK;
 }
 
+// Candidates kept per query for the re-rank: the tuned multiple of kq,
+// in whole warps, at least 32 and at most 128.
+int tc_list_len(int kq) {
+  return std::min(128, (std::max(tune_params().tc_oversample * kq, 32) + 31) / 32 * 32);
+}
+
 // Per-range list length of the fused selection for kq neighbours (0 = the
 // pass-buffer form).
 int tc_fused_r(int kq) {
@@ -863,7 +1003,7 @@ int tc_fused_r(int kq) {
 template <typename T>
 int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool self,
              int32_t* idx_out, double* key_out, Workspace& ws, cudaStream_t s) {
-  const int L = std::min(128, (std::max(4 * kq, 32) + 31) / 32 * 32);
+  const int L = tc_list_len(kq);
   const int S = L / 32;
   const int d_pad = (d + kTK - 1) / kTK * kTK;
   const int64_t n_pad = (n + kTN - 1) / kTN * kTN;
@@ -903,7 +1043,7 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     // per-range lists
     const int sms = num_sms();
     const int ys_lo = std::min(n_tiles, R == 32 ? 4 : 2);
-    const int64_t per_range = m_pad * R * (int64_t)(sizeof(float) + sizeof(int32_t));
+    const int64_t per_range = 2 * m_pad * R * (int64_t)(sizeof(float) + sizeof(int32_t));
     const int ys_hi = (int)std::max<int64_t>(
         ys_lo, std::min<int64_t>(std::min(n_tiles, 128), (1ll << 30) / per_range));
     int nseg = ys_lo;
@@ -915,23 +1055,30 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
       if (cost < best) { best = cost; nseg = ys; }
     }
     const int tpc = ceil_div(n_tiles, nseg);
-    float* pkey = ws.get<float>((size_t)m_pad * nseg * R);
-    int32_t* pidx = ws.get<int32_t>((size_t)m_pad * nseg * R);
+    float* pkey = ws.get<float>((size_t)m_pad * 2 * nseg * R);
+    int32_t* pidx = ws.get<int32_t>((size_t)m_pad * 2 * nseg * R);
     if (!pkey || !pidx) return FMGP_ENOMEM;
     if (R == 8) {
       FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<8>, kTcSelSmem));
-      FMGP_LAUNCH(tc_dist_kernel<8><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcThreads, kTcSelSmem, s>>>(
+      FMGP_LAUNCH(tc_dist_kernel<8><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcSelThreads, kTcSelSmem, s>>>(
           tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
     } else {
       FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<32>, kTcSelSmem));
-      FMGP_LAUNCH(tc_dist_kernel<32><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcThreads, kTcSelSmem, s>>>(
+      FMGP_LAUNCH(tc_dist_kernel<32><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcSelThreads, kTcSelSmem, s>>>(
           tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
     }
-    switch (S) {
-      case 1: FMGP_LAUNCH(select_parts_kernel<1><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
-      case 2: FMGP_LAUNCH(select_parts_kernel<2><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
-      case 3: FMGP_LAUNCH(select_parts_kernel<3><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
-      default: FMGP_LAUNCH(select_parts_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, nseg, R, L, cand, dL)); break;
+    const int tot = 2 * nseg * R;
+    if (tot <= 128)
+      FMGP_LAUNCH(select_parts_bisect_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL));
+    else if (tot <= 256)
+      FMGP_LAUNCH(select_parts_bisect_kernel<8><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL));
+    else if (tot <= 512)
+      FMGP_LAUNCH(select_parts_bisect_kernel<16><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL));
+    else switch (S) {
+      case 1: FMGP_LAUNCH(select_parts_kernel<1><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
+      case 2: FMGP_LAUNCH(select_parts_kernel<2><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
+      case 3: FMGP_LAUNCH(select_parts_kernel<3><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
+      default: FMGP_LAUNCH(select_parts_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
     }
   } else {
     // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
@@ -962,11 +1109,28 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     }
   }
   FMGP_CUDA_TRY(cudaGetLastError());
+  // FP32 rows for the re-rank's bounds pass
+  const float* Xa = reinterpret_cast<const float*>(X);
+  const float* Qa = reinterpret_cast<const float*>(Q);
+  if (sizeof(T) == 8) {
+    float* xf = ws.get<float>((size_t)n * d);
+    if (!xf) return FMGP_ENOMEM;
+    if ((rc = to_f32(reinterpret_cast<const double*>(X), n * d, xf, s))) return rc;
+    Xa = xf;
+    if (self) {
+      Qa = xf;
+    } else {
+      float* qf = ws.get<float>((size_t)m * d);
+      if (!qf) return FMGP_ENOMEM;
+      if ((rc = to_f32(reinterpret_cast<const double*>(Q), m * d, qf, s))) return rc;
+      Qa = qf;
+    }
+  }
   switch (S) {
-    case 1: rc = launch_rerank<T, 1>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    case 2: rc = launch_rerank<T, 2>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    case 3: rc = launch_rerank<T, 3>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    default: rc = launch_rerank<T, 4>(X, Q, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 1: rc = launch_rerank<T, 1>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 2: rc = launch_rerank<T, 2>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 3: rc = launch_rerank<T, 3>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    default: rc = launch_rerank<T, 4>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
   }
   if (rc) return rc;
   FMGP_CUDA_TRY(cudaGetLastError());
@@ -981,7 +1145,7 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
 bool tc_knn_eligible(int64_t n, int d, int64_t m, int kq) {
   const TuneParams& tp = tune_params();
   if (!tp.use_tensor_cores) return false;
-  const int L = std::min(128, (std::max(4 * kq, 32) + 31) / 32 * 32);
+  const int L = tc_list_len(kq);
   return d >= 16 && kq <= 96 && n > 2 * L && n >= 4096 && m >= 128;
 }
 

@@ -83,3 +83,31 @@ def test_argument_errors_are_caught_on_the_host():
     assert lib.fmgp_predict(fake, b.F64, 100, 2, fake, 29, fake, 30, 1, ctypes.byref(k),
                             b.PREC_FP64, fake, -1, fake, None, None) == b.FMGP_EINVAL
     assert b"m = -1" in lib.fmgp_last_error()
+
+
+def test_tuning_keys_are_host_only_and_range_checked():
+    """Launch-shape and path controls: defaults, round trip, refusal of
+    unknown keys and out-of-range values (host code only)."""
+    from paper_2205_10879_gb300 import _binding as b
+    lib = b.load()
+    lib.fmgp_tune_get.restype = ctypes.c_double
+    lib.fmgp_tune_set.argtypes = [ctypes.c_char_p, ctypes.c_double]
+    lib.fmgp_tune_get.argtypes = [ctypes.c_char_p]
+    defaults = {b"tensor_cores": 1.0, b"tc_fused_select": 1.0, b"tc_oversample": 2.0,
+                b"block_warps": 0.0}
+    for key, v in defaults.items():
+        assert lib.fmgp_tune_get(key) == v, key
+    assert lib.fmgp_tune_get(b"no_such_key") == -1.0
+    assert lib.fmgp_tune_set(b"no_such_key", 1.0) == b.FMGP_EINVAL
+    for key, bad in ((b"tc_oversample", 1.0), (b"tc_oversample", 5.0), (b"block_warps", 9.0),
+                     (b"grid_target", 0.5)):
+        assert lib.fmgp_tune_set(key, bad) == b.FMGP_EINVAL, key
+        assert lib.fmgp_tune_get(key) == defaults.get(key, 12.0)
+    try:
+        assert lib.fmgp_tune_set(b"tc_oversample", 3.0) == 0
+        assert lib.fmgp_tune_get(b"tc_oversample") == 3.0
+        assert lib.fmgp_tune_set(b"tc_fused_select", 0.0) == 0
+        assert lib.fmgp_tune_get(b"tc_fused_select") == 0.0
+    finally:
+        lib.fmgp_tune_set(b"tc_oversample", 2.0)
+        lib.fmgp_tune_set(b"tc_fused_select", 1.0)

@@ -107,3 +107,22 @@ def test_tensor_core_nearest_both_forms(cuda, n, d, m):
             assert fb.diag_counter(1) == c0 + 1
             assert fb.diag_counter(2) <= 0.05 * m
         np.testing.assert_array_equal(near.cpu().numpy(), ref[:, 0])
+
+
+def test_oversampling_changes_no_result(cuda):
+    """The re-rank's candidate count is a speed setting: the certificate
+    (or the exhaustive fallback) makes every setting give the same table."""
+    X = _data("sparse32", 6000, 784, 11)
+    tables = []
+    prev = fb.tune_get("tc_oversample")
+    try:
+        for ovs in (2, 3, 4):
+            fb.tune_set("tc_oversample", ovs)
+            nbr, _ = fb.fmgp_build_knn(dev(X), 29)
+            tables.append(nbr)
+    finally:
+        fb.tune_set("tc_oversample", prev)
+    assert all(torch.equal(tables[0], t) for t in tables[1:])
+    rows = np.arange(0, 6000, 97)
+    ref_i, _ = oracle.knn(X.astype(np.float64), X.astype(np.float64)[rows], 29, rows)
+    np.testing.assert_array_equal(tables[0].cpu().numpy()[rows], ref_i)
