@@ -402,7 +402,7 @@ const char* fmgp_version(void);
  *                  tcgen05 distance kernel (default), 0 = distances go through
  *                  a pass buffer in HBM and a separate selection kernel
  *   "tc_oversample" candidates kept per requested neighbour for the exact
- *                  re-rank of the tensor-core search (2..4, default 2; at
+ *                  re-rank of the tensor-core search (2..4, default 4; at
  *                  least 32, at most 128 per query)
  * Process-wide; returns FMGP_EINVAL for an unknown key or a value out of range.
  */

@@ -10,7 +10,7 @@ struct TuneParams {
   int block_warps = 0;           // warps per CTA for block kernels (0 = automatic)
   bool use_tensor_cores = true;  // tcgen05 candidate search for d >= 16
   bool tc_fused_select = true;   // candidate selection inside the tcgen05 epilogue (kq <= 32)
-  int tc_oversample = 2;         // re-rank candidates per requested neighbour (2..4)
+  int tc_oversample = 4;         // re-rank candidates per requested neighbour (2..4)
 };
 
 TuneParams& tune_params();

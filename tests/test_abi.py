@@ -93,7 +93,7 @@ def test_tuning_keys_are_host_only_and_range_checked():
     lib.fmgp_tune_get.restype = ctypes.c_double
     lib.fmgp_tune_set.argtypes = [ctypes.c_char_p, ctypes.c_double]
     lib.fmgp_tune_get.argtypes = [ctypes.c_char_p]
-    defaults = {b"tensor_cores": 1.0, b"tc_fused_select": 1.0, b"tc_oversample": 2.0,
+    defaults = {b"tensor_cores": 1.0, b"tc_fused_select": 1.0, b"tc_oversample": 4.0,
                 b"block_warps": 0.0}
     for key, v in defaults.items():
         assert lib.fmgp_tune_get(key) == v, key
@@ -109,5 +109,5 @@ def test_tuning_keys_are_host_only_and_range_checked():
         assert lib.fmgp_tune_set(b"tc_fused_select", 0.0) == 0
         assert lib.fmgp_tune_get(b"tc_fused_select") == 0.0
     finally:
-        lib.fmgp_tune_set(b"tc_oversample", 2.0)
+        lib.fmgp_tune_set(b"tc_oversample", 4.0)
         lib.fmgp_tune_set(b"tc_fused_select", 1.0)
