@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(256) select_merge_kernel(
 template <int S>
 __global__ void __launch_bounds__(256) select_parts_kernel(
     const float* __restrict__ pkey, const int32_t* __restrict__ pidx, int64_t m, int nseg, int R,
-    int L, int32_t* __restrict__ cand, float* __restrict__ dL) {
+    int L, int32_t* __restrict__ cand, float* __restrict__ ckey, float* __restrict__ dL) {
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= m) return;
@@ -530,7 +530,10 @@ __global__ void __launch_bounds__(256) select_parts_kernel(
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int g = lane * S + s;
-    if (g < L) cand[q * L + g] = top.i[s];
+    if (g < L) {
+      cand[q * L + g] = top.i[s];
+      ckey[q * L + g] = top.i[s] == INT_MAX ? 0.f : __uint_as_float(top.k[s]);
+    }
   }
   if (lane == 0)
     dL[q] = fminf(bound, top.full() ? __uint_as_float(top.tk) : __int_as_float(0x7f800000));
@@ -544,7 +547,7 @@ __global__ void __launch_bounds__(256) select_parts_kernel(
 template <int PER>
 __global__ void __launch_bounds__(256) select_parts_bisect_kernel(
     const float* __restrict__ pkey, const int32_t* __restrict__ pidx, int64_t m, int nseg, int R,
-    int L, int32_t* __restrict__ cand, float* __restrict__ dL) {
+    int L, int32_t* __restrict__ cand, float* __restrict__ ckey, float* __restrict__ dL) {
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= m) return;
@@ -614,7 +617,11 @@ __global__ void __launch_bounds__(256) select_parts_bisect_kernel(
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const unsigned int bal = __ballot_sync(kFull, mem[p]);
-    if (mem[p]) cand[q * L + base + __popc(bal & ((1u << lane) - 1u))] = ii[p];
+    if (mem[p]) {
+      const int pos = base + __popc(bal & ((1u << lane) - 1u));
+      cand[q * L + pos] = ii[p];
+      ckey[q * L + pos] = __uint_as_float(kk[p]);
+    }
     base += __popc(bal);
   }
   for (int g = base + lane; g < L; g += 32) cand[q * L + g] = INT_MAX;
@@ -668,7 +675,8 @@ template <typename T, int S, int KS>
 __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     const T* __restrict__ X, const T* __restrict__ Q, const float* __restrict__ Xa,
     const float* __restrict__ Qa, int d, int64_t m, int L, int kq,
-    const int32_t* __restrict__ cand, const float* __restrict__ dL,
+    const int32_t* __restrict__ cand, const float* __restrict__ ckey,
+    const float* __restrict__ xdl, const float* __restrict__ dL,
     const float* __restrict__ qnorm2, const float* __restrict__ qdelta,
     const unsigned int* __restrict__ xstats, const int* __restrict__ err,
     int32_t* __restrict__ idx_out, double* __restrict__ key_out, int* fb_list, int* fb_count) {
@@ -688,14 +696,56 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
   const float xmaxn = __uint_as_float(xstats[0]);
   const float qnrm = sqrtf(qnorm2[w]) * 1.0001f + qdelta[w];
   const float econv = (sizeof(T) == 8) ? 1.01f * u * (qnrm + xmaxn + __uint_as_float(xstats[1])) : 0.f;
-  // A: FP32 bounds for all L candidates
   float lo[S], hi[S];
+  // A0: the tensor-core distance of each candidate with its rigorous error
+  // (FP32 accumulation E, BF16 rounding of both vectors) bounds the exact
+  // distance; candidates whose lower bound exceeds the kq-th smallest upper
+  // bound cannot be among the kq nearest and skip the FP32 pass.  The others
+  // are compacted into the slot list.
+  int nsurv = L;
+  {
+    const float qn0 = sqrtf(qnorm2[w]) * 1.0001f;
+    const float E0 =
+        2.0f * d * 4.0f * u * qn0 * xmaxn + d * u * (qn0 * qn0 + xmaxn * xmaxn) + 1e-30f;
+    const float qd = qdelta[w];
+    int jg[S];
+    WarpTopK<KS> u0;
+    u0.init(kq);
+#pragma unroll
+    for (int g = 0; g < S; ++g) {
+      const int a = 32 * g + lane;
+      jg[g] = a < L ? cand[w * L + a] : INT_MAX;
+      const bool valid = jg[g] != INT_MAX;
+      const float D = valid ? ckey[w * L + a] : 0.0f;
+      const float xd = valid ? xdl[jg[g]] : 0.0f;
+      const float l = fmaxf(sqrtf(fmaxf(D - E0, 0.0f)) - qd - xd, 0.0f);
+      const float h = sqrtf(D + E0) + qd + xd;
+      lo[g] = valid ? l * l * (1.0f - 1e-5f) : __int_as_float(0x7f800000);
+      u0.offer(valid ? (unsigned long long)__float_as_uint(h * h * (1.0f + 1e-5f)) : ~0ull,
+               valid ? a : INT_MAX, lane);
+    }
+    const float Ub = u0.full() ? __uint_as_float((unsigned int)u0.tk) : __int_as_float(0x7f800000);
+    nsurv = 0;
+#pragma unroll
+    for (int g = 0; g < S; ++g) {
+      const bool take = jg[g] != INT_MAX && lo[g] <= Ub;
+      const unsigned bal = __ballot_sync(kFull, take);
+      if (take) lists[wid][1][nsurv + __popc(bal & ((1u << lane) - 1u))] = jg[g];
+      nsurv += __popc(bal);
+    }
+    __syncwarp();
+  }
+  // A: FP32 bounds for the surviving candidates (slots 0 .. nsurv-1)
   WarpTopK<KS> ub;
   ub.init(kq);
 #pragma unroll
   for (int g = 0; g < S; ++g) {
     const int a = 32 * g + lane;
-    const int j = a < L ? cand[w * L + a] : INT_MAX;
+    if (32 * g >= nsurv) {  // warp-uniform: no candidate left in this group
+      lo[g] = hi[g] = __int_as_float(0x7f800000);
+      continue;
+    }
+    const int j = a < nsurv ? lists[wid][1][a] : INT_MAX;
     rowlist[lane] = (j == INT_MAX) ? -1 : j;
     __syncwarp();
     float acc = 0.f;
@@ -871,7 +921,10 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     const int a = 32 * g + lane;
     const bool take = a < L && lo[g] <= U;
     const unsigned bal = __ballot_sync(kFull, take);
-    if (take) keep[nkeep + __popc(bal & ((1u << lane) - 1u))] = cand[w * L + a];
+    const int cj = take ? lists[wid][1][a] : 0;
+    __syncwarp();
+    if (take) keep[nkeep + __popc(bal & ((1u << lane) - 1u))] = cj;
+    __syncwarp();
     nkeep += __popc(bal);
   }
   __syncwarp();
@@ -925,15 +978,15 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
 }
 
 template <typename T, int S>
-int launch_rerank(const T* X, const T* Q, const float* Xa, const float* Qa, int d, int64_t m, int L, int kq, const int32_t* cand,
+int launch_rerank(const T* X, const T* Q, const float* Xa, const float* Qa, int d, int64_t m, int L, int kq, const int32_t* cand, const float* ckey, const float* xdl,
                   const float* dL, const float* qn2, const float* qdl, const unsigned int* xst,
                   const int* err, int32_t* idx, double* key, int* fbl, int* fbc, cudaStream_t s) {
   const int blocks = ceil_div(m, kRrWarps);
   const int KS = (kq + 31) / 32;
-  if (KS == 1) FMGP_LAUNCH((rerank_kernel<T, S, 1><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else if (KS == 2) FMGP_LAUNCH((rerank_kernel<T, S, 2><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else if (KS == 3) FMGP_LAUNCH((rerank_kernel<T, S, 3><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else FMGP_LAUNCH((rerank_kernel<T, S, 4><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  if (KS == 1) FMGP_LAUNCH((rerank_kernel<T, S, 1><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else if (KS == 2) FMGP_LAUNCH((rerank_kernel<T, S, 2><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else if (KS == 3) FMGP_LAUNCH((rerank_kernel<T, S, 3><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  else FMGP_LAUNCH((rerank_kernel<T, S, 4><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
@@ -1026,11 +1079,12 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   const int n_tiles = (int)(n_pad / kTN), k_chunks = d_pad / kTK;
   const int64_t qblocks = m_pad / kTM;
   int32_t* cand = ws.get<int32_t>((size_t)m * L);
+  float* ckey = ws.get<float>((size_t)m * L);
   float* dL = ws.get<float>(m);
   int* err = ws.get<int>(1);
   int* fb_list = ws.get<int>(m);
   int* fb_count = ws.get<int>(1);
-  if (!cand || !dL || !err || !fb_list || !fb_count) return FMGP_ENOMEM;
+  if (!cand || !ckey || !dL || !err || !fb_list || !fb_count) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   FMGP_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(int), s));
   const int sblocks = ceil_div(m * 32, 256);
@@ -1069,16 +1123,16 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     }
     const int tot = 2 * nseg * R;
     if (tot <= 128)
-      FMGP_LAUNCH(select_parts_bisect_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL));
+      FMGP_LAUNCH(select_parts_bisect_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL));
     else if (tot <= 256)
-      FMGP_LAUNCH(select_parts_bisect_kernel<8><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL));
+      FMGP_LAUNCH(select_parts_bisect_kernel<8><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL));
     else if (tot <= 512)
-      FMGP_LAUNCH(select_parts_bisect_kernel<16><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL));
+      FMGP_LAUNCH(select_parts_bisect_kernel<16><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL));
     else switch (S) {
-      case 1: FMGP_LAUNCH(select_parts_kernel<1><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
-      case 2: FMGP_LAUNCH(select_parts_kernel<2><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
-      case 3: FMGP_LAUNCH(select_parts_kernel<3><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
-      default: FMGP_LAUNCH(select_parts_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, dL)); break;
+      case 1: FMGP_LAUNCH(select_parts_kernel<1><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
+      case 2: FMGP_LAUNCH(select_parts_kernel<2><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
+      case 3: FMGP_LAUNCH(select_parts_kernel<3><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
+      default: FMGP_LAUNCH(select_parts_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
     }
   } else {
     // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
@@ -1090,8 +1144,7 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     while (tpc > 1 && qblocks * ((chunk_tiles + tpc - 1) / tpc) < want) tpc = (tpc + 1) / 2;
     const int ysplit = (chunk_tiles + tpc - 1) / tpc;
     float* Dc = ws.get<float>((size_t)m_pad * chunk_tiles * kTN);
-    float* ckey = ws.get<float>((size_t)m * L);
-    if (!Dc || !ckey) return FMGP_ENOMEM;
+    if (!Dc) return FMGP_ENOMEM;
     FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<0>, kTcSmem));
     const int64_t ldc = (int64_t)chunk_tiles * kTN;
     for (int t0 = 0; t0 < n_tiles; t0 += chunk_tiles) {
@@ -1127,10 +1180,10 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     }
   }
   switch (S) {
-    case 1: rc = launch_rerank<T, 1>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    case 2: rc = launch_rerank<T, 2>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    case 3: rc = launch_rerank<T, 3>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    default: rc = launch_rerank<T, 4>(X, Q, Xa, Qa, d, m, L, kq, cand, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 1: rc = launch_rerank<T, 1>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 2: rc = launch_rerank<T, 2>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    case 3: rc = launch_rerank<T, 3>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
+    default: rc = launch_rerank<T, 4>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
   }
   if (rc) return rc;
   FMGP_CUDA_TRY(cudaGetLastError());
