@@ -148,7 +148,10 @@ constexpr int kBfTile = 256;   // candidate rows staged per pass (8 per lane)
 constexpr int kBfSub = kBfTile / 32;
 constexpr int kBfChunk = 64;   // feature columns staged per pass
 
-__global__ void maxabs_kernel(const void* X, int f64, int64_t count, unsigned int* out_bits) {
+// gate: optional device count; nothing to do (and no bound needed) when it is 0.
+__global__ void maxabs_kernel(const void* X, int f64, int64_t count, unsigned int* out_bits,
+                              const int* gate) {
+  if (gate && *gate == 0) return;
   float m = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -328,17 +331,20 @@ const float* brute_rows(const T* X, int64_t n, int d, Workspace& ws, cudaStream_
   return f;
 }
 
+// Xf_in: an FP32 copy of X the caller already holds (or null).  With a query
+// list the magnitude bound is only computed when the list is not empty.
 template <typename T>
 int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, int excl,
                  Workspace& ws, int32_t* idx, double* key, cudaStream_t s,
-                 const int* qlist = nullptr, const int* qcount = nullptr) {
+                 const int* qlist = nullptr, const int* qcount = nullptr,
+                 const float* Xf_in = nullptr) {
   unsigned int* mx = ws.get<unsigned int>(1);
   if (!mx) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), s));
-  int rc = maxabs_into(X, sizeof(T) == 8, n * d, mx, s);
-  if (!rc && Q != X) rc = maxabs_into(Q, sizeof(T) == 8, m * d, mx, s);
+  int rc = maxabs_into(X, sizeof(T) == 8, n * d, mx, s, qcount);
+  if (!rc && Q != X) rc = maxabs_into(Q, sizeof(T) == 8, m * d, mx, s, qcount);
   if (rc) return rc;
-  const float* Xf = brute_rows(X, n, d, ws, s, &rc);
+  const float* Xf = Xf_in ? Xf_in : brute_rows(X, n, d, ws, s, &rc);
   if (rc) return rc;
   return launch_brute_mx<T>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
 }
@@ -534,12 +540,12 @@ int nn1_scan_t(const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_
 
 int knn_brute_list(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
                    int kq, bool self, const int* qlist, const int* qcount, int32_t* idx,
-                   double* key, Workspace& ws, cudaStream_t stream) {
+                   double* key, Workspace& ws, cudaStream_t stream, const float* Xf) {
   if (dtype == FMGP_F64)
     return launch_brute<double>((const double*)X, n, d, (const double*)Q, m, kq, self ? 1 : 0, ws,
-                                idx, key, stream, qlist, qcount);
+                                idx, key, stream, qlist, qcount, Xf);
   return launch_brute<float>((const float*)X, n, d, (const float*)Q, m, kq, self ? 1 : 0, ws, idx,
-                             key, stream, qlist, qcount);
+                             key, stream, qlist, qcount, Xf);
 }
 
 int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t* nbr,
@@ -582,10 +588,11 @@ int knn_query(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, 
   return knn_query_brute(X, dtype, n, d, Q, m, kq, idx, key, ws, stream);
 }
 
-int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaStream_t s) {
+int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaStream_t s,
+                const int* gate) {
   if (count <= 0) return FMGP_OK;
   const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), (int64_t)num_sms() * 8);
-  FMGP_LAUNCH(maxabs_kernel<<<blocks, 256, 0, s>>>(X, f64, count, mx));
+  FMGP_LAUNCH(maxabs_kernel<<<blocks, 256, 0, s>>>(X, f64, count, mx, gate));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }

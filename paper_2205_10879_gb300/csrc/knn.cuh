@@ -26,9 +26,10 @@ int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t*
 // Exhaustive exact scan for the queries listed in qlist[0..*qcount) (count
 // read on the device); self = the queries are rows of X (each excluded from
 // its own list).
+// Xf: an FP32 copy of X the caller already holds (null: made here for FP64).
 int knn_brute_list(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m,
                    int kq, bool self, const int* qlist, const int* qcount, int32_t* idx,
-                   double* key, Workspace& ws, cudaStream_t stream);
+                   double* key, Workspace& ws, cudaStream_t stream, const float* Xf = nullptr);
 
 // kq nearest training points of each of m query points (no exclusion):
 // grid search for d <= 3, tensor-core or exhaustive search otherwise.
@@ -46,7 +47,9 @@ int knn_query_brute(const void* X, fmgp_dtype dtype, int64_t n, int d, const voi
 
 // atomicMax of max |X[i]| (FP32 bits, i < count) into *mx: the magnitude bound
 // whose rounding slack the exhaustive scan's FP32 lower bounds include.
-int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaStream_t s);
+// gate: optional device count; the kernel does nothing while it is 0.
+int maxabs_into(const void* X, bool f64, int64_t count, unsigned int* mx, cudaStream_t s,
+                const int* gate = nullptr);
 
 // Exhaustive scan with the magnitude bound supplied: *mx must be at least
 // max |coordinate| over X and all of Q (FP32 bits, rounded up).

@@ -134,6 +134,34 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// Issue a 32x32b.x32 TMEM load without waiting: v must not be read before
+// tmem_wait_regs(v).
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+}
+// Wait for the thread's TMEM loads; v passes through the wait so that no use
+// of it is moved above it.
+__device__ __forceinline__ void tmem_wait_regs(uint32_t (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]),
+                 "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+                 "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]),
+                 "+r"(v[30]), "+r"(v[31])
+               :
+               : "memory");
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -163,6 +191,63 @@ __device__ __forceinline__ void sorted_insert(float (&bk)[R], int (&bi)[R], floa
     bk[s] = a ? bk[s - 1] : (b ? dv : bk[s]);
   }
   if (dv < bk[0]) { bk[0] = dv; bi[0] = col; }
+}
+
+// Fused selection of one 32-column chunk (TMEM values v, column norms xv):
+// w = ||x||^2 - 2 q.x, the lane's hits below its R-th value as a bit mask
+// (sign of w - threshold shifted in by a funnel shift per column), then each
+// lane pops its own hits into its sorted list; the warp pays for its busiest
+// lane, not for the union of all lanes' hits.
+template <int R>
+__device__ __forceinline__ void select_chunk(const uint32_t (&v)[32], const float4 (&xv)[8],
+                                             float (&bk)[R], int (&bi)[R], float* scr, int sw,
+                                             int64_t gcol, int64_t n_valid, int self,
+                                             int64_t qrow) {
+  float4* scr4 = reinterpret_cast<float4*>(scr);
+  const float thr = bk[R - 1];
+  float w[32];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 x = xv[q];
+    float4 o;
+    o.x = w[4 * q + 0] = fmaf(-2.0f, __uint_as_float(v[4 * q + 0]), x.x);
+    o.y = w[4 * q + 1] = fmaf(-2.0f, __uint_as_float(v[4 * q + 1]), x.y);
+    o.z = w[4 * q + 2] = fmaf(-2.0f, __uint_as_float(v[4 * q + 2]), x.z);
+    o.w = w[4 * q + 3] = fmaf(-2.0f, __uint_as_float(v[4 * q + 3]), x.w);
+    scr4[q ^ sw] = o;
+  }
+  // bit j = (w_j < thr) = sign bit of w_j - thr (thr = +inf gives -inf:
+  // set), shifted in from the top column of each 8-column group down
+  unsigned int g8[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    unsigned int mg = 0;
+#pragma unroll
+    for (int e = 7; e >= 0; --e) mg = __funnelshift_l(__float_as_uint(w[8 * g + e] - thr), mg, 1);
+    g8[g] = mg;
+  }
+  unsigned int mask = g8[0] | (g8[1] << 8) | (g8[2] << 16) | (g8[3] << 24);
+  const int64_t lim = n_valid - gcol;
+  if (lim < 32) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
+  if (self) {
+    const int64_t sj = qrow - gcol;
+    if (sj >= 0 && sj < 32) mask &= ~(1u << sj);
+  }
+  while (__any_sync(kFull, mask != 0u)) {
+    if (mask) {
+      const int j = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const float wj = scr[(((j >> 2) ^ sw) << 2) | (j & 3)];
+      if (wj < bk[R - 1]) sorted_insert<R>(bk, bi, wj, (int)(gcol + j));
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void load_norms(const float* xnorm, int64_t gcol, float4 (&xv)[8]) {
+  const float4* xn4 = reinterpret_cast<const float4*>(xnorm + gcol);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) xv[q] = xn4[q];
 }
 
 // Approximate squared distances of query block blockIdx.x against candidate
@@ -267,7 +352,6 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
     const float qn = qnorm[qrow];
     float* scr = reinterpret_cast<float*>(smem + (size_t)kStages * kStageBytes + 256) +
                  (h * kTM + row) * kScrStride;
-    float4* scr4 = reinterpret_cast<float4*>(scr);
     const int sw = row & 7;
     float bk[R];  // ascending w values of the kept candidates
     int bi[R];
@@ -279,63 +363,41 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
       const bool ok = mbar_wait(&tfull[b], u & 1u, abort);
       if (!__all_sync(kFull, ok)) { *abort = 1; break; }
       tc_fence_after();
-      for (int c = h * (kTN / 64); c < (h + 1) * (kTN / 64); ++c) {
-        const int64_t gcol = (int64_t)(t_first + t) * kTN + c * 32;
-        // the columns' norms are loaded before the TMEM load (which orders
-        // memory after it) so the two latencies overlap; with R = 32 the
-        // registers this holds would spill, so they are loaded after it
-        const float4* xn4 = reinterpret_cast<const float4*>(xnorm + gcol);
-        float4 xv[8];
-        if constexpr (R <= 8) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) xv[q] = xn4[q];
-        }
-        uint32_t v[32];
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN);
+      const int c0 = h * (kTN / 64);  // this warpgroup's 4 chunks: c0 .. c0 + 3
+      const int64_t g0 = (int64_t)(t_first + t) * kTN + c0 * 32;
+      if constexpr (R <= 8) {
+        // software pipelined: chunk c+1's TMEM load and norms are in flight
+        // while chunk c is filtered
+        uint32_t va[32], vb[32];
+        float4 xa[8], xb[8];
+        load_norms(xnorm, g0, xa);
         __syncwarp();
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN + c * 32), v);
-        if constexpr (R > 8) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) xv[q] = xn4[q];
-        }
-        const float thr = bk[R - 1];
-        float w[32];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 x = xv[q];
-          float4 o;
-          o.x = w[4 * q + 0] = fmaf(-2.0f, __uint_as_float(v[4 * q + 0]), x.x);
-          o.y = w[4 * q + 1] = fmaf(-2.0f, __uint_as_float(v[4 * q + 1]), x.y);
-          o.z = w[4 * q + 2] = fmaf(-2.0f, __uint_as_float(v[4 * q + 2]), x.z);
-          o.w = w[4 * q + 3] = fmaf(-2.0f, __uint_as_float(v[4 * q + 3]), x.w);
-          scr4[q ^ sw] = o;
-        }
-        // bit j = (w_j < thr) = sign bit of w_j - thr (thr = +inf gives -inf:
-        // set), shifted in from the top column of each 8-column group down
-        unsigned int g8[4];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          unsigned int mg = 0;
-#pragma unroll
-          for (int e = 7; e >= 0; --e)
-            mg = __funnelshift_l(__float_as_uint(w[8 * g + e] - thr), mg, 1);
-          g8[g] = mg;
-        }
-        unsigned int mask = g8[0] | (g8[1] << 8) | (g8[2] << 16) | (g8[3] << 24);
-        const int64_t lim = n_valid - gcol;
-        if (lim < 32) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
-        if (self) {
-          const int64_t sj = qrow - gcol;
-          if (sj >= 0 && sj < 32) mask &= ~(1u << sj);
-        }
-        // each lane pops its own hits: the warp pays for the busiest lane,
-        // not for the union of all lanes' hits
-        while (__any_sync(kFull, mask != 0u)) {
-          if (mask) {
-            const int j = __ffs(mask) - 1;
-            mask &= mask - 1u;
-            const float wj = scr[(((j >> 2) ^ sw) << 2) | (j & 3)];
-            if (wj < bk[R - 1]) sorted_insert<R>(bk, bi, wj, (int)(gcol + j));
-          }
+        tmem_ld32_issue(tbase + (uint32_t)(c0 * 32), va);
+        tmem_wait_regs(va);
+        load_norms(xnorm, g0 + 32, xb);
+        tmem_ld32_issue(tbase + (uint32_t)(c0 * 32 + 32), vb);
+        select_chunk<R>(va, xa, bk, bi, scr, sw, g0, n_valid, self, qrow);
+        tmem_wait_regs(vb);
+        load_norms(xnorm, g0 + 64, xa);
+        tmem_ld32_issue(tbase + (uint32_t)(c0 * 32 + 64), va);
+        select_chunk<R>(vb, xb, bk, bi, scr, sw, g0 + 32, n_valid, self, qrow);
+        tmem_wait_regs(va);
+        load_norms(xnorm, g0 + 96, xb);
+        tmem_ld32_issue(tbase + (uint32_t)(c0 * 32 + 96), vb);
+        select_chunk<R>(va, xa, bk, bi, scr, sw, g0 + 64, n_valid, self, qrow);
+        tmem_wait_regs(vb);
+        select_chunk<R>(vb, xb, bk, bi, scr, sw, g0 + 96, n_valid, self, qrow);
+      } else {
+        // R = 32: the list leaves no registers for a second chunk in flight
+        for (int c = 0; c < kTN / 64; ++c) {
+          uint32_t v[32];
+          float4 xv[8];
+          __syncwarp();
+          tmem_ld32_issue(tbase + (uint32_t)((c0 + c) * 32), v);
+          tmem_wait_regs(v);
+          load_norms(xnorm, g0 + c * 32, xv);
+          select_chunk<R>(v, xv, bk, bi, scr, sw, g0 + c * 32, n_valid, self, qrow);
         }
       }
       tc_fence_before();
@@ -390,44 +452,62 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
   }
 }
 
-// One warp per row: BF16 copy (padded), squared norm of the rounded row, and
-// the norm of its rounding error; running maxima in stats (float bits).
+// One warp per row (grid-strided): BF16 copy (padded), squared norm of the
+// rounded row, and the norm of its rounding error; the running maxima over
+// the real rows go to stats (float bits), one pair of atomics per CTA.
+constexpr int kPackThreads = 256;
 template <typename T>
-__global__ void pack_bf16_kernel(const T* __restrict__ X, int64_t rows, int d, int64_t rows_pad,
-                                 int d_pad, __nv_bfloat16* __restrict__ Xb,
-                                 float* __restrict__ norm2, float* __restrict__ delta,
-                                 unsigned int* stats) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= rows_pad) return;
-  float n2 = 0.f, e2 = 0.f;
-  for (int j = lane; j < d_pad; j += 32) {
-    float xb = 0.f;
-    if (w < rows && j < d) {
-      const double v = (double)X[w * d + j];
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      xb = __bfloat162float(h);
-      Xb[w * d_pad + j] = h;
-      const float e = (float)(v - (double)xb);
-      e2 = fmaf(e, e, e2);
-    } else {
-      Xb[w * d_pad + j] = __float2bfloat16(0.f);
+__global__ void __launch_bounds__(kPackThreads) pack_bf16_kernel(
+    const T* __restrict__ X, int64_t rows, int d, int64_t rows_pad, int d_pad,
+    __nv_bfloat16* __restrict__ Xb, float* __restrict__ norm2, float* __restrict__ delta,
+    unsigned int* stats) {
+  __shared__ float red[2][kPackThreads / 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (kPackThreads / 32);
+  float mnorm = 0.f, mdel = 0.f;
+  for (int64_t w = (int64_t)blockIdx.x * (kPackThreads / 32) + wib; w < rows_pad; w += nwarps) {
+    float n2 = 0.f, e2 = 0.f;
+    for (int j = lane; j < d_pad; j += 32) {
+      float xb = 0.f;
+      if (w < rows && j < d) {
+        const double v = (double)X[w * d + j];
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        xb = __bfloat162float(h);
+        Xb[w * d_pad + j] = h;
+        const float e = (float)(v - (double)xb);
+        e2 = fmaf(e, e, e2);
+      } else {
+        Xb[w * d_pad + j] = __float2bfloat16(0.f);
+      }
+      n2 = fmaf(xb, xb, n2);
     }
-    n2 = fmaf(xb, xb, n2);
-  }
-  for (int o = 16; o; o >>= 1) {
-    n2 += __shfl_xor_sync(kFull, n2, o);
-    e2 += __shfl_xor_sync(kFull, e2, o);
-  }
-  if (lane == 0) {
+    for (int o = 16; o; o >>= 1) {
+      n2 += __shfl_xor_sync(kFull, n2, o);
+      e2 += __shfl_xor_sync(kFull, e2, o);
+    }
     // generous rounding: the bound only needs to be an upper bound
     const float dl = sqrtf(e2) * 1.0001f + 1e-30f;
-    norm2[w] = n2;
-    delta[w] = dl;
-    if (w < rows) {
-      atomicMax(&stats[0], __float_as_uint(sqrtf(n2) * 1.0001f));
-      atomicMax(&stats[1], __float_as_uint(dl));
+    if (lane == 0) {
+      norm2[w] = n2;
+      delta[w] = dl;
     }
+    if (w < rows) {
+      mnorm = fmaxf(mnorm, sqrtf(n2) * 1.0001f);
+      mdel = fmaxf(mdel, dl);
+    }
+  }
+  if (lane == 0) {
+    red[0][wib] = mnorm;
+    red[1][wib] = mdel;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kPackThreads / 32; ++i) {
+      mnorm = fmaxf(mnorm, red[0][i]);
+      mdel = fmaxf(mdel, red[1][i]);
+    }
+    atomicMax(&stats[0], __float_as_uint(mnorm));
+    atomicMax(&stats[1], __float_as_uint(mdel));
   }
 }
 
@@ -1034,7 +1114,9 @@ int pack(const T* X, int64_t rows, int d, int64_t rows_pad, int d_pad, Workspace
   *stats = ws.get<unsigned int>(2);
   if (!*Xb || !*n2 || !*dl || !*stats) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(*stats, 0, 2 * sizeof(unsigned int), s));
-  FMGP_LAUNCH(pack_bf16_kernel<T><<<ceil_div(rows_pad * 32, 256), 256, 0, s>>>(
+  const int blocks = (int)std::min<int64_t>(ceil_div(rows_pad, kPackThreads / 32),
+                                            (int64_t)num_sms() * 8);
+  FMGP_LAUNCH(pack_bf16_kernel<T><<<blocks, kPackThreads, 0, s>>>(
       X, rows, d, rows_pad, d_pad, *Xb, *n2, *dl, *stats));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
@@ -1190,7 +1272,7 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   diag_record_tc(fb_count, s);
   // exhaustive exact scan for uncertified queries
   return knn_brute_list(X, sizeof(T) == 8 ? FMGP_F64 : FMGP_F32, n, d, Q, m, kq, self, fb_list,
-                        fb_count, idx_out, key_out, ws, s);
+                        fb_count, idx_out, key_out, ws, s, Xa);
 }
 
 }  // namespace
