@@ -38,6 +38,24 @@ int knn_query(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, 
 
 // Tensor-core candidate search + certified exact re-rank (d >= 16).
 bool tc_knn_eligible(int64_t n, int d, int64_t m, int kq);
+
+// Training side of the tensor-core search, packed once for repeated query
+// batches (resident models): BF16 rows padded to the tile, squared norms and
+// rounding-error norms per row, their maxima, and FP32 rows for the re-rank.
+// Buffers belong to the Workspace given to tc_pack_train.
+struct TcPacked {
+  const void* Xb = nullptr;
+  const float* xn2 = nullptr;
+  const float* xdl = nullptr;
+  const unsigned int* xst = nullptr;
+  const float* Xa = nullptr;
+};
+int tc_pack_train(const void* X, fmgp_dtype dtype, int64_t n, int d, Workspace& ws,
+                  cudaStream_t s, TcPacked* out);
+// As tc_knn with self = false, with the training side taken from P.
+int tc_knn_query_packed(const TcPacked& P, const void* X, fmgp_dtype dtype, int64_t n, int d,
+                        const void* Q, int64_t m, int kq, int32_t* idx_out, double* key_out,
+                        Workspace& ws, cudaStream_t s);
 int tc_knn(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m, int kq,
            bool self, int32_t* idx_out, double* key_out, Workspace& ws, cudaStream_t s);
 

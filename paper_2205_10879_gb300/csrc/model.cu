@@ -1,8 +1,9 @@
 // Resident fitted models: a model borrows the caller's X, neighbour table and
 // coefficients and owns what prediction would otherwise rebuild per call (the
 // search grid over X for d <= 3, an FP32 copy of an FP64 X for the
-// nearest-point scan at 4 <= d <= 15, the double-float copy of X for the
-// mixed form), so repeated prediction batches (the serving loop) only run the
+// nearest-point scan at 4 <= d <= 15, the packed training side of the
+// tensor-core search at d >= 16, the double-float copy of X for the mixed
+// form), so repeated prediction batches (the serving loop) only run the
 // nearest-point lookup and the gather-dot.
 #include "model.cuh"
 #include "predict.cuh"
@@ -61,6 +62,10 @@ extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int
     if (!m->Xf32) rc = FMGP_ENOMEM;
     else rc = to_f32((const double*)X, n * d, m->Xf32, s);
   }
+  if (!rc && d > kNn1ScanMaxD && tc_knn_eligible(n, d, 1 << 20, 1)) {
+    rc = tc_pack_train(X, dtype, n, d, ws, s, &m->tc);
+    m->has_tc = (rc == FMGP_OK);
+  }
   if (!rc && precision == FMGP_PREC_MIXED) {
     m->Xdf = ws.get<float2>((size_t)n * d);
     if (!m->Xdf) rc = FMGP_ENOMEM;
@@ -116,6 +121,9 @@ int model_predict(const Model& md, const void* Z, int64_t m, double* Yhat, int32
   int rc = md.has_grid ? nearest_on_grid(md.grid, Z, md.dtype, m, near, s)
            : md.d <= kNn1ScanMaxD
                ? nearest_scan(md.X, md.dtype, md.n, md.d, Z, m, nullptr, near, ws, s, md.Xf32)
+           : md.has_tc && tc_knn_eligible(md.n, md.d, m, 1)
+               ? tc_knn_query_packed(md.tc, md.X, md.dtype, md.n, md.d, Z, m, 1, near, nullptr,
+                                     ws, s)
                : nearest_train(md.X, md.dtype, md.n, md.d, Z, m, near, tune_params(), ws, s);
   if (rc) return rc;
   const KParams kp = make_kparams(md.kern);

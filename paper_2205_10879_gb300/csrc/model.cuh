@@ -21,6 +21,8 @@ struct Model {
   GridView grid{};
   float2* Xdf = nullptr;
   float* Xf32 = nullptr;  // FP32 copy of an FP64 X for the nearest-point scan (4 <= d <= 15)
+  bool has_tc = false;    // training side of the tensor-core search packed (d >= 16)
+  TcPacked tc{};
   void* bufs[kMaxBufs];
   int nbufs = 0;
   size_t bytes = 0;

@@ -1135,9 +1135,25 @@ int tc_fused_r(int kq) {
   return kq <= 4 ? 8 : (kq <= 32 ? 32 : 0);
 }
 
+// FP32 rows of X for the re-rank's bounds pass: X itself, or a copy of an
+// FP64 X.
+template <typename T>
+int f32_rows(const T* X, int64_t n, int d, Workspace& ws, cudaStream_t s, const float** out) {
+  if (sizeof(T) == 4) {
+    *out = reinterpret_cast<const float*>(X);
+    return FMGP_OK;
+  }
+  float* f = ws.get<float>((size_t)n * d);
+  if (!f) return FMGP_ENOMEM;
+  *out = f;
+  return to_f32(reinterpret_cast<const double*>(X), n * d, f, s);
+}
+
+// pre: the training side packed by tc_pack_train (null: packed here).
 template <typename T>
 int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool self,
-             int32_t* idx_out, double* key_out, Workspace& ws, cudaStream_t s) {
+             int32_t* idx_out, double* key_out, Workspace& ws, cudaStream_t s,
+             const TcPacked* pre = nullptr) {
   const int L = tc_list_len(kq);
   const int S = L / 32;
   const int d_pad = (d + kTK - 1) / kTK * kTK;
@@ -1146,8 +1162,16 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   __nv_bfloat16 *Xb, *Qb;
   float *xn2, *xdl, *qn2, *qdl;
   unsigned int *xst, *qst;
-  int rc = pack<T>(X, n, d, n_pad, d_pad, ws, s, &Xb, &xn2, &xdl, &xst);
-  if (rc) return rc;
+  int rc = FMGP_OK;
+  if (pre) {
+    Xb = reinterpret_cast<__nv_bfloat16*>(const_cast<void*>(pre->Xb));
+    xn2 = const_cast<float*>(pre->xn2);
+    xdl = const_cast<float*>(pre->xdl);
+    xst = const_cast<unsigned int*>(pre->xst);
+  } else {
+    rc = pack<T>(X, n, d, n_pad, d_pad, ws, s, &Xb, &xn2, &xdl, &xst);
+    if (rc) return rc;
+  }
   if (self && m_pad <= n_pad) {
     Qb = Xb; qn2 = xn2; qdl = xdl; qst = xst;
   } else {
@@ -1245,22 +1269,12 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   }
   FMGP_CUDA_TRY(cudaGetLastError());
   // FP32 rows for the re-rank's bounds pass
-  const float* Xa = reinterpret_cast<const float*>(X);
-  const float* Qa = reinterpret_cast<const float*>(Q);
-  if (sizeof(T) == 8) {
-    float* xf = ws.get<float>((size_t)n * d);
-    if (!xf) return FMGP_ENOMEM;
-    if ((rc = to_f32(reinterpret_cast<const double*>(X), n * d, xf, s))) return rc;
-    Xa = xf;
-    if (self) {
-      Qa = xf;
-    } else {
-      float* qf = ws.get<float>((size_t)m * d);
-      if (!qf) return FMGP_ENOMEM;
-      if ((rc = to_f32(reinterpret_cast<const double*>(Q), m * d, qf, s))) return rc;
-      Qa = qf;
-    }
-  }
+  const float* Xa = nullptr;
+  const float* Qa = nullptr;
+  if (pre) Xa = pre->Xa;
+  else if ((rc = f32_rows<T>(X, n, d, ws, s, &Xa))) return rc;
+  if (self) Qa = Xa;
+  else if ((rc = f32_rows<T>(Q, m, d, ws, s, &Qa))) return rc;
   switch (S) {
     case 1: rc = launch_rerank<T, 1>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
     case 2: rc = launch_rerank<T, 2>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
@@ -1282,6 +1296,41 @@ bool tc_knn_eligible(int64_t n, int d, int64_t m, int kq) {
   if (!tp.use_tensor_cores) return false;
   const int L = tc_list_len(kq);
   return d >= 16 && kq <= 96 && n > 2 * L && n >= 4096 && m >= 128;
+}
+
+int tc_pack_train(const void* X, fmgp_dtype dtype, int64_t n, int d, Workspace& ws,
+                  cudaStream_t s, TcPacked* out) {
+  const int d_pad = (d + kTK - 1) / kTK * kTK;
+  const int64_t n_pad = (n + kTN - 1) / kTN * kTN;
+  __nv_bfloat16* Xb;
+  float *xn2, *xdl;
+  unsigned int* xst;
+  const float* Xa;
+  int rc;
+  if (dtype == FMGP_F64) {
+    rc = pack<double>((const double*)X, n, d, n_pad, d_pad, ws, s, &Xb, &xn2, &xdl, &xst);
+    if (!rc) rc = f32_rows<double>((const double*)X, n, d, ws, s, &Xa);
+  } else {
+    rc = pack<float>((const float*)X, n, d, n_pad, d_pad, ws, s, &Xb, &xn2, &xdl, &xst);
+    if (!rc) rc = f32_rows<float>((const float*)X, n, d, ws, s, &Xa);
+  }
+  if (rc) return rc;
+  out->Xb = Xb;
+  out->xn2 = xn2;
+  out->xdl = xdl;
+  out->xst = xst;
+  out->Xa = Xa;
+  return FMGP_OK;
+}
+
+int tc_knn_query_packed(const TcPacked& P, const void* X, fmgp_dtype dtype, int64_t n, int d,
+                        const void* Q, int64_t m, int kq, int32_t* idx_out, double* key_out,
+                        Workspace& ws, cudaStream_t s) {
+  if (dtype == FMGP_F64)
+    return tc_knn_t<double>((const double*)X, n, d, (const double*)Q, m, kq, false, idx_out,
+                            key_out, ws, s, &P);
+  return tc_knn_t<float>((const float*)X, n, d, (const float*)Q, m, kq, false, idx_out, key_out,
+                         ws, s, &P);
 }
 
 int tc_knn(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, int64_t m, int kq,

@@ -24,13 +24,36 @@ def _fit(W, k, prec):
     return fb.FmgpModel(X, nbr, C, k, gk, prec)
 
 
+def _wide(n, d, dtype, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.random((n, d)).astype(dtype)
+    Z = rng.random((700, d)).astype(dtype)
+    return wl.Workload(f"d{d}", X, np.sin(X.sum(1, keepdims=True)).astype(np.float64), Z,
+                       Z[:, :1].astype(np.float64), 20, wl.KernelSpec("rbf", 0.0, 0.7, 1.0, 1e-3),
+                       np.arange(5))
+
+
 @pytest.mark.parametrize("prec", [fb.PREC_FP64, fb.PREC_MIXED])
-def test_model_predict_matches_fmgp_predict(cuda, prec):
-    W = wl.tiny()
-    md = _fit(W, 30, prec)
+@pytest.mark.parametrize("shape", ["grid", "scan", "tensor64", "tensor32"])
+def test_model_predict_matches_fmgp_predict(cuda, prec, shape):
+    """A resident model (search grid, FP32 scan copy, or packed tensor-core
+    training side, each built once) predicts exactly what fmgp_predict does."""
+    if shape == "grid":
+        W, k = wl.tiny(), 30
+    elif shape == "scan":
+        W, k = _wide(5000, 8, np.float64, 1), 20
+    elif shape == "tensor64":
+        W, k = _wide(6000, 24, np.float64, 2), 20
+    else:
+        W, k = _wide(6000, 40, np.float32, 3), 20
+    md = _fit(W, k, prec)
     Z = dev(W.Z)
+    c0 = fb.diag_counter(1)
     y1, n1 = md.predict(Z)
-    y2, n2 = fb.fmgp_predict(md.X, md.nbr, md.C, 30, md.kernel, Z, prec)
+    torch.cuda.synchronize()
+    if shape.startswith("tensor"):
+        assert fb.diag_counter(1) == c0 + 1, "tensor-core path not taken"
+    y2, n2 = fb.fmgp_predict(md.X, md.nbr, md.C, k, md.kernel, Z, prec)
     assert torch.equal(n1, n2)
     assert torch.equal(y1, y2)
     assert md.device_bytes() > 0
@@ -41,7 +64,7 @@ def _models():
     a = _fit(wl.tiny(n=4000, m=10), 30, fb.PREC_FP64)
     b = _fit(wl.large(n=60_000, m=10), 64, fb.PREC_MIXED)
     rng = np.random.default_rng(3)
-    Xh = rng.random((3000, 16))
+    Xh = rng.random((5000, 16))  # enough rows for the tensor-core lookup
     W16 = wl.Workload("d16", Xh, np.sin(Xh.sum(1, keepdims=True)), Xh[:5], Xh[:5, :1], 16,
                       wl.KernelSpec("rbf", 0.0, 0.4, 1.0, 1e-3), np.arange(5))
     c = _fit(W16, 16, fb.PREC_FP64)
