@@ -673,8 +673,8 @@ def serving_bench(a, dev):
     k in {16,32,64,128}, Matern/RBF, mixed precision; n capped at 200,000 for
     d >= 16, whose kNN table is built by exhaustive scan), one continuous-
     batching server (4 streams), Poisson request streams of log-uniform 1..65,536
-    points at 50% and 90% of the measured saturation rate: p50/p99 latency
-    (submission to results in host memory) and predictions/s."""
+    points at 25%, 50%, 75% and 90% of the measured saturation rate: p50/p99
+    latency (submission to results in host memory) and predictions/s."""
     from paper_2205_10879_gb300 import _binding as fb
     from paper_2205_10879_gb300 import serving, workloads as wl
     specs = wl.serving_models()
@@ -694,9 +694,9 @@ def serving_bench(a, dev):
     req_rate = sat["requests"] / sat["wall_s"]
     out = {"models": [{"n": int(m.n), "d": int(m.d), "k": int(m.k)} for m in models],
            "fit_seconds": fit_s, "saturation": sat}
-    for frac in (0.5, 0.9):
+    for frac in (0.25, 0.5, 0.75, 0.9):
         lat, pts, wall = serving.run_poisson(srv, models, frac * req_rate, a.serving_requests,
-                                             12 + int(frac * 10))
+                                             12 + int(frac * 100))
         out[f"load_{int(frac * 100)}"] = serving.latency_summary(lat, pts, wall)
     out["server"] = srv.stats()
     srv.close()
