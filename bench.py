@@ -374,6 +374,19 @@ def run_ours(a):
                "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in (hX, hY, hZ, hB))),
                "d2h_bytes_per_step": int(hOut.numel() * hOut.element_size() + 8)}
+    # kNN work per query (untimed call with the grid search's counters on)
+    knn_visits = None
+    if W.X.shape[1] <= 3:
+        fb.tune_set("count_visits", 1)
+        try:
+            fb.fmgp_build_knn(X, kq, nbr_out=nbr)
+            torch.cuda.synchronize()
+            nq = fb.diag_counter(5)
+            if nq > 0:
+                knn_visits = {"candidates_examined_per_query": fb.diag_counter(3) / nq,
+                              "fp64_keys_per_query": fb.diag_counter(4) / nq, "kq": kq}
+        finally:
+            fb.tune_set("count_visits", 0)
     line = {
         "metric": METRIC, "value": (n + m) / (ms * 1e-3) * ws, "unit": "points/s",
         "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
@@ -386,7 +399,7 @@ def run_ours(a):
         "precompute_pts_per_s": n / (phase_ms[1] * 1e-3),
         "precompute_with_knn_pts_per_s": n / ((phase_ms[0] + phase_ms[1]) * 1e-3),
         "predictions_per_s": m / (phase_ms[2] * 1e-3),
-        "knn_queries_per_s": n / (phase_ms[0] * 1e-3),
+        "knn_queries_per_s": n / (phase_ms[0] * 1e-3), "knn_work": knn_visits,
         "loocv_pts_per_s": b / (phase_ms[3] * 1e-3),
         "rmse": rmse, "fp64_path": fp64, "muygps_predict": muy, "roofline": roof, "e2e": e2e,
         "block_status": {str(v): int(c) for v, c in zip(*np.unique(st_main, return_counts=True))},

@@ -401,6 +401,8 @@ const char* fmgp_version(void);
  *   "tc_fused_select" 1 = for kq <= 32 the candidates are selected inside the
  *                  tcgen05 distance kernel (default), 0 = distances go through
  *                  a pass buffer in HBM and a separate selection kernel
+ *   "count_visits" 1 = the grid kNN (d <= 3) counts candidates examined and FP64
+ *                  keys formed (diagnostic counters 3-5), 0 = off (default)
  *   "tc_oversample" candidates kept per requested neighbour for the exact
  *                  re-rank of the tensor-core search (2..4, default 4; at
  *                  least 32, at most 128 per query)
@@ -430,7 +432,10 @@ int fmgp_autotune_reset(void);
 /* Diagnostic counters: 0 = kernels enqueued, 1 = tensor-core kNN calls,
  * 2 = queries of the most recent tensor-core kNN call that lacked a
  * certificate and were redone by the exact scan (valid once that call's
- * stream has completed). */
+ * stream has completed); with the tuning key "count_visits" set, for the most
+ * recent grid kNN call (d <= 3): 3 = candidates examined (FP32 lower bound
+ * formed), 4 = canonical FP64 keys formed, 5 = queries (valid once that
+ * call's stream has completed; -1 when unavailable). */
 int64_t fmgp_diag_counter(int32_t which);
 
 /* Number of CUDA kernels this library has enqueued since it was loaded

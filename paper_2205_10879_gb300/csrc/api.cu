@@ -183,6 +183,36 @@ void diag_record_tc(const int* fb_count_dev, cudaStream_t s) {
     cudaMemcpyAsync(g_tc_fallbacks_host, fb_count_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
+static unsigned long long* g_visits_dev = nullptr;
+static unsigned long long* g_visits_host = nullptr;  // pinned: examined, keys
+static std::atomic<long long> g_visits_queries{0};
+
+unsigned long long* diag_visits_begin(int64_t queries, cudaStream_t s) {
+  static std::once_flag once;
+  std::call_once(once, []() {
+    if (cudaMalloc((void**)&g_visits_dev, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaHostAlloc((void**)&g_visits_host, 2 * sizeof(unsigned long long),
+                      cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      g_visits_dev = nullptr;
+      g_visits_host = nullptr;
+    }
+  });
+  if (!g_visits_dev || !g_visits_host) return nullptr;
+  if (cudaMemsetAsync(g_visits_dev, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_visits_queries.store(queries);
+  return g_visits_dev;
+}
+
+void diag_visits_end(cudaStream_t s) {
+  if (g_visits_dev && g_visits_host)
+    cudaMemcpyAsync(g_visits_host, g_visits_dev, 2 * sizeof(unsigned long long),
+                    cudaMemcpyDeviceToHost, s);
+}
+
 // Precompute / LOOCV blocks in the requested precision.
 static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, int mode,
                       const fmgp_kernel& kern, fmgp_precision precision, Workspace& ws,
@@ -267,6 +297,9 @@ int64_t fmgp_diag_counter(int32_t which) {
   if (which == 0) return (int64_t)g_launches.load();
   if (which == 1) return (int64_t)g_tc_calls.load();
   if (which == 2) return g_tc_fallbacks_host ? (int64_t)*(volatile int*)g_tc_fallbacks_host : -1;
+  if (which == 3 || which == 4)
+    return g_visits_host ? (int64_t)((volatile unsigned long long*)g_visits_host)[which - 3] : -1;
+  if (which == 5) return g_visits_host ? (int64_t)g_visits_queries.load() : -1;
   return -1;
 }
 
@@ -284,6 +317,8 @@ int fmgp_tune_set(const char* key, double value) {
     tp.use_tensor_cores = value != 0.0;
   } else if (k == "tc_fused_select") {
     tp.tc_fused_select = value != 0.0;
+  } else if (k == "count_visits") {
+    tp.count_visits = value != 0.0;
   } else if (k == "tc_oversample") {
     if (!(value >= 2 && value <= 4)) { set_error("tc_oversample out of range [2, 4]"); return FMGP_EINVAL; }
     tp.tc_oversample = (int)value;
@@ -303,6 +338,7 @@ double fmgp_tune_get(const char* key) {
   if (k == "tensor_cores") return tp.use_tensor_cores ? 1.0 : 0.0;
   if (k == "tc_fused_select") return tp.tc_fused_select ? 1.0 : 0.0;
   if (k == "tc_oversample") return tp.tc_oversample;
+  if (k == "count_visits") return tp.count_visits ? 1.0 : 0.0;
   return -1.0;
 }
 

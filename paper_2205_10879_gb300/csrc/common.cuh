@@ -169,6 +169,11 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // that needed the exact fallback (device int) to a host slot read by
 // fmgp_diag_counter after the stream has completed.
 void diag_record_tc(const int* fb_count_dev, cudaStream_t s);
+// Grid kNN visit counters: zeroed device counters for a call over `queries`
+// queries (null if they cannot be had), and their copy to the host slots read
+// by fmgp_diag_counter once the stream has completed.
+unsigned long long* diag_visits_begin(int64_t queries, cudaStream_t s);
+void diag_visits_end(cudaStream_t s);
 int num_sms();
 
 }  // namespace fmgp

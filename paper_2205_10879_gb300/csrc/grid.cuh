@@ -34,6 +34,8 @@ struct GridView {
   int64_t n;
   int D;
   int G;
+  // optional device counters (diagnostics): candidates examined, FP64 keys formed
+  unsigned long long* visits = nullptr;
 };
 
 // Lower bound, in FP32, of the true squared distance between q and x given

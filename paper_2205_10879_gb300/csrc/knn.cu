@@ -58,6 +58,7 @@ __device__ __forceinline__ void grid_knn_search(const GridView& gv, const GridGe
   int cq[3] = {0, 0, 0};
   cell_of<D>(g, qf, cq);
   float pre = density_threshold<D>(gv, g, cq, kq);
+  unsigned int n_exam = 0, n_key = 0;  // per lane, for the optional counters
   for (int attempt = 0; attempt < 2; ++attempt) {
     top.init(kq);
     for (int r = 0;; ++r) {
@@ -77,9 +78,11 @@ __device__ __forceinline__ void grid_knn_search(const GridView& gv, const GridGe
               float xf[D];
 #pragma unroll
               for (int t = 0; t < D; ++t) xf[t] = gv.xs32[(int64_t)j * D + t];
+              ++n_exam;
               if (dist_lower_f32<D>(qf, xf, cerr) <= fminf(top.t_up, pre)) {
                 ck = dbits(canon_key<double>(q64, gv.xs64 + (int64_t)j * D, D));
                 ci = id;
+                ++n_key;
               }
             }
           }
@@ -96,6 +99,14 @@ __device__ __forceinline__ void grid_knn_search(const GridView& gv, const GridGe
     if (top.full() && top.t_up <= pre) break;
     if (pre == __int_as_float(0x7f800000)) break;
     pre = __int_as_float(0x7f800000);
+  }
+  if (gv.visits) {
+    n_exam = __reduce_add_sync(kFull, n_exam);
+    n_key = __reduce_add_sync(kFull, n_key);
+    if (lane == 0) {
+      atomicAdd(&gv.visits[0], (unsigned long long)n_exam);
+      atomicAdd(&gv.visits[1], (unsigned long long)n_key);
+    }
   }
 }
 
@@ -554,9 +565,12 @@ int knn_self(const void* X, fmgp_dtype dtype, int64_t n, int d, int kq, int32_t*
     GridView gv;
     int rc = build_grid(X, dtype, n, d, tp.grid_target, ws, stream, &gv);
     if (rc) return rc;
-    if (d == 1) return launch_grid_self<1>(gv, kq, nbr, dist, stream);
-    if (d == 2) return launch_grid_self<2>(gv, kq, nbr, dist, stream);
-    return launch_grid_self<3>(gv, kq, nbr, dist, stream);
+    if (tp.count_visits) gv.visits = diag_visits_begin(n, stream);
+    rc = d == 1   ? launch_grid_self<1>(gv, kq, nbr, dist, stream)
+         : d == 2 ? launch_grid_self<2>(gv, kq, nbr, dist, stream)
+                  : launch_grid_self<3>(gv, kq, nbr, dist, stream);
+    if (!rc && gv.visits) diag_visits_end(stream);
+    return rc;
   }
   if (tc_knn_eligible(n, d, n, kq))
     return tc_knn(X, dtype, n, d, X, n, kq, true, nbr, dist, ws, stream);
@@ -574,16 +588,20 @@ int knn_query(const void* X, fmgp_dtype dtype, int64_t n, int d, const void* Q, 
     GridView gv;
     int rc = build_grid(X, dtype, n, d, tp.grid_target, ws, stream, &gv);
     if (rc) return rc;
+    if (tp.count_visits) gv.visits = diag_visits_begin(m, stream);
     if (dtype == FMGP_F64) {
       const double* q = (const double*)Q;
-      if (d == 1) return launch_grid_query<1>(gv, q, m, kq, idx, key, stream);
-      if (d == 2) return launch_grid_query<2>(gv, q, m, kq, idx, key, stream);
-      return launch_grid_query<3>(gv, q, m, kq, idx, key, stream);
+      rc = d == 1   ? launch_grid_query<1>(gv, q, m, kq, idx, key, stream)
+           : d == 2 ? launch_grid_query<2>(gv, q, m, kq, idx, key, stream)
+                    : launch_grid_query<3>(gv, q, m, kq, idx, key, stream);
+    } else {
+      const float* q = (const float*)Q;
+      rc = d == 1   ? launch_grid_query<1>(gv, q, m, kq, idx, key, stream)
+           : d == 2 ? launch_grid_query<2>(gv, q, m, kq, idx, key, stream)
+                    : launch_grid_query<3>(gv, q, m, kq, idx, key, stream);
     }
-    const float* q = (const float*)Q;
-    if (d == 1) return launch_grid_query<1>(gv, q, m, kq, idx, key, stream);
-    if (d == 2) return launch_grid_query<2>(gv, q, m, kq, idx, key, stream);
-    return launch_grid_query<3>(gv, q, m, kq, idx, key, stream);
+    if (!rc && gv.visits) diag_visits_end(stream);
+    return rc;
   }
   return knn_query_brute(X, dtype, n, d, Q, m, kq, idx, key, ws, stream);
 }

@@ -94,7 +94,7 @@ def test_tuning_keys_are_host_only_and_range_checked():
     lib.fmgp_tune_set.argtypes = [ctypes.c_char_p, ctypes.c_double]
     lib.fmgp_tune_get.argtypes = [ctypes.c_char_p]
     defaults = {b"tensor_cores": 1.0, b"tc_fused_select": 1.0, b"tc_oversample": 4.0,
-                b"block_warps": 0.0}
+                b"block_warps": 0.0, b"count_visits": 0.0}
     for key, v in defaults.items():
         assert lib.fmgp_tune_get(key) == v, key
     assert lib.fmgp_tune_get(b"no_such_key") == -1.0

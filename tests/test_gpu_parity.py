@@ -371,3 +371,21 @@ def test_loocv_mixed(cuda, precision):
     Qr, resr = oracle.loocv(W.X, W.Y, nb, 50, W.batch, ok)
     assert abs(Q - Qr) / abs(Qr) < MIXED_TOL
     assert rel_rms(res.cpu().numpy(), resr) < MIXED_TOL
+
+
+def test_grid_knn_visit_counters(cuda):
+    """The optional counters of the grid kNN: every query examines at least kq
+    candidates and keys at least kq of them; counting changes no result."""
+    W = wl.tiny(n=3000, m=10)
+    X = dev(W.X)
+    ref, _ = fb.fmgp_build_knn(X, 29)
+    fb.tune_set("count_visits", 1)
+    try:
+        nbr, _ = fb.fmgp_build_knn(X, 29)
+        torch.cuda.synchronize()
+        exam, keys, nq = fb.diag_counter(3), fb.diag_counter(4), fb.diag_counter(5)
+    finally:
+        fb.tune_set("count_visits", 0)
+    assert torch.equal(nbr, ref)
+    assert nq == W.n
+    assert 29 * nq <= keys <= exam <= W.n * (W.n - 1)
