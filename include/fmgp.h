@@ -401,6 +401,9 @@ const char* fmgp_version(void);
  *   "tc_fused_select" 1 = for kq <= 32 the candidates are selected inside the
  *                  tcgen05 distance kernel (default), 0 = distances go through
  *                  a pass buffer in HBM and a separate selection kernel
+ *   "tc_fused_r"   candidates each epilogue thread keeps per range in the fused
+ *                  selection: 0 = by kq (8 for kq <= 4, 16 for kq <= 16, 32 for
+ *                  kq <= 32; default), or 8, 16, 32 (used when R >= kq / 4)
  *   "count_visits" 1 = the grid kNN (d <= 3) counts candidates examined and FP64
  *                  keys formed (diagnostic counters 3-5), 0 = off (default)
  *   "tc_oversample" candidates kept per requested neighbour for the exact

@@ -317,6 +317,9 @@ int fmgp_tune_set(const char* key, double value) {
     tp.use_tensor_cores = value != 0.0;
   } else if (k == "tc_fused_select") {
     tp.tc_fused_select = value != 0.0;
+  } else if (k == "tc_fused_r") {
+    if (!(value == 0 || value == 8 || value == 16 || value == 32)) { set_error("tc_fused_r must be 0, 8, 16 or 32"); return FMGP_EINVAL; }
+    tp.tc_fused_r = (int)value;
   } else if (k == "count_visits") {
     tp.count_visits = value != 0.0;
   } else if (k == "tc_oversample") {
@@ -339,6 +342,7 @@ double fmgp_tune_get(const char* key) {
   if (k == "tc_fused_select") return tp.tc_fused_select ? 1.0 : 0.0;
   if (k == "tc_oversample") return tp.tc_oversample;
   if (k == "count_visits") return tp.count_visits ? 1.0 : 0.0;
+  if (k == "tc_fused_r") return tp.tc_fused_r;
   return -1.0;
 }
 

@@ -11,6 +11,7 @@ struct TuneParams {
   bool use_tensor_cores = true;  // tcgen05 candidate search for d >= 16
   bool tc_fused_select = true;   // candidate selection inside the tcgen05 epilogue (kq <= 32)
   int tc_oversample = 4;         // re-rank candidates per requested neighbour (2..4)
+  int tc_fused_r = 0;            // per-range list length of the fused selection (0 = by kq)
   bool count_visits = false;     // grid kNN counts candidates examined and FP64 keys formed
 };
 

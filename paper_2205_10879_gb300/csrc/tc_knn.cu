@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
       const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN);
       const int c0 = h * (kTN / 64);  // this warpgroup's 4 chunks: c0 .. c0 + 3
       const int64_t g0 = (int64_t)(t_first + t) * kTN + c0 * 32;
-      if constexpr (R <= 8) {
+      if constexpr (R <= 16) {
         // software pipelined: chunk c+1's TMEM load and norms are in flight
         // while chunk c is filtered
         uint32_t va[32], vb[32];
@@ -1129,10 +1129,12 @@ int tc_list_len(int kq) {
 }
 
 // Per-range list length of the fused selection for kq neighbours (0 = the
-// pass-buffer form).
+// pass-buffer form); the tc_fused_r tuning key overrides it (R >= kq / 4).
 int tc_fused_r(int kq) {
   if (!tune_params().tc_fused_select) return 0;
-  return kq <= 4 ? 8 : (kq <= 32 ? 32 : 0);
+  const int o = tune_params().tc_fused_r;
+  if (o && kq <= 32 && (o == 8 || o == 16 || o == 32) && kq <= 4 * o) return o;
+  return kq <= 4 ? 8 : kq <= 16 ? 16 : kq <= 32 ? 32 : 0;
 }
 
 // FP32 rows of X for the re-rank's bounds pass: X itself, or a copy of an
@@ -1202,7 +1204,7 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     // ranges' R-th keys lie well beyond the kq nearest, and at most ~1 GB of
     // per-range lists
     const int sms = num_sms();
-    const int ys_lo = std::min(n_tiles, R == 32 ? 4 : 2);
+    const int ys_lo = std::min(n_tiles, R >= 16 ? 4 : 2);
     const int64_t per_range = 2 * m_pad * R * (int64_t)(sizeof(float) + sizeof(int32_t));
     const int ys_hi = (int)std::max<int64_t>(
         ys_lo, std::min<int64_t>(std::min(n_tiles, 128), (1ll << 30) / per_range));
@@ -1221,6 +1223,10 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     if (R == 8) {
       FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<8>, kTcSelSmem));
       FMGP_LAUNCH(tc_dist_kernel<8><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcSelThreads, kTcSelSmem, s>>>(
+          tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
+    } else if (R == 16) {
+      FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<16>, kTcSelSmem));
+      FMGP_LAUNCH(tc_dist_kernel<16><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcSelThreads, kTcSelSmem, s>>>(
           tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
     } else {
       FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<32>, kTcSelSmem));

@@ -45,7 +45,7 @@ class _Fused:
 @pytest.mark.parametrize("kind,n,d,kq", [("sparse32", 6000, 784, 29), ("u64", 5000, 16, 1),
                                          ("u64", 9000, 64, 31), ("u32", 8000, 64, 63),
                                          ("u32", 4099, 16, 4), ("u64", 4500, 40, 5),
-                                         ("u32", 7001, 24, 32)])
+                                         ("u32", 7001, 24, 32), ("u64", 6100, 32, 16)])
 def test_tensor_core_knn_bitexact_and_certified(cuda, kind, n, d, kq, fused):
     X = _data(kind, n, d, n + d)
     c0 = fb.diag_counter(1)
@@ -126,3 +126,21 @@ def test_oversampling_changes_no_result(cuda):
     rows = np.arange(0, 6000, 97)
     ref_i, _ = oracle.knn(X.astype(np.float64), X.astype(np.float64)[rows], 29, rows)
     np.testing.assert_array_equal(tables[0].cpu().numpy()[rows], ref_i)
+
+
+@pytest.mark.parametrize("r", [8, 16, 32])
+def test_fused_list_length_changes_no_result(cuda, r):
+    """The per-range list length of the fused selection is a speed setting:
+    every length gives the oracle's table (uncertified queries, if any, go
+    through the exact scan)."""
+    X = _data("u32", 5000, 48, 7)
+    prev = fb.tune_get("tc_fused_r")
+    try:
+        fb.tune_set("tc_fused_r", r)
+        nbr, dist = fb.fmgp_build_knn(dev(X), 12, with_dist=True)
+    finally:
+        fb.tune_set("tc_fused_r", prev)
+    rows = np.arange(0, 5000, 41)
+    ref_i, ref_k = oracle.knn(X.astype(np.float64), X.astype(np.float64)[rows], 12, rows)
+    np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
+    np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
