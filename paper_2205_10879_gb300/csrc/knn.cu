@@ -183,11 +183,19 @@ __global__ void maxabs_kernel(const void* X, int f64, int64_t count, unsigned in
 // canonical FP64 keys of those rows together and offers them to the list.
 // So the FP64 key path runs once per round (not once for every row that any
 // lane passes), and the result is the exact top kq by (key, index).
+//
+// Split form (part_idx != null): the launch covers list positions
+// [pos0, pos_end) and blockIdx.y picks the candidate rows
+// [y * range_rows, (y + 1) * range_rows); each warp writes the exact top kq of
+// its range (INT_MAX past the end) to part_idx/part_key at
+// ((p - pos0) * gridDim.y + y) * kq, for merge_parts_kernel.  Otherwise the
+// positions [pos0, count) scan all rows into idx_out/key_out.
 template <typename T, int L>
 __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
     const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_t m, int kq,
     int exclude_self, const unsigned int* maxabs_bits, int32_t* idx_out, double* key_out,
-    const int* qlist, const int* qcount) {
+    const int* qlist, const int* qcount, int64_t pos0, int64_t pos_end, int64_t range_rows,
+    int32_t* part_idx, double* part_key) {
   extern __shared__ float sm[];
   const int ld = d | 1;                      // query rows
   const int tld = min(d, kBfChunk) | 1;      // tile rows: odd stride, conflict-free
@@ -195,10 +203,12 @@ __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
   float* qs = sm + kBfTile * tld;            // kBfWarps x ld
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // query of this warp: position p of the (optional) list
-  const int64_t count = qlist ? (int64_t)*qcount : m;
-  if ((int64_t)blockIdx.x * kBfWarps >= count) return;  // whole CTA idle
-  const int64_t pos = (int64_t)blockIdx.x * kBfWarps + wid;
+  const int64_t count = min(qlist ? (int64_t)*qcount : m, pos_end);
+  if (pos0 + (int64_t)blockIdx.x * kBfWarps >= count) return;  // whole CTA idle
+  const int64_t pos = pos0 + (int64_t)blockIdx.x * kBfWarps + wid;
   const bool qvalid = pos < count;
+  const int64_t r0 = part_idx ? (int64_t)blockIdx.y * range_rows : 0;
+  const int64_t r1 = part_idx ? min(n, r0 + range_rows) : n;
   const int64_t q = qvalid ? (qlist ? (int64_t)qlist[pos] : pos) : 0;
   const float M = __uint_as_float(*maxabs_bits);
   const float cerr = (sizeof(T) == 8) ? 2.5f * kU * M : 0.f;
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
   // stage this CTA's queries (FP32)
   for (int e = threadIdx.x; e < kBfWarps * d; e += blockDim.x) {
     const int w = e / d, j = e % d;
-    const int64_t pp = (int64_t)blockIdx.x * kBfWarps + w;
+    const int64_t pp = pos0 + (int64_t)blockIdx.x * kBfWarps + w;
     const int64_t qq = pp < count ? (qlist ? (int64_t)qlist[pp] : pp) : -1;
     qs[w * ld + j] = qq >= 0 ? (float)Q[qq * d + j] : 0.f;
   }
@@ -214,7 +224,7 @@ __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
   top.init(kq);
   const float* myq = qs + wid * ld;
   const T* qr = Q + q * d;
-  for (int64_t base = 0; base < n; base += kBfTile) {
+  for (int64_t base = r0; base < r1; base += kBfTile) {
     float acc[kBfSub];
 #pragma unroll
     for (int u = 0; u < kBfSub; ++u) acc[u] = 0.f;
@@ -224,7 +234,7 @@ __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
       for (int e = threadIdx.x; e < kBfTile * cw; e += blockDim.x) {
         const int rr = e / cw, j = e - rr * cw;
         const int64_t row = base + rr;
-        tile[rr * tld + j] = row < n ? Xf[row * d + c0 + j] : 0.f;
+        tile[rr * tld + j] = row < r1 ? Xf[row * d + c0 + j] : 0.f;
       }
       __syncthreads();
       for (int j = 0; j < cw; ++j) {
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
 #pragma unroll
     for (int u = 0; u < kBfSub; ++u) {
       const int64_t cand = base + u * 32 + lane;
-      if (cand < n && !(exclude_self && cand == q)) pm |= 1u << u;
+      if (cand < r1 && !(exclude_self && cand == q)) pm |= 1u << u;
     }
     while (true) {
       // next marked row of each lane whose bound passes the current k-th key
@@ -274,7 +284,38 @@ __global__ void __launch_bounds__(kBfWarps * 32) knn_brute_kernel(
       top.offer(ck, ci, lane);
     }
   }
-  if (qvalid) top.store(kq, lane, idx_out + q * kq, key_out ? key_out + q * kq : nullptr);
+  if (!qvalid) return;
+  if (part_idx) {
+    const int64_t slot = ((pos - pos0) * gridDim.y + blockIdx.y) * kq;
+    top.store(kq, lane, part_idx + slot, part_key + slot);
+  } else {
+    top.store(kq, lane, idx_out + q * kq, key_out ? key_out + q * kq : nullptr);
+  }
+}
+
+// One warp per list position p in [pos0, min(count, pos_end)): the kq best by
+// (key, index) of the ny partial lists the split scan wrote for it.
+template <int L>
+__global__ void __launch_bounds__(256) merge_parts_kernel(
+    const int32_t* __restrict__ part_idx, const double* __restrict__ part_key, int ny, int kq,
+    const int* qlist, const int* qcount, int64_t pos0, int64_t pos_end, int32_t* idx_out,
+    double* key_out) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t pos = pos0 + w;
+  if (pos >= min((int64_t)*qcount, pos_end)) return;
+  const int64_t q = qlist[pos];
+  const int tot = ny * kq;
+  const int32_t* pi = part_idx + w * tot;
+  const unsigned long long* pk = reinterpret_cast<const unsigned long long*>(part_key) + w * tot;
+  WarpTopK<L> top;
+  top.init(kq);
+  for (int base = 0; base < tot; base += 32) {
+    const int e = base + lane;
+    const int j = e < tot ? pi[e] : INT_MAX;
+    top.offer(j != INT_MAX ? pk[e] : ~0ull, j, lane);
+  }
+  top.store(kq, lane, idx_out + q * kq, key_out ? key_out + q * kq : nullptr);
 }
 
 template <int D>
@@ -302,10 +343,18 @@ int launch_grid_query(const GridView& gv, const T* Q, int64_t m, int kq, int32_t
   return FMGP_OK;
 }
 
+// List positions (the exact fallback of the tensor-core search) below
+// kSplitPos are spread over up to kSplitRanges candidate ranges, so that a
+// short list keeps many SMs busy; the partial lists are merged per position.
+// Positions beyond scan all rows, kBfWarps queries per CTA.
+constexpr int kSplitPos = 64;
+constexpr int kSplitRanges = 64;
+
 template <typename T, int L>
 int launch_brute_t(const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_t m, int kq,
                    int excl, const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
-                   const int* qlist = nullptr, const int* qcount = nullptr) {
+                   const int* qlist = nullptr, const int* qcount = nullptr,
+                   Workspace* ws = nullptr) {
   const int ld = d | 1;
   const int tld = std::min(d, kBfChunk) | 1;
   const size_t smem = sizeof(float) * ((size_t)kBfTile * tld + (size_t)kBfWarps * ld);
@@ -315,7 +364,31 @@ int launch_brute_t(const T* X, const float* Xf, int64_t n, int d, const T* Q, in
   }
   auto kern = knn_brute_kernel<T, L>;
   FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
-  FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, qlist, qcount));
+  if (!qlist) {
+    FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(
+        X, Xf, n, d, Q, m, kq, excl, mx, idx, key, nullptr, nullptr, 0, m, 0, nullptr, nullptr));
+    FMGP_CUDA_TRY(cudaGetLastError());
+    return FMGP_OK;
+  }
+  if (!ws) {
+    set_error("exhaustive kNN over a list needs a workspace");
+    return FMGP_EINVAL;
+  }
+  const int64_t P = std::min<int64_t>(m, kSplitPos);
+  const int64_t range_rows =
+      (int64_t)ceil_div(ceil_div(n, std::min<int64_t>(kSplitRanges, ceil_div(n, kBfTile))),
+                        kBfTile) * kBfTile;
+  const int ny = ceil_div(n, range_rows);
+  int32_t* pidx = ws->get<int32_t>((size_t)P * ny * kq);
+  double* pkey = ws->get<double>((size_t)P * ny * kq);
+  if (!pidx || !pkey) return FMGP_ENOMEM;
+  FMGP_LAUNCH(kern<<<dim3((unsigned)ceil_div(P, kBfWarps), (unsigned)ny), kBfWarps * 32, smem, s>>>(
+      X, Xf, n, d, Q, m, kq, excl, mx, idx, key, qlist, qcount, 0, P, range_rows, pidx, pkey));
+  FMGP_LAUNCH(merge_parts_kernel<L><<<ceil_div(P * 32, 256), 256, 0, s>>>(
+      pidx, pkey, ny, kq, qlist, qcount, 0, P, idx, key));
+  if (m > P)
+    FMGP_LAUNCH(kern<<<ceil_div(m - P, kBfWarps), kBfWarps * 32, smem, s>>>(
+        X, Xf, n, d, Q, m, kq, excl, mx, idx, key, qlist, qcount, P, m, 0, nullptr, nullptr));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
 }
@@ -323,12 +396,13 @@ int launch_brute_t(const T* X, const float* Xf, int64_t n, int d, const T* Q, in
 template <typename T>
 int launch_brute_mx(const T* X, const float* Xf, int64_t n, int d, const T* Q, int64_t m, int kq,
                     int excl, const unsigned int* mx, int32_t* idx, double* key, cudaStream_t s,
-                    const int* qlist = nullptr, const int* qcount = nullptr) {
-  if (kq <= 32) return launch_brute_t<T, 1>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 64) return launch_brute_t<T, 2>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 96) return launch_brute_t<T, 3>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  if (kq <= 128) return launch_brute_t<T, 4>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
-  return launch_brute_t<T, 5>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+                    const int* qlist = nullptr, const int* qcount = nullptr,
+                    Workspace* ws = nullptr) {
+  if (kq <= 32) return launch_brute_t<T, 1>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount, ws);
+  if (kq <= 64) return launch_brute_t<T, 2>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount, ws);
+  if (kq <= 96) return launch_brute_t<T, 3>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount, ws);
+  if (kq <= 128) return launch_brute_t<T, 4>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount, ws);
+  return launch_brute_t<T, 5>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount, ws);
 }
 
 // FP32 rows the exhaustive scan stages: X itself, or a copy of an FP64 X.
@@ -357,7 +431,7 @@ int launch_brute(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, in
   if (rc) return rc;
   const float* Xf = Xf_in ? Xf_in : brute_rows(X, n, d, ws, s, &rc);
   if (rc) return rc;
-  return launch_brute_mx<T>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount);
+  return launch_brute_mx<T>(X, Xf, n, d, Q, m, kq, excl, mx, idx, key, s, qlist, qcount, &ws);
 }
 
 // ------------------------------------------- nearest point, 4 <= d < 16 --

@@ -144,3 +144,27 @@ def test_fused_list_length_changes_no_result(cuda, r):
     ref_i, ref_k = oracle.knn(X.astype(np.float64), X.astype(np.float64)[rows], 12, rows)
     np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
     np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
+
+
+@pytest.mark.parametrize("kind,n,d,kq,r", [("sparse32", 6000, 784, 29, 8), ("u64", 6000, 40, 20, 8)])
+def test_exact_fallback_of_uncertified_queries(cuda, kind, n, d, kq, r):
+    """Per-range lists too short for kq leave many queries without a
+    certificate; the exhaustive scan over the device-side list (the first
+    positions split over candidate ranges and merged, the rest scanned whole)
+    must still give the oracle's table."""
+    X = _data(kind, n, d, 5)
+    prev = fb.tune_get("tc_fused_r")
+    try:
+        fb.tune_set("tc_fused_r", r)
+        nbr, dist = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
+        torch.cuda.synchronize()
+        redone = fb.diag_counter(2)
+    finally:
+        fb.tune_set("tc_fused_r", prev)
+    assert redone > 64, redone  # both the split and the whole-scan positions ran
+    rows = np.arange(0, n, 37)
+    ref_i, ref_k = oracle.knn(X.astype(np.float64), X.astype(np.float64)[rows], kq, rows)
+    np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
+    np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
+    ref_all, _ = fb.fmgp_build_knn(dev(X), kq)
+    assert torch.equal(nbr, ref_all)
