@@ -168,3 +168,21 @@ def test_exact_fallback_of_uncertified_queries(cuda, kind, n, d, kq, r):
     np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
     ref_all, _ = fb.fmgp_build_knn(dev(X), kq)
     assert torch.equal(nbr, ref_all)
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+def test_bf16_useless_data_still_exact(cuda, fused):
+    """Coordinates near 1000 with spread 10: BF16 (spacing 4 there) cannot
+    separate the points, so the certificate fails for nearly every query and
+    the exact scan answers them; the table must still be the oracle's."""
+    rng = np.random.default_rng(21)
+    X = 1000.0 + 10.0 * rng.random((5000, 24))
+    with _Fused(fused):
+        nbr, dist = fb.fmgp_build_knn(dev(X), 6, with_dist=True)
+        torch.cuda.synchronize()
+        redone = fb.diag_counter(2)
+    assert redone > 100, redone
+    rows = np.arange(0, 5000, 23)
+    ref_i, ref_k = oracle.knn(X, X[rows], 6, rows)
+    np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
+    np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
