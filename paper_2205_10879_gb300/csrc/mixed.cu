@@ -458,14 +458,27 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
       float prev = 1.0f;
       bool conv = false;
       for (int step = 1; step <= kMaxRefine; ++step) {
-        // residual y - K x in DF; lane owns rows; K_ab = (upper hi, packed lo)
+        // residual y - K x; lane owns rows; K_ab = (upper hi, packed lo).
+        // Compensated dot product (Dot2 of Ogita, Rump & Oishi, SIAM J. Sci.
+        // Comput. 26, 2005): the leading products hi * x.hi are split exactly
+        // (TwoProduct by FMA) and summed with TwoSum into p; the rounding
+        // errors and the small cross terms hi * x.lo + lo * x.hi collect in
+        // one FP32 sum e.  The result is as accurate as if computed with twice
+        // the working precision (error ~u|r| + (n u)^2 sum |K_ab x_b|), far
+        // below what the FP32 correction solve can use; only fl(p + e) is
+        // passed on.
         for (int c = 0; c < r; ++c) {
-          dfl acc[NS];
+          float p[NS], e[NS];
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
             const int row = lane + 32 * s;
-            acc[s] = dfl{0.0f, 0.0f};
-            if (row < k) acc[s] = df_add(YS[row * r + c], df_neg(df_mul(kp.diag, XV[row * r + c])));
+            p[s] = 0.0f;
+            e[s] = 0.0f;
+            if (row < k) {
+              const dfl a = df_add(YS[row * r + c], df_neg(df_mul(kp.diag, XV[row * r + c])));
+              p[s] = a.hi;
+              e[s] = a.lo;
+            }
           }
           int cb = 0;  // b(b-1)/2
 #pragma unroll 2
@@ -480,7 +493,16 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
                 const bool below = b < row;
                 const float hi = below ? M[b * ldl + row] : M[row * ldl + b];
                 const float lo = below ? LO[row * (row - 1) / 2 + b] : LO[cb + row];
-                acc[s] = df_add(acc[s], df_neg(df_mul(dfl{hi, lo}, xb)));
+                const float h = __fmul_rn(hi, xb.hi);
+                const float hr = __fmaf_rn(hi, xb.hi, -h);  // hi * x.hi = h + hr exactly
+                const float t = __fadd_rn(p[s], -h);        // TwoSum(p, -h) = t + q
+                const float bv = __fsub_rn(t, p[s]);
+                const float q = __fadd_rn(__fsub_rn(p[s], __fsub_rn(t, bv)), __fsub_rn(-h, bv));
+                p[s] = t;
+                float es = __fsub_rn(e[s], hr);
+                es = __fadd_rn(es, q);
+                es = __fmaf_rn(-hi, xb.lo, es);
+                e[s] = __fmaf_rn(-lo, xb.hi, es);
               }
             }
             cb += b;
@@ -488,7 +510,7 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
 #pragma unroll
           for (int s = 0; s < NS; ++s) {
             const int row = lane + 32 * s;
-            if (row < k) RV[row * r + c] = acc[s].hi;
+            if (row < k) RV[row * r + c] = __fadd_rn(p[s], e[s]);
           }
         }
         __syncwarp();
