@@ -61,6 +61,7 @@ __device__ __forceinline__ void grid_knn_search(const GridView& gv, const GridGe
   unsigned int n_exam = 0, n_key = 0;  // per lane, for the optional counters
   for (int attempt = 0; attempt < 2; ++attempt) {
     top.init(kq);
+    bool fresh = true;  // the first batch goes into the empty list by one sort
     for (int r = 0;; ++r) {
       for_ring_segments<D>(r, cq, g.G, [&](int c0a, int c0b, int c1, int c2) {
         const float lim = fminf(top.t_up, pre);
@@ -86,7 +87,12 @@ __device__ __forceinline__ void grid_knn_search(const GridView& gv, const GridGe
               }
             }
           }
-          top.offer(ck, ci, lane);
+          if (fresh) {
+            top.fill_sorted(ck, ci, lane);
+            fresh = false;
+          } else {
+            top.offer(ck, ci, lane);
+          }
         }
       });
       const float out = outside_lower<D>(g, qf, margin, cq, r);

@@ -60,6 +60,42 @@ struct WarpTopK {
     t_up = key_bits_to_float_up(tk);
   }
 
+  // Into an empty list (just after init), put the one candidate per lane
+  // (ck = ~0 for none) in order: a bitonic sort across the warp by (key,
+  // index), then lane l takes sorted positions l*L .. l*L+L-1.  The same list
+  // as offering them one by one, for the cost of one sorting network.
+  __device__ __forceinline__ void fill_sorted(unsigned long long ck, int ci, int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(kFull, ck, stride);
+        const int oi = __shfl_xor_sync(kFull, ci, stride);
+        const bool asc = (lane & size) == 0;
+        const bool low = (lane & stride) == 0;
+        // the lower lane of a pair keeps the smaller in an ascending run
+        const bool take = (low == asc) ? key_less(ok, oi, ck, ci) : key_less(ck, ci, ok, oi);
+        if (take) { ck = ok; ci = oi; }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < L; ++s) {
+      const int src = lane * L + s;
+      const unsigned long long vk = __shfl_sync(kFull, ck, src & 31);
+      const int vi = __shfl_sync(kFull, ci, src & 31);
+      k[s] = src < 32 ? vk : ~0ull;
+      i[s] = src < 32 ? vi : INT_MAX;
+    }
+    unsigned long long mk = k[0];
+    int mi = i[0];
+#pragma unroll
+    for (int s = 1; s < L; ++s)
+      if (s == ts) { mk = k[s]; mi = i[s]; }
+    tk = __shfl_sync(kFull, mk, tl);
+    ti = __shfl_sync(kFull, mi, tl);
+    t_up = key_bits_to_float_up(tk);
+  }
+
   // Offer one candidate per lane (ck = ~0 for none); inserts every candidate
   // that belongs in the list, lowest lane first.
   __device__ __forceinline__ void offer(unsigned long long ck, int ci, int lane) {
