@@ -99,7 +99,13 @@ enum {
  *   dist_out n x kq FP64 canonical keys (squared distances), or NULL.
  *   flags    0 (reserved).
  * Search: a uniform grid over the bounding box for d <= 3; a tiled scan with
- * an FP32 prefilter and an exact FP64 re-rank for d >= 4.
+ * an FP32 prefilter and an exact FP64 re-rank for 4 <= d <= 15 (and for
+ * d >= 16 below 4,096 points, above kq = 96, or with "tensor_cores" off);
+ * otherwise candidates from a BF16 tcgen05 GEMM with FP32 accumulation (the
+ * candidate selection fused into its epilogue for kq <= 32), an exact re-rank
+ * of tc_oversample * kq candidates, and a certificate that every candidate
+ * left out is farther than the kq-th; queries without one are redone by the
+ * exhaustive scan.  The table never depends on the path taken.
  * Returns FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM or FMGP_ECUDA.
  */
 int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
@@ -145,6 +151,10 @@ int fmgp_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
  *   Z          m x d test features, same dtype as X; m >= 0 (m = 0 is a no-op).
  *   Yhat_out   m x r FP64.
  *   nearest_out m int32 j* per test point, or NULL.
+ * Nearest-point search: the grid for d <= 3, a thread-per-query FP32 scan with
+ * FP64 keys for the candidates it cannot separate for 4 <= d <= 15, and the
+ * tensor-core search of fmgp_build_knn (kq = 1) for d >= 16; j* is exact on
+ * every path.
  * Returns FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM or FMGP_ECUDA.
  */
 int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
