@@ -17,7 +17,7 @@ constexpr float kU = 5.9604645e-8f;  // 2^-24
 // ---------------------------------------------------------------- grid ----
 // Initial distance threshold from the local density: the number of points in
 // the 3^D block of cells around the query, over the block's volume, gives the
-// radius expected to hold ~1.6 kq points.  It only prunes: if the search ends
+// radius expected to hold ~1.4 kq points.  It only prunes: if the search ends
 // with fewer than kq points inside it, or with a k-th key above it, the query
 // is searched again without it, so the result never depends on the guess.
 template <int D>
@@ -41,7 +41,7 @@ __device__ __forceinline__ float density_threshold(const GridView& gv, const Gri
              gv.cell_start[cell_linear(lo0, c1, c2, g.G, D)];
   if (cnt < 2 || !(vol > 0.f)) return __int_as_float(0x7f800000);
   const float unit = D == 1 ? 2.f : (D == 2 ? 3.14159265f : 4.18879020f);
-  const float rD = 1.6f * (float)kq * vol / ((float)cnt * unit);  // r^D
+  const float rD = 1.4f * (float)kq * vol / ((float)cnt * unit);  // r^D
   const float r = D == 1 ? rD : (D == 2 ? sqrtf(rD) : cbrtf(rD));
   return r * r;
 }
