@@ -87,7 +87,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done) : "r"(addr), "r"(parity) : "memory");
     if (done) return true;
-    if (*abort) return false;
+    if (abort && *abort) return false;
     if (global_timer() - t0 > 2000000000ull) return false;
   }
 }
@@ -274,10 +274,12 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
+  uint64_t* drain = (uint64_t*)(tmem_slot + 2);  // MMA completion after an abort
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int qb = blockIdx.x;
   const int t_first = tile0 + blockIdx.y * tpc;
   const int n_tiles = max(0, min(tpc, tile_end - t_first));
+  int it_issued = 0;  // stages the producer filled (its thread only)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kTcEpiWarps(R));
     }
+    mbar_init(drain, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -317,6 +320,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
           tma_load_2d(a + kABytes, &tmX, &full[s], kc * kTK, (t_first + t) * kTN);
         }
       }
+      it_issued = it;
     }
   } else if (warp == 5) {
     if (lane == 0) {  // MMA issuer
@@ -444,8 +448,22 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
   }
   tc_fence_before();
   __syncthreads();
-  if (*abort && threadIdx.x == 0) atomicExch(err, 1);
+  const bool aborted = *abort != 0;
+  if (aborted && threadIdx.x == 0) atomicExch(err, 1);
+  // After an abort, wait (bounded, whatever the flag) for this CTA's own
+  // asynchronous work: the producer for the copies it issued, so none lands in
+  // shared memory after the CTA is gone; the MMA thread for its MMAs, before
+  // the accumulator is freed.
+  if (aborted && warp == 4 && lane == 0) {
+    for (int j = max(0, it_issued - kStages); j < it_issued; ++j)
+      mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u, nullptr);
+  }
   if (warp == 5) {
+    if (aborted && lane == 0) {
+      mma_commit(drain);
+      mbar_wait(drain, 0u, nullptr);
+    }
+    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(2 * kTN));
