@@ -16,6 +16,9 @@ Each pin is chosen so that a plausible slip in the oracle fails it:
    precomputed C (Eq. 6).
  - sigma^2 invariance of the mean and 1/sigma^2 scaling of C.
  - Long-double re-evaluation bounds the FP64 rounding error.
+ - k = 1 and k = 2 neighbourhoods: C and the prediction in closed form (a
+   scalar division, the textbook 2 x 2 inverse) with the Bessel-form kernel;
+   the LOOCV objective with one neighbour in closed form.
  - Subsampled precompute (Sec. 5): with every training point as a centre it is
    the full method; at a test point whose nearest training point is a centre
    it agrees with the full method; at a centre it interpolates (as Eq. 7 does).
@@ -388,3 +391,60 @@ def test_subsample_interpolates_at_centres():
     yr, cr = oracle.predict_rows(W.X, nbr, rows, Cs, kern, W.X[rows])
     np.testing.assert_array_equal(cr, rows)
     np.testing.assert_allclose(yr, W.Y[rows] - 1e-4 * Cs[:, 0, :], rtol=0, atol=1e-9)
+
+
+def _nearest_other(X, i):
+    d2 = ((X - X[i]) ** 2).sum(1)
+    d2[i] = np.inf
+    return int(np.argmin(d2))
+
+
+def test_small_neighbourhoods_match_closed_forms():
+    """k = 1 and k = 2 reduce Eqs. 6-7 to a scalar division and the textbook
+    2 x 2 inverse, with the kernel from the Bessel form of Eq. 3: pins the
+    assembly (variance, nugget on the diagonal only), the solve and the
+    prediction's use of S_{j*} = [j*, its neighbour]."""
+    W = wl.tiny(n=300, m=25)
+    s2, tau2, rho, nu = 1.7, 3e-3, 0.1, 1.5
+    kern = oracle.kernel("matern", nu, rho, s2, tau2)
+    X, y, Z = W.X, W.Y[:, 0], W.Z
+    nn = np.array([_nearest_other(X, i) for i in range(W.n)])
+    # k = 1: C_i = y_i / (s2 (1 + tau2)); yhat(z) = s2 phi(|z - x_j*|) C_j*
+    C1, _ = oracle.precompute(X, W.Y, nn[:, None].astype(np.int32), 1, kern)
+    np.testing.assert_allclose(C1[:, 0, 0], y / (s2 * (1 + tau2)), rtol=1e-13)
+    yh1, near = oracle.predict(X, nn[:, None].astype(np.int32), C1, kern, Z)
+    dz = np.sqrt(((Z - X[near]) ** 2).sum(1))
+    np.testing.assert_allclose(yh1[:, 0], matern_bessel(dz / rho, nu) * y[near] / (1 + tau2),
+                               rtol=1e-11)
+    # k = 2: S_i = [i, nn(i)], K = s2 [[1+tau2, p], [p, 1+tau2]]
+    C2, _ = oracle.precompute(X, W.Y, nn[:, None].astype(np.int32), 2, kern)
+    p = matern_bessel(np.sqrt(((X - X[nn]) ** 2).sum(1)) / rho, nu)
+    a = 1 + tau2
+    det = s2 * (a * a - p * p)
+    c0 = (a * y - p * y[nn]) / det
+    c1 = (-p * y + a * y[nn]) / det
+    np.testing.assert_allclose(C2[:, 0, 0], c0, rtol=1e-9)
+    np.testing.assert_allclose(C2[:, 1, 0], c1, rtol=1e-9)
+    yh2, near2 = oracle.predict(X, nn[:, None].astype(np.int32), C2, kern, Z)
+    j = near2
+    pz0 = matern_bessel(np.sqrt(((Z - X[j]) ** 2).sum(1)) / rho, nu)
+    pz1 = matern_bessel(np.sqrt(((Z - X[nn[j]]) ** 2).sum(1)) / rho, nu)
+    np.testing.assert_allclose(yh2[:, 0], s2 * (pz0 * c0[j] + pz1 * c1[j]), rtol=1e-9,
+                               atol=1e-12)
+
+
+def test_loocv_with_one_neighbour_is_a_scaled_copy():
+    """k = 1 in Eqs. 4-5: each batch point is predicted from its nearest other
+    point alone, yhat_i = phi(d_ij) y_j / (1 + tau2), so Q is the mean squared
+    difference."""
+    W = wl.tiny(n=250, m=5)
+    tau2, rho = 1e-2, 0.2
+    kern = oracle.kernel("matern", 0.5, rho, 2.0, tau2)
+    X, y = W.X, W.Y[:, 0]
+    nn = np.array([_nearest_other(X, i) for i in range(W.n)], np.int32)
+    batch = np.array([0, 9, 41, 100, 249], np.int64)
+    Q, res = oracle.loocv(X, W.Y, nn[:, None], 1, batch, kern)
+    d = np.sqrt(((X[batch] - X[nn[batch]]) ** 2).sum(1))
+    yh = matern_bessel(d / rho, 0.5) * y[nn[batch]] / (1 + tau2)
+    np.testing.assert_allclose(res, (y[batch] - yh) ** 2, rtol=1e-10, atol=1e-15)
+    assert Q == pytest.approx(np.mean((y[batch] - yh) ** 2), rel=1e-10)
