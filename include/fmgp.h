@@ -100,10 +100,10 @@ enum {
  *   flags    0 (reserved).
  * Search: a uniform grid over the bounding box for d <= 3; a tiled scan with
  * an FP32 prefilter and an exact FP64 re-rank for 4 <= d <= 15 (and for
- * d >= 16 below 4,096 points, above kq = 96, or with "tensor_cores" off);
- * otherwise candidates from a BF16 tcgen05 GEMM with FP32 accumulation (the
- * candidate selection fused into its epilogue for kq <= 32), an exact re-rank
- * of tc_oversample * kq candidates, and a certificate that every candidate
+ * d >= 16 below 4,096 points or with "tensor_cores" off); otherwise
+ * candidates from a BF16 tcgen05 GEMM with FP32 accumulation (the candidate
+ * selection fused into its epilogue), an exact re-rank of tc_oversample * kq
+ * candidates (2 kq above kq = 64), and a certificate that every candidate
  * left out is farther than the kq-th; queries without one are redone by the
  * exhaustive scan.  The table never depends on the path taken.
  * Returns FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM or FMGP_ECUDA.
@@ -385,6 +385,10 @@ int fmgp_server_destroy(fmgp_server* srv);
  *  - Only FMGP_PREC_FP64 is accepted (FMGP_EUNSUPPORTED otherwise).
  *  - The first call on a device looks up the array's device address with
  *    that device current; make that first call before any stream capture.
+ *    It is also the call at which the CUDA driver loads this library's
+ *    kernels and the array onto the device (with lazy module loading, the
+ *    default), which takes device memory: make it once during start-up, as
+ *    a warm-up, or run with CUDA_MODULE_LOADING=EAGER.
  *  - All calls share the one array, which keeps the previous call's contents
  *    (the call clears its failure counter itself).  Calls that overlap on the
  *    GPU, from several streams or threads, race on it: serialise them.
@@ -408,17 +412,24 @@ const char* fmgp_version(void);
  *   "grid_target"  mean training points per grid cell of the d <= 3 search (default 12)
  *   "block_warps"  warps per CTA of the neighbourhood kernels, 0 = automatic
  *   "tensor_cores" 1 = tcgen05 candidate search for kNN at d >= 16 (default), 0 = off
- *   "tc_fused_select" 1 = for kq <= 32 the candidates are selected inside the
- *                  tcgen05 distance kernel (default), 0 = distances go through
- *                  a pass buffer in HBM and a separate selection kernel
+ *   "tc_fused_select" 1 = the candidates are selected inside the tcgen05
+ *                  distance kernel (default), 0 = distances go through a pass
+ *                  buffer in HBM and a separate selection kernel
  *   "tc_fused_r"   candidates each epilogue thread keeps per range in the fused
- *                  selection: 0 = by kq (8 for kq <= 4, 16 for kq <= 16, 32 for
- *                  kq <= 32; default), or 8, 16, 32 (used when R >= kq / 4)
+ *                  selection: 0 = by kq (8 for kq <= 4, 16 for kq <= 16, 32
+ *                  above; default), or 8, 16, 32 (used when kq <= 32 and
+ *                  R >= kq / 4).  Above kq = 32 the lists keep 32 and the
+ *                  candidates are split into at least ceil(kq / 8) ranges.
  *   "count_visits" 1 = the grid kNN (d <= 3) counts candidates examined and FP64
  *                  keys formed (diagnostic counters 3-5), 0 = off (default)
  *   "tc_oversample" candidates kept per requested neighbour for the exact
  *                  re-rank of the tensor-core search (2..4, default 4; at
- *                  least 32, at most 128 per query)
+ *                  least 32; at most 128 per query, or 2 kq where that is
+ *                  larger, up to 320)
+ *   "tc_chunk_queries" queries per pass of the fused tensor-core selection
+ *                  (rounded down to whole blocks of 128, at least one block;
+ *                  0 = as many as keep its per-range lists within ~1 GB,
+ *                  default)
  * Process-wide; returns FMGP_EINVAL for an unknown key or a value out of range.
  */
 int fmgp_tune_set(const char* key, double value);

@@ -26,6 +26,8 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+void clear_error() { g_err[0] = 0; }
+
 int cuda_fail(cudaError_t e, const char* what) {
   set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
   return FMGP_ECUDA;
@@ -325,6 +327,9 @@ int fmgp_tune_set(const char* key, double value) {
   } else if (k == "tc_oversample") {
     if (!(value >= 2 && value <= 4)) { set_error("tc_oversample out of range [2, 4]"); return FMGP_EINVAL; }
     tp.tc_oversample = (int)value;
+  } else if (k == "tc_chunk_queries") {
+    if (!(value >= 0 && value <= 2147483647.0)) { set_error("tc_chunk_queries out of range"); return FMGP_EINVAL; }
+    tp.tc_chunk_queries = (int64_t)value;
   } else {
     set_error("unknown tuning key '%s'", key);
     return FMGP_EINVAL;
@@ -343,12 +348,13 @@ double fmgp_tune_get(const char* key) {
   if (k == "tc_oversample") return tp.tc_oversample;
   if (k == "count_visits") return tp.count_visits ? 1.0 : 0.0;
   if (k == "tc_fused_r") return tp.tc_fused_r;
+  if (k == "tc_chunk_queries") return (double)tp.tc_chunk_queries;
   return -1.0;
 }
 
 int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
                    int32_t* nbr_out, double* dist_out, int32_t flags, void* stream) {
-  g_err[0] = 0;
+  clear_error();
   if (!dtype_ok(dtype)) return FMGP_EINVAL;
   FMGP_REQUIRE(X && nbr_out, "X and nbr_out must be non-NULL");
   FMGP_REQUIRE(n >= 2 && n < INT32_MAX, "n = %lld out of range [2, 2^31)", (long long)n);
@@ -379,7 +385,7 @@ int fmgp_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
                     int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
                     const fmgp_kernel* kernel, fmgp_precision precision, void* C_out,
                     int8_t* status_out, void* stream) {
-  g_err[0] = 0;
+  clear_error();
   int rc = validate_block_args(X, dtype, Y, n, d, r, k > 1 ? nbr : (const int32_t*)X, nbr_ld,
                                kernel, precision);
   if (rc) return rc;
@@ -422,7 +428,7 @@ int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const in
                  int32_t nbr_ld, const void* C, int32_t k, int32_t r, const fmgp_kernel* kernel,
                  fmgp_precision precision, const void* Z, int64_t m, double* Yhat_out,
                  int32_t* nearest_out, void* stream) {
-  g_err[0] = 0;
+  clear_error();
   if (!dtype_ok(dtype) || !kernel_ok(kernel) || !prec_ok(precision)) return FMGP_EINVAL;
   FMGP_REQUIRE(m >= 0, "m = %lld must be >= 0", (long long)m);
   FMGP_REQUIRE(X && C, "X and C must be non-NULL");
@@ -451,7 +457,7 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
                          const int64_t* batch, int64_t b, const fmgp_kernel* kernel,
                          fmgp_precision precision, double* Q_out, double* resid_out,
                          void* stream) {
-  g_err[0] = 0;
+  clear_error();
   int rc = validate_block_args(X, dtype, Y, n, d, r, nbr, nbr_ld, kernel, precision);
   if (rc) return rc;
   FMGP_REQUIRE(Q_out && batch, "Q_out and batch must be non-NULL");
@@ -499,7 +505,7 @@ int fmgp_muygps_predict(const void* X, fmgp_dtype dtype, const double* Y, int64_
                         int32_t r, const void* Z, int64_t m, int32_t k, const fmgp_kernel* kernel,
                         fmgp_precision precision, double* Yhat_out, int32_t* nbr_out,
                         void* stream) {
-  g_err[0] = 0;
+  clear_error();
   if (!dtype_ok(dtype) || !kernel_ok(kernel) || !prec_ok(precision)) return FMGP_EINVAL;
   FMGP_REQUIRE(X && Y, "X and Y must be non-NULL");
   FMGP_REQUIRE(n >= 1 && n < INT32_MAX, "n = %lld out of range [1, 2^31)", (long long)n);
@@ -546,7 +552,7 @@ int fmgp_precompute_rows(const void* X, fmgp_dtype dtype, const double* Y, int64
                          const int32_t* rows, int64_t s_rows, const fmgp_kernel* kernel,
                          fmgp_precision precision, void* C_out, int8_t* status_out,
                          void* stream) {
-  g_err[0] = 0;
+  clear_error();
   int rc = validate_block_args(X, dtype, Y, n, d, r, k > 1 ? nbr : (const int32_t*)X, nbr_ld,
                                kernel, precision);
   if (rc) return rc;
@@ -594,7 +600,7 @@ int fmgp_predict_rows(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, con
                       int32_t k, int32_t r, const fmgp_kernel* kernel, fmgp_precision precision,
                       const void* Z, int64_t m, double* Yhat_out, int32_t* nearest_out,
                       void* stream) {
-  g_err[0] = 0;
+  clear_error();
   if (!dtype_ok(dtype) || !kernel_ok(kernel) || !prec_ok(precision)) return FMGP_EINVAL;
   FMGP_REQUIRE(m >= 0, "m = %lld must be >= 0", (long long)m);
   FMGP_REQUIRE(X && C && rows, "X, C and rows must be non-NULL");

@@ -47,6 +47,8 @@ constexpr int kTcThreads = 192;          // warps 0-3 epilogue, 4 producer, 5 MM
 // half of each tile's columns, so two warps per SM sub-partition hide the
 // latency of the TMEM loads and the per-chunk filtering
 constexpr int kTcSelThreads = 320;
+// longest candidate list of the re-rank (2 kq for kq = 160)
+constexpr int kMaxTcList = 320;
 constexpr int kTcEpiWarps(int R) { return R > 0 ? 8 : 4; }
 constexpr size_t kTcSmem = (size_t)kStages * kStageBytes + 1024 + 256;
 // fused selection: per epilogue thread a 32-float row of the current chunk's
@@ -250,8 +252,9 @@ __device__ __forceinline__ void load_norms(const float* xnorm, int64_t gcol, flo
   for (int q = 0; q < 8; ++q) xv[q] = xn4[q];
 }
 
-// Approximate squared distances of query block blockIdx.x against candidate
-// tiles tile0 + blockIdx.y*tpc .. (at most tpc tiles, not past tile_end).
+// Approximate squared distances of query block qb0 + blockIdx.x against
+// candidate tiles tile0 + blockIdx.y*tpc .. (at most tpc tiles, not past
+// tile_end).  Query q below is counted from the first query of block qb0.
 // R == 0: out row q (query q), column (t - tile0)*256 + j holds candidate
 //   t*256 + j.
 // R > 0: for each half h of the tile columns, the R smallest (clamped at 0;
@@ -263,9 +266,10 @@ __device__ __forceinline__ void load_norms(const float* xnorm, int64_t gcol, flo
 template <int R>
 __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist_kernel(
     const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX,
-    const float* __restrict__ qnorm, const float* __restrict__ xnorm, int tile0, int tile_end,
-    int tpc, int k_chunks, int64_t ld_out, float* __restrict__ out, int64_t n_valid, int self,
-    float* __restrict__ pkey, int32_t* __restrict__ pidx, int* __restrict__ err) {
+    const float* __restrict__ qnorm, const float* __restrict__ xnorm, int qb0, int tile0,
+    int tile_end, int tpc, int k_chunks, int64_t ld_out, float* __restrict__ out,
+    int64_t n_valid, int self, float* __restrict__ pkey, int32_t* __restrict__ pidx,
+    int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + (size_t)kStages * kStageBytes);
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
   volatile int* abort = (volatile int*)(tmem_slot + 1);
   uint64_t* drain = (uint64_t*)(tmem_slot + 2);  // MMA completion after an abort
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int qb = blockIdx.x;
+  const int qb = qb0 + (int)blockIdx.x;
   const int t_first = tile0 + blockIdx.y * tpc;
   const int n_tiles = max(0, min(tpc, tile_end - t_first));
   int it_issued = 0;  // stages the producer filled (its thread only)
@@ -408,7 +412,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[b]);
     }
-    const int64_t seg = qrow * 2 * gridDim.y + 2 * blockIdx.y + h;
+    const int64_t seg = (qrow - (int64_t)qb0 * kTM) * 2 * gridDim.y + 2 * blockIdx.y + h;
     float* okey = pkey + seg * R;
     int32_t* oidx = pidx + seg * R;
 #pragma unroll
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
   } else {  // epilogue warps 0-3: TMEM lanes 32*warp .. 32*warp+31
     const int row = warp * 32 + lane;
     const float qn = qnorm[(int64_t)qb * kTM + row];
-    float* orow = out + ((int64_t)qb * kTM + row) * ld_out;
+    float* orow = out + ((int64_t)(qb - qb0) * kTM + row) * ld_out;
     for (int t = 0; t < n_tiles; ++t) {
       const int b = t & 1;
       const uint32_t u = (uint32_t)(t >> 1);
@@ -547,7 +551,7 @@ __global__ void __launch_bounds__(256) select_merge_kernel(
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const int g = lane * S + s;
-      const int j = cand[q * L + g];
+      const int j = g < L ? cand[q * L + g] : INT_MAX;
       top.k[s] = j == INT_MAX ? ~0u : __float_as_uint(ckey[q * L + g]);
       top.i[s] = j;
     }
@@ -767,10 +771,20 @@ __device__ __forceinline__ void load_rows(const T* X, int d, const int* rows, in
   }
 }
 
+// Dynamic shared memory of rerank_kernel<T, S, KS>: per warp a row tile
+// (32 candidate rows and the query row, kRrChunk features each), and two
+// candidate-slot lists and two FP32 interval bounds of 32*S entries.
+template <typename T>
+constexpr size_t rr_smem_bytes(int S) {
+  return (size_t)kRrWarps * 33 * (kRrChunk + 1) * sizeof(T) +
+         (size_t)kRrWarps * 2 * 32 * S * (sizeof(int) + sizeof(float));
+}
+
 // Xa, Qa: FP32 copies of the rows for the bounds pass A (X, Q themselves for
 // FP32 inputs; for FP64 inputs converted once, not per candidate visit).
+// At most 32*S candidates per query (L <= 32*S), kq <= 32*KS.
 template <typename T, int S, int KS>
-__global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
+__global__ void __launch_bounds__(kRrWarps * 32, 1) rerank_kernel(
     const T* __restrict__ X, const T* __restrict__ Q, const float* __restrict__ Xa,
     const float* __restrict__ Qa, int d, int64_t m, int L, int kq,
     const int32_t* __restrict__ cand, const float* __restrict__ ckey,
@@ -778,16 +792,22 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     const float* __restrict__ qnorm2, const float* __restrict__ qdelta,
     const unsigned int* __restrict__ xstats, const int* __restrict__ err,
     int32_t* __restrict__ idx_out, double* __restrict__ key_out, int* fb_list, int* fb_count) {
-  __shared__ T tiles[kRrWarps][33 * (kRrChunk + 1)];
-  __shared__ int lists[kRrWarps][2][128];
-  __shared__ float ivl[kRrWarps][2][128];  // FP32 interval (lo, hi) per candidate slot
+  constexpr int LCAP = 32 * S;
+  extern __shared__ __align__(16) unsigned char rr_smem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kRrWarps + wid;
   if (w >= m) return;  // warps are independent: no CTA-wide barrier below
-  T* tile = tiles[wid];
+  T* tile = reinterpret_cast<T*>(rr_smem) + (size_t)wid * 33 * (kRrChunk + 1);
+  int* lists0 = reinterpret_cast<int*>(rr_smem + (size_t)kRrWarps * 33 * (kRrChunk + 1) * sizeof(T)) +
+                (size_t)wid * 2 * LCAP;
+  // ivl0[0..LCAP) / ivl0[LCAP..2 LCAP): FP32 interval (lo, hi) per candidate slot
+  float* ivl0 = reinterpret_cast<float*>(
+                    rr_smem + (size_t)kRrWarps * 33 * (kRrChunk + 1) * sizeof(T) +
+                    (size_t)kRrWarps * 2 * LCAP * sizeof(int)) +
+                (size_t)wid * 2 * LCAP;
   T* qrow = tile + 32 * (kRrChunk + 1);
-  int* rowlist = lists[wid][0];
-  int* keep = lists[wid][1];
+  int* rowlist = lists0;
+  int* keep = lists0 + LCAP;
   const T* qr = Q + w * d;
   const float u = 5.9604645e-8f;
   const float gam = (d + 4) * u * 1.1f;
@@ -828,7 +848,7 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     for (int g = 0; g < S; ++g) {
       const bool take = jg[g] != INT_MAX && lo[g] <= Ub;
       const unsigned bal = __ballot_sync(kFull, take);
-      if (take) lists[wid][1][nsurv + __popc(bal & ((1u << lane) - 1u))] = jg[g];
+      if (take) keep[nsurv + __popc(bal & ((1u << lane) - 1u))] = jg[g];
       nsurv += __popc(bal);
     }
     __syncwarp();
@@ -843,7 +863,7 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
       lo[g] = hi[g] = __int_as_float(0x7f800000);
       continue;
     }
-    const int j = a < nsurv ? lists[wid][1][a] : INT_MAX;
+    const int j = a < nsurv ? keep[a] : INT_MAX;
     rowlist[lane] = (j == INT_MAX) ? -1 : j;
     __syncwarp();
     float acc = 0.f;
@@ -867,10 +887,10 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     const float h = sqrtf(acc * (1.0f + gam)) + econv;
     lo[g] = valid ? l * l * (1.0f - 1e-6f) : __int_as_float(0x7f800000);
     hi[g] = valid ? h * h * (1.0f + 1e-6f) : __int_as_float(0x7f800000);
-    if (a < 128) {
-      ivl[wid][0][a] = lo[g];
-      ivl[wid][1][a] = hi[g];
-      lists[wid][1][a] = rowlist[lane];
+    if (a < LCAP) {
+      ivl0[a] = lo[g];
+      ivl0[LCAP + a] = hi[g];
+      keep[a] = rowlist[lane];
     }
     ub.offer(valid ? (unsigned long long)__float_as_uint(hi[g]) : ~0ull, valid ? a : INT_MAX, lane);
     __syncwarp();
@@ -906,7 +926,7 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
         if (pos + 1 < kq) {
           const int a = ord.i[s2];
           const int b = (s2 + 1 < KS) ? ord.i[(s2 + 1 < KS) ? s2 + 1 : s2] : nxt0;
-          if (!(ivl[wid][1][a] < ivl[wid][0][b])) ok = false;
+          if (!(ivl0[LCAP + a] < ivl0[b])) ok = false;
         }
       }
       if (__all_sync(kFull, ok)) {
@@ -914,8 +934,8 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
 #pragma unroll
         for (int s2 = 0; s2 < KS; ++s2) {
           const int pos = lane * KS + s2;
-          if (pos < kq) idx_out[w * kq + pos] = lists[wid][1][ord.i[s2]];
-          if (pos == kq - 1) hk = ivl[wid][1][ord.i[s2]];
+          if (pos < kq) idx_out[w * kq + pos] = keep[ord.i[s2]];
+          if (pos == kq - 1) hk = ivl0[LCAP + ord.i[s2]];
         }
         hk = __shfl_sync(kFull, hk, (kq - 1) / KS);
         // certificate with the kq-th member's upper bound
@@ -961,7 +981,7 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
         }
         base += __popc(bal);
       }
-      rowlist[lane] = my_slot >= 0 ? lists[wid][1][my_slot] : -1;
+      rowlist[lane] = my_slot >= 0 ? keep[my_slot] : -1;
       __syncwarp();
       dfl acc = {0.0f, 0.0f};
       for (int c0 = 0; c0 < d; c0 += kRrChunk) {
@@ -993,7 +1013,7 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
       }
       if (cnt >= kq && __all_sync(kFull, ok2)) {
         const int slot = __shfl_sync(kFull, my_slot, src);
-        if (lane < kq) idx_out[w * kq + lane] = lists[wid][1][slot];
+        if (lane < kq) idx_out[w * kq + lane] = keep[slot];
         float hk = __shfl_sync(kFull, mine.hi + fabsf(mine.lo), kq - 1);
         hk = hk * (1.0f + 1e-6f) + 1e-37f;  // upper bound of the kq-th canonical key
         const float xdel0 = __uint_as_float(xstats[1]);
@@ -1019,7 +1039,7 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
     const int a = 32 * g + lane;
     const bool take = a < L && lo[g] <= U;
     const unsigned bal = __ballot_sync(kFull, take);
-    const int cj = take ? lists[wid][1][a] : 0;
+    const int cj = take ? keep[a] : 0;
     __syncwarp();
     if (take) keep[nkeep + __popc(bal & ((1u << lane) - 1u))] = cj;
     __syncwarp();
@@ -1075,18 +1095,54 @@ __global__ void __launch_bounds__(kRrWarps * 32) rerank_kernel(
   }
 }
 
-template <typename T, int S>
-int launch_rerank(const T* X, const T* Q, const float* Xa, const float* Qa, int d, int64_t m, int L, int kq, const int32_t* cand, const float* ckey, const float* xdl,
-                  const float* dL, const float* qn2, const float* qdl, const unsigned int* xst,
-                  const int* err, int32_t* idx, double* key, int* fbl, int* fbc, cudaStream_t s) {
+template <typename T, int S, int KS>
+int launch_rerank_t(const T* X, const T* Q, const float* Xa, const float* Qa, int d, int64_t m,
+                    int L, int kq, const int32_t* cand, const float* ckey, const float* xdl,
+                    const float* dL, const float* qn2, const float* qdl, const unsigned int* xst,
+                    const int* err, int32_t* idx, double* key, int* fbl, int* fbc,
+                    cudaStream_t s) {
   const int blocks = ceil_div(m, kRrWarps);
-  const int KS = (kq + 31) / 32;
-  if (KS == 1) FMGP_LAUNCH((rerank_kernel<T, S, 1><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else if (KS == 2) FMGP_LAUNCH((rerank_kernel<T, S, 2><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else if (KS == 3) FMGP_LAUNCH((rerank_kernel<T, S, 3><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
-  else FMGP_LAUNCH((rerank_kernel<T, S, 4><<<blocks, kRrWarps * 32, 0, s>>>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
+  constexpr size_t smem = rr_smem_bytes<T>(S);
+  FMGP_CUDA_TRY(ensure_smem((const void*)rerank_kernel<T, S, KS>, smem));
+  FMGP_LAUNCH((rerank_kernel<T, S, KS><<<blocks, kRrWarps * 32, smem, s>>>(
+      X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx, key, fbl, fbc)));
   FMGP_CUDA_TRY(cudaGetLastError());
   return FMGP_OK;
+}
+
+// The instance for L candidates (L <= 32*S) and kq results (kq <= 32*KS).
+// Lists of up to 128 candidates come in every (S, KS); longer ones only for
+// L = round_up(2 kq, 32), i.e. S = 6, 8, 10 with KS = S / 2 (a shorter L or
+// kq rounds up to the next instance).
+template <typename T>
+int launch_rerank(const T* X, const T* Q, const float* Xa, const float* Qa, int d, int64_t m,
+                  int L, int kq, const int32_t* cand, const float* ckey, const float* xdl,
+                  const float* dL, const float* qn2, const float* qdl, const unsigned int* xst,
+                  const int* err, int32_t* idx, double* key, int* fbl, int* fbc,
+                  cudaStream_t s) {
+  const int S = (L + 31) / 32, KS = (kq + 31) / 32;
+#define FMGP_RR(SS, KK)                                                                       \
+  return launch_rerank_t<T, SS, KK>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, \
+                                    xst, err, idx, key, fbl, fbc, s)
+  if (S <= 4) {
+    const int si = S * 4 + KS;
+    switch (si) {
+      case 1 * 4 + 1: FMGP_RR(1, 1);
+      case 2 * 4 + 1: FMGP_RR(2, 1);
+      case 2 * 4 + 2: FMGP_RR(2, 2);
+      case 3 * 4 + 1: FMGP_RR(3, 1);
+      case 3 * 4 + 2: FMGP_RR(3, 2);
+      case 3 * 4 + 3: FMGP_RR(3, 3);
+      case 4 * 4 + 1: FMGP_RR(4, 1);
+      case 4 * 4 + 2: FMGP_RR(4, 2);
+      case 4 * 4 + 3: FMGP_RR(4, 3);
+      default: FMGP_RR(4, 4);
+    }
+  }
+  if (S <= 6 && KS <= 3) FMGP_RR(6, 3);
+  if (S <= 8 && KS <= 4) FMGP_RR(8, 4);
+  FMGP_RR(10, 5);
+#undef FMGP_RR
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1140,19 +1196,32 @@ int pack(const T* X, int64_t rows, int d, int64_t rows_pad, int d_pad, Workspace
   return FMGP_OK;
 }
 
-// Candidates kept per query for the re-rank: the tuned multiple of kq,
-// in whole warps, at least 32 and at most 128.
+// Candidates kept per query for the re-rank, in whole warps: the tuned
+// multiple of kq (at least 32) up to 128, and above that 2 kq (at most 320,
+// i.e. kq <= 160).
 int tc_list_len(int kq) {
-  return std::min(128, (std::max(tune_params().tc_oversample * kq, 32) + 31) / 32 * 32);
+  const int want = std::max(32, std::min(tune_params().tc_oversample * kq, std::max(128, 2 * kq)));
+  return std::min(kMaxTcList, (want + 31) / 32 * 32);
 }
 
 // Per-range list length of the fused selection for kq neighbours (0 = the
 // pass-buffer form); the tc_fused_r tuning key overrides it (R >= kq / 4).
+// Above kq = 32 the lists keep 32 and the candidates are split into more
+// ranges instead (tc_fused_ranges_min).
 int tc_fused_r(int kq) {
   if (!tune_params().tc_fused_select) return 0;
   const int o = tune_params().tc_fused_r;
   if (o && kq <= 32 && (o == 8 || o == 16 || o == 32) && kq <= 4 * o) return o;
-  return kq <= 4 ? 8 : kq <= 16 ? 16 : kq <= 32 ? 32 : 0;
+  return kq <= 4 ? 8 : kq <= 16 ? 16 : 32;
+}
+
+// Fewest candidate ranges per query block for the fused selection: with 2
+// column halves per range, 2 * ranges * R list entries hold at least four
+// times kq, so no half-range is expected to hold more than an eighth of the
+// kq nearest and every range's R-th value lies well beyond the kq-th.
+int tc_fused_ranges_min(int kq, int R) {
+  if (kq <= 32) return R >= 16 ? 4 : 2;
+  return std::max(4, (4 * kq + 2 * R - 1) / (2 * R));
 }
 
 // FP32 rows of X for the re-rank's bounds pass: X itself, or a copy of an
@@ -1218,14 +1287,18 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   if (R > 0) {
     // candidate ranges per query block: the split with the shortest
     // makespan (whole waves of one CTA per SM x tiles per CTA, plus a tile's
-    // worth of start-up), at least 4 ranges for R = 32 and 2 for R = 8 so the
-    // ranges' R-th keys lie well beyond the kq nearest, and at most ~1 GB of
-    // per-range lists
+    // worth of start-up), with at least tc_fused_ranges_min ranges so the
+    // ranges' R-th keys lie well beyond the kq nearest.  Up to kq = 32 the
+    // per-range lists of all queries stay within ~1 GB; above it the ranges
+    // are at most 12 (768 list entries per query) and the query blocks are
+    // processed in chunks whose lists take at most ~1 GB.
     const int sms = num_sms();
-    const int ys_lo = std::min(n_tiles, R >= 16 ? 4 : 2);
+    const int ys_lo = std::min(n_tiles, tc_fused_ranges_min(kq, R));
     const int64_t per_range = 2 * m_pad * R * (int64_t)(sizeof(float) + sizeof(int32_t));
-    const int ys_hi = (int)std::max<int64_t>(
-        ys_lo, std::min<int64_t>(std::min(n_tiles, 128), (1ll << 30) / per_range));
+    const int ys_hi =
+        kq <= 32 ? (int)std::max<int64_t>(
+                       ys_lo, std::min<int64_t>(std::min(n_tiles, 128), (1ll << 30) / per_range))
+                 : std::max(ys_lo, std::min(n_tiles, 12));
     int nseg = ys_lo;
     int64_t best = INT64_MAX;
     for (int ys = ys_lo; ys <= ys_hi; ++ys) {
@@ -1235,34 +1308,52 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
       if (cost < best) { best = cost; nseg = ys; }
     }
     const int tpc = ceil_div(n_tiles, nseg);
-    float* pkey = ws.get<float>((size_t)m_pad * 2 * nseg * R);
-    int32_t* pidx = ws.get<int32_t>((size_t)m_pad * 2 * nseg * R);
+    const int64_t lists_per_qb = (int64_t)kTM * 2 * nseg * R;  // entries per query block
+    const int64_t cq = tune_params().tc_chunk_queries;
+    const int64_t chunk_qb = std::max<int64_t>(
+        1, std::min<int64_t>(qblocks, cq > 0 ? cq / kTM : (1ll << 30) / (lists_per_qb * 8)));
+    float* pkey = ws.get<float>((size_t)(chunk_qb * lists_per_qb));
+    int32_t* pidx = ws.get<int32_t>((size_t)(chunk_qb * lists_per_qb));
     if (!pkey || !pidx) return FMGP_ENOMEM;
-    if (R == 8) {
-      FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<8>, kTcSelSmem));
-      FMGP_LAUNCH(tc_dist_kernel<8><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcSelThreads, kTcSelSmem, s>>>(
-          tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
-    } else if (R == 16) {
-      FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<16>, kTcSelSmem));
-      FMGP_LAUNCH(tc_dist_kernel<16><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcSelThreads, kTcSelSmem, s>>>(
-          tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
-    } else {
-      FMGP_CUDA_TRY(ensure_smem((const void*)tc_dist_kernel<32>, kTcSelSmem));
-      FMGP_LAUNCH(tc_dist_kernel<32><<<dim3((unsigned)qblocks, (unsigned)nseg), kTcSelThreads, kTcSelSmem, s>>>(
-          tmQ, tmX, qn2, xn2, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0, pkey, pidx, err));
-    }
+    const void* kfn = R == 8 ? (const void*)tc_dist_kernel<8>
+                    : R == 16 ? (const void*)tc_dist_kernel<16> : (const void*)tc_dist_kernel<32>;
+    FMGP_CUDA_TRY(ensure_smem(kfn, kTcSelSmem));
     const int tot = 2 * nseg * R;
-    if (tot <= 128)
-      FMGP_LAUNCH(select_parts_bisect_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL));
-    else if (tot <= 256)
-      FMGP_LAUNCH(select_parts_bisect_kernel<8><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL));
-    else if (tot <= 512)
-      FMGP_LAUNCH(select_parts_bisect_kernel<16><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL));
-    else switch (S) {
-      case 1: FMGP_LAUNCH(select_parts_kernel<1><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
-      case 2: FMGP_LAUNCH(select_parts_kernel<2><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
-      case 3: FMGP_LAUNCH(select_parts_kernel<3><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
-      default: FMGP_LAUNCH(select_parts_kernel<4><<<sblocks, 256, 0, s>>>(pkey, pidx, m, 2 * nseg, R, L, cand, ckey, dL)); break;
+    for (int64_t qb0 = 0; qb0 < qblocks; qb0 += chunk_qb) {
+      const int64_t nqb = std::min(chunk_qb, qblocks - qb0);
+      const int64_t q0 = qb0 * kTM;
+      const int64_t mc = std::min<int64_t>(m, (qb0 + nqb) * kTM) - q0;  // queries of the chunk
+      const dim3 grid((unsigned)nqb, (unsigned)nseg);
+      if (R == 8)
+        FMGP_LAUNCH(tc_dist_kernel<8><<<grid, kTcSelThreads, kTcSelSmem, s>>>(
+            tmQ, tmX, qn2, xn2, (int)qb0, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0,
+            pkey, pidx, err));
+      else if (R == 16)
+        FMGP_LAUNCH(tc_dist_kernel<16><<<grid, kTcSelThreads, kTcSelSmem, s>>>(
+            tmQ, tmX, qn2, xn2, (int)qb0, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0,
+            pkey, pidx, err));
+      else
+        FMGP_LAUNCH(tc_dist_kernel<32><<<grid, kTcSelThreads, kTcSelSmem, s>>>(
+            tmQ, tmX, qn2, xn2, (int)qb0, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0,
+            pkey, pidx, err));
+      const int cblocks = (int)ceil_div(mc * 32, 256);
+      int32_t* cc = cand + q0 * L;
+      float* ck = ckey + q0 * L;
+      float* cd = dL + q0;
+      if (tot <= 128)
+        FMGP_LAUNCH(select_parts_bisect_kernel<4><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd));
+      else if (tot <= 256)
+        FMGP_LAUNCH(select_parts_bisect_kernel<8><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd));
+      else if (tot <= 512)
+        FMGP_LAUNCH(select_parts_bisect_kernel<16><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd));
+      else if (tot <= 768)
+        FMGP_LAUNCH(select_parts_bisect_kernel<24><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd));
+      else switch (S) {  // kq <= 32 here: L <= 128
+        case 1: FMGP_LAUNCH(select_parts_kernel<1><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd)); break;
+        case 2: FMGP_LAUNCH(select_parts_kernel<2><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd)); break;
+        case 3: FMGP_LAUNCH(select_parts_kernel<3><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd)); break;
+        default: FMGP_LAUNCH(select_parts_kernel<4><<<cblocks, 256, 0, s>>>(pkey, pidx, mc, 2 * nseg, R, L, cc, ck, cd)); break;
+      }
     }
   } else {
     // candidate range in chunks of whole tiles; the chunk buffer holds ~1 GB
@@ -1280,14 +1371,17 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     for (int t0 = 0; t0 < n_tiles; t0 += chunk_tiles) {
       const int t1 = std::min(n_tiles, t0 + chunk_tiles);
       FMGP_LAUNCH(tc_dist_kernel<0><<<dim3((unsigned)qblocks, (unsigned)ysplit), kTcThreads, kTcSmem, s>>>(
-          tmQ, tmX, qn2, xn2, t0, t1, tpc, k_chunks, ldc, Dc, n, 0, nullptr, nullptr, err));
+          tmQ, tmX, qn2, xn2, 0, t0, t1, tpc, k_chunks, ldc, Dc, n, 0, nullptr, nullptr, err));
       const int64_t col0 = (int64_t)t0 * kTN, ncols = (int64_t)(t1 - t0) * kTN;
       const int first = t0 == 0 ? 1 : 0;
-      switch (S) {
+      switch (S <= 4 ? S : S <= 6 ? 6 : S <= 8 ? 8 : 10) {  // list slots per lane >= L / 32
         case 1: FMGP_LAUNCH(select_merge_kernel<1><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
         case 2: FMGP_LAUNCH(select_merge_kernel<2><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
         case 3: FMGP_LAUNCH(select_merge_kernel<3><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
-        default: FMGP_LAUNCH(select_merge_kernel<4><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+        case 4: FMGP_LAUNCH(select_merge_kernel<4><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+        case 6: FMGP_LAUNCH(select_merge_kernel<6><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+        case 8: FMGP_LAUNCH(select_merge_kernel<8><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
+        default: FMGP_LAUNCH(select_merge_kernel<10><<<sblocks, 256, 0, s>>>(Dc, ldc, m, col0, ncols, n, L, self, first, cand, ckey, dL)); break;
       }
     }
   }
@@ -1299,12 +1393,8 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   else if ((rc = f32_rows<T>(X, n, d, ws, s, &Xa))) return rc;
   if (self) Qa = Xa;
   else if ((rc = f32_rows<T>(Q, m, d, ws, s, &Qa))) return rc;
-  switch (S) {
-    case 1: rc = launch_rerank<T, 1>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    case 2: rc = launch_rerank<T, 2>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    case 3: rc = launch_rerank<T, 3>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-    default: rc = launch_rerank<T, 4>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err, idx_out, key_out, fb_list, fb_count, s); break;
-  }
+  rc = launch_rerank<T>(X, Q, Xa, Qa, d, m, L, kq, cand, ckey, xdl, dL, qn2, qdl, xst, err,
+                        idx_out, key_out, fb_list, fb_count, s);
   if (rc) return rc;
   FMGP_CUDA_TRY(cudaGetLastError());
   diag_record_tc(fb_count, s);
@@ -1319,7 +1409,7 @@ bool tc_knn_eligible(int64_t n, int d, int64_t m, int kq) {
   const TuneParams& tp = tune_params();
   if (!tp.use_tensor_cores) return false;
   const int L = tc_list_len(kq);
-  return d >= 16 && kq <= 96 && n > 2 * L && n >= 4096 && m >= 128;
+  return d >= 16 && kq <= kMaxK && n > 2 * L && n >= 4096 && m >= 128;
 }
 
 int tc_pack_train(const void* X, fmgp_dtype dtype, int64_t n, int d, Workspace& ws,

@@ -186,3 +186,69 @@ def test_bf16_useless_data_still_exact(cuda, fused):
     ref_i, ref_k = oracle.knn(X, X[rows], 6, rows)
     np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
     np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("kind,n,d,kq", [("u64", 9000, 16, 127), ("u32", 9000, 16, 159),
+                                         ("u32", 8500, 64, 127), ("u64", 8003, 64, 159),
+                                         ("u32", 6000, 40, 97)])
+def test_tensor_core_knn_large_kq(cuda, kind, n, d, kq, fused):
+    """Neighbour counts above 96 (the k - 1 = 127 table of a k = 128 model, and
+    the largest, 159): fused selection with 32-entry lists over at least
+    kq / 8 candidate ranges, or the pass buffer; re-rank lists of 2 kq.  The
+    table equals the oracle's bit for bit and most queries are certified."""
+    X = _data(kind, n, d, n + d + kq)
+    c0 = fb.diag_counter(1)
+    with _Fused(fused):
+        nbr, dist = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
+        torch.cuda.synchronize()
+        fallbacks = fb.diag_counter(2)
+    assert fb.diag_counter(1) == c0 + 1, "tensor-core path not taken"
+    assert 0 <= fallbacks <= 0.2 * n, fallbacks
+    rows = np.random.default_rng(2).choice(n, 200, replace=False)
+    ref_i, ref_k = oracle.knn(X.astype(np.float64), X.astype(np.float64)[rows], kq, rows)
+    np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
+    np.testing.assert_array_equal(dist.cpu().numpy()[rows], ref_k)
+    fb.tune_set("tensor_cores", 0)
+    try:
+        nbr2, dist2 = fb.fmgp_build_knn(dev(X), kq, with_dist=True)
+    finally:
+        fb.tune_set("tensor_cores", 1)
+    assert torch.equal(nbr, nbr2) and torch.equal(dist, dist2)
+
+
+@pytest.mark.parametrize("kq", [31, 127])
+def test_fused_selection_in_query_chunks(cuda, kq):
+    """The fused selection processed in passes over blocks of queries (here
+    3 blocks of 128 per pass, the last pass ragged) gives the same table as
+    one pass, for self kNN and for external queries."""
+    rng = np.random.default_rng(kq)
+    n, m, d = 7000, 1000, 32
+    X = rng.random((n, d))
+    Z = rng.random((m, d))
+    prev = fb.tune_get("tc_chunk_queries")
+    try:
+        fb.tune_set("tc_chunk_queries", 0)
+        one, _ = fb.fmgp_build_knn(dev(X), kq)
+        fb.tune_set("tc_chunk_queries", 384)
+        c0 = fb.diag_counter(1)
+        chunked, _ = fb.fmgp_build_knn(dev(X), kq)
+        torch.cuda.synchronize()
+        assert fb.diag_counter(1) == c0 + 1
+    finally:
+        fb.tune_set("tc_chunk_queries", prev)
+    assert torch.equal(one, chunked)
+    rows = np.arange(0, n, 53)
+    ref_i, _ = oracle.knn(X, X[rows], kq, rows)
+    np.testing.assert_array_equal(chunked.cpu().numpy()[rows], ref_i)
+    # plain MuyGPs neighbours of external queries: the same search with self = false
+    Y = dev(np.sin(X[:, :1] * 3.0))
+    kern = fb.make_kernel("rbf", 0.0, 1.5, 1.0, 1e-2)
+    k = kq + 1 if kq < 160 else kq
+    try:
+        fb.tune_set("tc_chunk_queries", 384)
+        _, nb_q = fb.fmgp_muygps_predict(dev(X), Y, dev(Z), k, kern, fb.PREC_FP64, with_nbr=True)
+    finally:
+        fb.tune_set("tc_chunk_queries", prev)
+    ref_q, _ = oracle.knn(X, Z, k)
+    np.testing.assert_array_equal(nb_q.cpu().numpy(), ref_q)
