@@ -119,6 +119,8 @@ void note_launch();
   } while (0)
 
 void set_error(const char* fmt, ...);
+// Empty this thread's error message (every entry point starts with it).
+void clear_error();
 int cuda_fail(cudaError_t e, const char* what);
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes`, calling

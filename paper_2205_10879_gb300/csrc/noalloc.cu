@@ -8,6 +8,7 @@
 // stream-ordered workspace the other entry points use.
 #include <mutex>
 #include "block.cuh"
+#include "knn.cuh"
 
 namespace fmgp {
 namespace {
@@ -84,6 +85,7 @@ extern "C" int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, con
                                             const int64_t* batch, int64_t b,
                                             const fmgp_kernel* kernel, fmgp_precision precision,
                                             double* Q_out, double* resid_out, void* stream) {
+  clear_error();
   if (dtype != FMGP_F32 && dtype != FMGP_F64) {
     set_error("dtype %d unknown", (int)dtype);
     return FMGP_EINVAL;
@@ -134,8 +136,10 @@ extern "C" int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, con
               a.layout.bytes_per_warp);
     return FMGP_EUNSUPPORTED;
   }
-  int warps = (int)((200 * 1024) / a.layout.bytes_per_warp);
-  if (warps > 8) warps = 8;
+  // the launch shape of fmgp_loocv_objective: the user's or the autotuner's
+  // warps per CTA, else (0) the occupancy-best one (the search allocates nothing)
+  int warps = tune_params().block_warps;
+  if (warps == 0) warps = tuned_block_warps((int)FMGP_PREC_FP64, k, d, r, (int)dtype);
   rc = launch_block_f64(a, X, dtype, kModeLoocv, warps, s);
   if (rc) return rc;
   FMGP_LAUNCH(noalloc_reduce<<<1, 1024, 0, s>>>(a.resid, b, &sc->q));
