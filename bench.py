@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--k", type=int, default=50)
     p.add_argument("--b", type=int, default=10_000)
     p.add_argument("--nu", type=float, default=1.5)
-    p.add_argument("--workload", default="spatial", choices=["spatial", "large", "highdim-knn", "nearest-d64"])
+    p.add_argument("--workload", default="spatial", choices=["spatial", "large", "highdim", "highdim-knn", "nearest-d64"])
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-muygps", action="store_true")
     p.add_argument("--no-highdim", action="store_true")
@@ -128,6 +128,44 @@ def ncu_evidence(kernel):
         except OSError:
             return None
     return ev
+
+
+# ----------------------------------------------------------------- peaks --
+def measured_peaks():
+    """The machine's measured HBM copy bandwidth and cuBLAS BF16 rates
+    (MEASURED_PEAKS.json beside this file), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def bf16_peak():
+    """Dense BF16 tensor peak in TFLOP/s for a kernel timed alone: the measured
+    burst figure, else 1900 (an earlier GB300 measurement)."""
+    p = measured_peaks()
+    return float(p["bf16_tflops"]) if p and p.get("bf16_tflops") else 1900.0
+
+
+def bf16_peak_source():
+    p = measured_peaks()
+    return "measured (bf16_tflops, burst)" if p and p.get("bf16_tflops") else "fallback"
+
+
+def alu_peak(fb, dev, pipe, sm_mhz=None):
+    """FMA-pipe peak in TFLOP/s measured in this run by the library's probe
+    kernel (fmgp_peak_probe), with the unit-count figure at the sampled clock
+    beside it."""
+    import torch
+    v = fb.peak_probe(pipe) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    per_clk = 256 if pipe == "fp32" else 4  # flops per SM per clock: 128 FFMA / 2 DFMA
+    mhz = sm_mhz or 2070.0
+    return v, {"peak_source": f"measured in this run: fmgp_peak_probe ({pipe} FMA, best of 3 "
+                              f"launches of ~30 ms)",
+               "peak_unit_count": sms * per_clk * mhz * 1e6 / 1e12,
+               "peak_unit_count_note": f"{sms} SMs x {per_clk // 2} FMA/clk x 2 x {mhz:.0f} MHz"}
 
 
 # ----------------------------------------------------------------- flops --
@@ -323,18 +361,17 @@ def run_ours(a):
     fl = precompute_flops_per_point(k, W.d, 1) * n
     pre_s = phase_ms[1] * 1e-3
     if prec == fb.PREC_FP64:
-        peak = 152 * 4 * 2070e6 / 1e12  # FP64: 2 DFMA/clk/SM
         roof = {"bound": "alu", "pipe": "fp64", "kernel": "block_f64_kernel"}
     else:
-        peak = 152 * 256 * 2070e6 / 1e12  # FP32: 128 FFMA/clk/SM
         roof = {"bound": "alu", "pipe": "fp32", "kernel": "block_mixed_kernel"}
+    peak, psrc = alu_peak(fb, dev, roof["pipe"], clocks["sm_mhz"] if clocks else None)
     achieved = fl / pre_s / 1e12
     ev = ncu_evidence(roof["kernel"]) if a.workload == "spatial" else None
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "traffic": ev["traffic"] if ev else None, "flops_per_launch": fl,
-                 "peak_source": "derived: 152 SMs x pipe FMA/clk x 2 x 2070 MHz",
                  "ncu": ({k: ev[k] for k in ("issue_active_pct", "fma_pipe_pct", "alu_pipe_pct",
                                               "profile")} if ev else None)})
+    roof.update(psrc)
     # e2e: same step from pinned host buffers, copies inside the timed region
     e2e = None
     if not a.no_e2e:
@@ -406,7 +443,7 @@ def run_ours(a):
         "gpu_launches": launches, "clocks": clocks,
     }
     if not a.no_highdim:
-        line["highdim_knn"] = highdim_knn_bench(a, dev, steps=a.steps, warmup=1)
+        line["highdim"] = highdim_bench(a, dev)
     if not a.no_training and a.workload == "spatial":
         line["training"] = training_bench(X, Y, batch, k, nbr, gk, prec)
     if not a.no_graph and a.workload == "spatial":
@@ -458,13 +495,91 @@ def highdim_knn_bench(a, dev, steps, warmup):
     n_pad = (W.n + 255) // 256 * 256
     d_pad = (W.d + 63) // 64 * 64
     flops = 2.0 * n_pad * n_pad * d_pad
-    peak = 1948.7
+    peak = bf16_peak()
     ach = flops / (ms * 1e-3) / 1e12
     return {"workload": "highdim-784 self kNN", "n": W.n, "d": W.d, "kq": 29, "ms": ms,
             "knn_queries_per_s": W.n / (ms * 1e-3), "tensor_core_calls": fb.diag_counter(1) - c0,
             "uncertified_queries": fb.diag_counter(2),
             "roofline_call": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                               "frac": ach / peak, "note": "whole call incl. pack/select/re-rank"}}
+
+
+def highdim_bench(a, dev, steps=2):
+    """The high-dimensional multi-response configuration end to end (the
+    stand-in for the 400-D star-galaxy images of Sec. 4.3): n = 60,000
+    training and m = 10,000 test points, d = 784 FP32 features with 80% exact
+    zeros, r = 10 centred one-hot responses, RBF rho = 7, tau^2 = 1e-2,
+    k = 30, LOOCV batch of 5,000.  Per precision: kNN table (tensor cores,
+    kq = 30), precompute, prediction (nearest point + gather-dot) and LOOCV,
+    each timed with CUDA events; RMSE against the held-out centred one-hot
+    responses, classification accuracy (argmax of the predicted responses
+    plus the column means, as Table 2 reports), and the mixed form's
+    difference from the FP64 form."""
+    import torch
+    from paper_2205_10879_gb300 import _binding as fb
+    from paper_2205_10879_gb300 import workloads as wl
+    W = wl.highdim()
+    s = W.kernel
+    gk = fb.make_kernel(s.kind, s.nu, s.length_scale, s.variance, s.nugget)
+    X, Y, Z = (torch.from_numpy(v).to(dev) for v in (W.X, W.Y, W.Z))
+    batch = torch.from_numpy(W.batch).to(dev)
+    k = kq = W.k
+    mu = W.extra["col_mean"]
+    labels = W.extra["labels_test"]
+    nbr = torch.empty((W.n, kq), dtype=torch.int32, device=dev)
+    yh = torch.empty((W.m, W.r), dtype=torch.float64, device=dev)
+    near = torch.empty(W.m, dtype=torch.int32, device=dev)
+    resid = torch.empty(len(W.batch), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "highdim-784: n=60000 m=10000 d=784 (80% zeros, FP32) r=10 rbf rho=7 "
+                       "tau2=1e-2 k=30", "n": W.n, "m": W.m, "d": W.d, "r": W.r, "k": k,
+           "loocv_batch": len(W.batch)}
+    preds = {}
+    for name, prec in (("mixed", fb.PREC_MIXED), ("fp64", fb.PREC_FP64)):
+        C = torch.empty(fb.coeff_shape(W.n, k, W.r, prec),
+                        dtype=torch.float64 if prec == fb.PREC_FP64 else torch.float32, device=dev)
+        st = torch.empty(W.n, dtype=torch.int8, device=dev)
+
+        def step(ev=None):
+            if ev: ev[0].record(stream)
+            fb.fmgp_build_knn(X, kq, nbr_out=nbr)
+            if ev: ev[1].record(stream)
+            fb.fmgp_precompute(X, Y, nbr, k, gk, prec, C_out=C, status_out=st)
+            if ev: ev[2].record(stream)
+            fb.fmgp_predict(X, nbr, C, k, gk, Z, prec, Yhat_out=yh, nearest_out=near)
+            if ev: ev[3].record(stream)
+            Q, _ = fb.fmgp_loocv_objective(X, Y, nbr, k, batch, gk, prec, resid_out=resid)
+            if ev: ev[4].record(stream)
+            return Q
+        step()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        for i in range(steps):
+            Q = step(evs[i])
+        torch.cuda.synchronize()
+        ph = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)]
+                       for i in range(steps)]).mean(axis=0)
+        y = yh.cpu().numpy().copy()
+        preds[name] = y
+        stv = st.cpu().numpy()
+        out[name] = {"phases_ms": {"knn": ph[0], "precompute": ph[1], "predict": ph[2],
+                                   "loocv": ph[3]},
+                     "ms_per_step": float(ph.sum()),
+                     "knn_queries_per_s": W.n / (ph[0] * 1e-3),
+                     "precompute_pts_per_s": W.n / (ph[1] * 1e-3),
+                     "predictions_per_s": W.m / (ph[2] * 1e-3),
+                     "loocv_pts_per_s": len(W.batch) / (ph[3] * 1e-3),
+                     "rmse": float(np.sqrt(np.mean((y - W.Ztrue) ** 2))),
+                     "accuracy": float(np.mean(np.argmax(y + mu, axis=1) == labels)),
+                     "loocv_q": Q,
+                     "block_status": {str(v): int(c) for v, c in zip(*np.unique(stv, return_counts=True))}}
+        del C, st
+    r64 = out["fp64"]["rmse"]
+    out["mixed_rel_rms_vs_fp64"] = float(np.linalg.norm(preds["mixed"] - preds["fp64"]) /
+                                         np.linalg.norm(preds["fp64"]))
+    out["equal_rmse"] = bool(abs(out["mixed"]["rmse"] - r64) <= 1e-3 * r64)
+    out["knn"] = highdim_knn_bench(a, dev, steps=max(2, steps), warmup=1)
+    return out
 
 
 def nearest_bench(a, dev, steps, warmup):
@@ -501,7 +616,7 @@ def nearest_bench(a, dev, steps, warmup):
         ts.append(e0.elapsed_time(e1))
     ms = float(np.mean(ts))
     flops = 2.0 * ((m + 127) // 128 * 128) * ((n + 255) // 256 * 256) * 64
-    peak = 1948.7
+    peak = bf16_peak()
     ach = flops / (ms * 1e-3) / 1e12
     return {"workload": "nearest-d64: nearest of 65,536 queries among 200,000 points, d = 64",
             "n": n, "m": m, "d": d, "k": k, "ms": ms, "predictions_per_s": m / (ms * 1e-3),
@@ -682,22 +797,28 @@ def borehole_bench(a, dev):
 
 # ------------------------------------------------------------- serving ----
 def serving_bench(a, dev):
-    """Eight resident models (n log-uniform in [1e4, 2e6], d in {2,3,16,64},
-    k in {16,32,64,128}, Matern/RBF, mixed precision; n capped at 200,000 for
-    d >= 16, whose kNN table is built by exhaustive scan), one continuous-
-    batching server (4 streams), Poisson request streams of log-uniform 1..65,536
+    """Eight resident models at their full sizes (n log-uniform in [1e4, 2e6],
+    d in {2,3,16,64}, k in {16,32,64,128}, Matern/RBF, mixed precision; the
+    d >= 16 tables from the tensor-core search), one continuous-batching
+    server (4 streams), Poisson request streams of log-uniform 1..65,536
     points at 25%, 50%, 75% and 90% of the measured saturation rate: p50/p99
-    latency (submission to results in host memory) and predictions/s."""
+    latency (submission to results in host memory) and predictions/s.  Each
+    model's fit (kNN table, precompute, resident model) is timed."""
     from paper_2205_10879_gb300 import _binding as fb
     from paper_2205_10879_gb300 import serving, workloads as wl
     specs = wl.serving_models()
-    models = []
+    models, fits = [], []
     t0 = time.perf_counter()
     for s in specs:
-        X, Y = s["X"], s["Y"]
-        if X.shape[1] >= 16 and X.shape[0] > 200_000:
-            X, Y = X[:200_000], Y[:200_000]
-        models.append(serving.fit_model(X, Y, s["k"], s["kernel"], fb.PREC_MIXED))
+        tm = {}
+        c0 = fb.diag_counter(1)
+        models.append(serving.fit_model(s["X"], s["Y"], s["k"], s["kernel"], fb.PREC_MIXED,
+                                        timings=tm))
+        tm.update(n=int(s["X"].shape[0]), d=int(s["X"].shape[1]), k=int(s["k"]),
+                  tensor_core_knn=bool(fb.diag_counter(1) > c0))
+        if tm["tensor_core_knn"]:
+            tm["uncertified_queries"] = fb.diag_counter(2)
+        fits.append(tm)
     fit_s = time.perf_counter() - t0
     srv = fb.FmgpServer(models, device_budget_bytes=4 << 30, host_staging_bytes=2 << 30,
                         streams=4)
@@ -705,8 +826,7 @@ def serving_bench(a, dev):
     lat, pts, wall = serving.run_poisson(srv, models, 0.0, max(40, a.serving_requests // 4), 11)
     sat = serving.latency_summary(lat, pts, wall)
     req_rate = sat["requests"] / sat["wall_s"]
-    out = {"models": [{"n": int(m.n), "d": int(m.d), "k": int(m.k)} for m in models],
-           "fit_seconds": fit_s, "saturation": sat}
+    out = {"models": fits, "fit_seconds": fit_s, "saturation": sat}
     for frac in (0.25, 0.5, 0.75, 0.9):
         lat, pts, wall = serving.run_poisson(srv, models, frac * req_rate, a.serving_requests,
                                              12 + int(frac * 100))
@@ -843,10 +963,49 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def _free_port():
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    return port
+
+
+def relaunch_replicas(a):
+    """--gpus N > 1 outside torchrun: run this same command as N ranks (one per
+    GPU; RANK, LOCAL_RANK, WORLD_SIZE and a rendezvous on 127.0.0.1 in the
+    environment, as torchrun sets them) and return the first non-zero exit
+    status; inside torchrun check that the world size is the one asked for."""
+    ws = os.environ.get("WORLD_SIZE")
+    if a.gpus > 1 and ws is None:
+        port = str(_free_port())
+        procs = []
+        for r in range(a.gpus):
+            env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(a.gpus),
+                       LOCAL_WORLD_SIZE=str(a.gpus), MASTER_ADDR="127.0.0.1", MASTER_PORT=port)
+            procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__)] + sys.argv[1:],
+                                          env=env))
+        rcs = [p.wait() for p in procs]
+        return next((rc for rc in rcs if rc != 0), 0)
+    if ws is not None and int(ws) != a.gpus and a.gpus != 1:
+        sys.stderr.write(f"bench.py: --gpus {a.gpus} but WORLD_SIZE={ws}\n")
+        return 2
+    return None
+
+
 def main():
     a = parse()
+    rc = relaunch_replicas(a)
+    if rc is not None:
+        sys.exit(rc)
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "highdim":
+        import torch
+        from paper_2205_10879_gb300 import _binding as fb
+        fb.load()
+        print(json.dumps(highdim_bench(a, torch.device("cuda", 0), max(2, a.steps))))
     elif a.workload == "highdim-knn":
         import torch
         from paper_2205_10879_gb300 import _binding as fb

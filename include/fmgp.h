@@ -401,6 +401,18 @@ int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, const double* 
                                  const fmgp_kernel* kernel, fmgp_precision precision,
                                  double* Q_out, double* resid_out, void* stream);
 
+/*
+ * fmgp_peak_probe -- measured throughput of an arithmetic pipe on the current
+ * device, the denominator of the roofline fractions of the neighbourhood
+ * kernels (the paper has no counterpart: measurement support).
+ * pipe 0 = FP32 fused multiply-add, 1 = FP64 fused multiply-add.  Every SM
+ * runs 2048 threads of 8 independent FMA chains for about 30 ms per launch;
+ * *flops_per_s receives the best of three timed launches after one warm-up
+ * (2 flops per FMA), timed with CUDA events on `stream`.  Synchronises
+ * `stream`.  Returns FMGP_OK, FMGP_EINVAL or FMGP_ECUDA.
+ */
+int fmgp_peak_probe(int32_t pipe, double* flops_per_s, void* stream);
+
 /* Thread-local description of the most recent error on this thread ("" if none). */
 const char* fmgp_last_error(void);
 

@@ -82,6 +82,8 @@ def load(build_if_missing=True):
         getattr(lib, f).restype = I32
     lib.fmgp_last_error.restype = ctypes.c_char_p
     lib.fmgp_version.restype = ctypes.c_char_p
+    lib.fmgp_peak_probe.argtypes = [I32, ctypes.POINTER(ctypes.c_double), P]
+    lib.fmgp_peak_probe.restype = I32
     lib.fmgp_kernel_launches.restype = ctypes.c_uint64
     lib.fmgp_muygps_predict.argtypes = [P, I32, P, I64, I32, I32, P, I64, I32, KP, I32, P, P, P]
     lib.fmgp_muygps_predict.restype = I32
@@ -246,6 +248,15 @@ def fmgp_predict_rows(X, nbr, rows, C, k, kernel, Z, precision=PREC_FP64, Yhat_o
                                     ctypes.byref(kernel), int(precision), _ptr(Z), m,
                                     _ptr(Yhat_out), _ptr(nearest_out), _stream(stream)))
     return Yhat_out, nearest_out
+
+
+def peak_probe(pipe, stream=None):
+    """Measured FMA throughput of the current device in flop/s: pipe "fp32"
+    or "fp64" (fmgp_peak_probe; synchronises the stream)."""
+    code = {"fp32": 0, "fp64": 1}[pipe]
+    v = ctypes.c_double(0.0)
+    _check(load().fmgp_peak_probe(code, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def fmgp_muygps_predict(X, Y, Z, k, kernel, precision=PREC_FP64, Yhat_out=None, nbr_out=None,

@@ -10,15 +10,27 @@ import torch
 from . import _binding as fb
 
 
-def fit_model(X, Y, k, kernel_spec, precision, device="cuda"):
-    """kNN table + precompute + resident model for one training set."""
+def fit_model(X, Y, k, kernel_spec, precision, device="cuda", timings=None):
+    """kNN table + precompute + resident model for one training set.  With a
+    dict `timings`, the kNN table, precompute and model creation times (ms,
+    CUDA events on the current stream) are stored in it."""
     s = kernel_spec
     gk = fb.make_kernel(s.kind, s.nu, s.length_scale, s.variance, s.nugget)
     Xd = torch.from_numpy(np.ascontiguousarray(X)).to(device)
     Yd = torch.from_numpy(np.ascontiguousarray(Y)).to(device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
     nbr, _ = fb.fmgp_build_knn(Xd, max(k - 1, 1))
+    ev[1].record()
     C, _ = fb.fmgp_precompute(Xd, Yd, nbr, k, gk, precision, with_status=False)
-    return fb.FmgpModel(Xd, nbr, C, k, gk, precision)
+    ev[2].record()
+    model = fb.FmgpModel(Xd, nbr, C, k, gk, precision)
+    ev[3].record()
+    if timings is not None:
+        torch.cuda.synchronize()
+        timings.update(knn_ms=ev[0].elapsed_time(ev[1]), precompute_ms=ev[1].elapsed_time(ev[2]),
+                       model_ms=ev[2].elapsed_time(ev[3]))
+    return model
 
 
 def run_poisson(server, models, rate_hz, count, seed, max_points=65_536):

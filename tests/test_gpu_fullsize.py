@@ -86,6 +86,17 @@ def test_large_full_size(cuda):
     _check(wl.large(), fb.PREC_MIXED, 64, 150, np.random.default_rng(22))
 
 
+@pytest.mark.parametrize("prec", [fb.PREC_FP64, fb.PREC_MIXED])
+def test_highdim_full_size(cuda, prec):
+    """The 784-D multi-response workload at its bench size: n = 60,000
+    training and m = 10,000 test points (FP32 features, 80% exact zeros),
+    r = 10 centred one-hot responses, RBF rho = 7, tau^2 = 1e-2, k = 30; the
+    kNN table (kq = 30) from the tensor-core search."""
+    c0 = fb.diag_counter(1)
+    _check(wl.highdim(), prec, 30, 300, np.random.default_rng(24))
+    assert fb.diag_counter(1) >= c0 + 2  # self table and nearest points on tensor cores
+
+
 def _oracle_rows(Xd, Y, nb, k, ok, rows):
     """The oracle's rows of C for the given training points (n x k x r array,
     zero elsewhere)."""
