@@ -413,6 +413,17 @@ int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, const double* 
  */
 int fmgp_peak_probe(int32_t pipe, double* flops_per_s, void* stream);
 
+/*
+ * fmgp_df_eval -- diagnostic: evaluate one of the double-float primitives of
+ * the mixed-precision path on the device, for testing them against FP64 (the
+ * paper has no counterpart).  Each x[i] (FP64, device) is split into a pair
+ * of FP32 numbers (hi = round(x), lo = round(x - hi)), the primitive is applied
+ * and y[i] (FP64, device) = hi + lo of the result.
+ *   fn 0: exp(-x) for x >= 0 (0 for x >= 88 or NaN); fn 1: sqrt(x) (0 for x <= 0).
+ * Asynchronous on `stream`.  Returns FMGP_OK, FMGP_EINVAL or FMGP_ECUDA.
+ */
+int fmgp_df_eval(int32_t fn, const double* x, int64_t n, double* y, void* stream);
+
 /* Thread-local description of the most recent error on this thread ("" if none). */
 const char* fmgp_last_error(void);
 

@@ -83,6 +83,8 @@ def load(build_if_missing=True):
     lib.fmgp_last_error.restype = ctypes.c_char_p
     lib.fmgp_version.restype = ctypes.c_char_p
     lib.fmgp_peak_probe.argtypes = [I32, ctypes.POINTER(ctypes.c_double), P]
+    lib.fmgp_df_eval.argtypes = [I32, P, I64, P, P]
+    lib.fmgp_df_eval.restype = I32
     lib.fmgp_peak_probe.restype = I32
     lib.fmgp_kernel_launches.restype = ctypes.c_uint64
     lib.fmgp_muygps_predict.argtypes = [P, I32, P, I64, I32, I32, P, I64, I32, KP, I32, P, P, P]
@@ -248,6 +250,16 @@ def fmgp_predict_rows(X, nbr, rows, C, k, kernel, Z, precision=PREC_FP64, Yhat_o
                                     ctypes.byref(kernel), int(precision), _ptr(Z), m,
                                     _ptr(Yhat_out), _ptr(nearest_out), _stream(stream)))
     return Yhat_out, nearest_out
+
+
+def df_eval(fn, x, stream=None):
+    """Diagnostic: the mixed path's double-float exp(-x) (fn "exp_neg") or
+    sqrt(x) (fn "sqrt") of a float64 device tensor, as float64."""
+    _dev(x, "x")
+    y = torch.empty_like(x)
+    _check(load().fmgp_df_eval({"exp_neg": 0, "sqrt": 1}[fn], _ptr(x), x.numel(), _ptr(y),
+                               _stream(stream)))
+    return y
 
 
 def peak_probe(pipe, stream=None):

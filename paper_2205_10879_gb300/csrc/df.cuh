@@ -105,51 +105,48 @@ __device__ __forceinline__ dfl df_sqrt(dfl x) {
   return {pos ? r.hi : 0.0f, pos ? r.lo : 0.0f};
 }
 
-// Constants of the DF exponential, filled on the host from FP64 values:
-// ln 2 = ln2_1 + ln2_2 + ln2_3 (Cody & Waite 1980; ln2_1 has 14 significant
-// bits so n * ln2_1 is exact for |n| < 2^10) and E[j + 24] = exp(-j/64) for
-// j = -24..24 as DF pairs.
+// Tables of the DF exponential, filled on the host from FP64 values (each
+// entry the DF rounding of the FP64 exp): e4[i] = exp(-i/4) for i < 352 and
+// e256[i] = exp(-i/256) for i < 64, so exp(-j/256) = e4[j >> 6] * e256[j & 63].
+constexpr int kDfExpRange = 88;  // arguments at or above give 0 (exp(-88) < FLT_MIN)
 struct DfConsts {
-  float ln2_1, ln2_2, ln2_3;
-  float e_hi[49], e_lo[49];
+  float2 e4[kDfExpRange * 4];
+  float2 e256[64];
 };
 
-// exp(-a) for a >= 0 (DF), relative error about 1e-13:
-//   a = n ln2 + r, |r| <= ln2/2 (Cody-Waite reduction: a.hi - n ln2_1 is
-//   exact by Sterbenz's lemma, the remaining small terms are summed in DF);
-//   r = j/64 + s, |s| <= 1/128 (r.hi - j/64 is exact as well);
-//   exp(-a) = 2^-n exp(-j/64) exp(-s),
-//   exp(-s) = 1 - s + s^2/2 in DF + s^3 (-1/6 + s/24 - s^2/120 + s^3/720) in
-//   FP32 (that tail is below 1e-7, so FP32 keeps it to ~1e-14).
-// Arguments at or above 87 (and NaN) give 0, by selection rather than an
-// early return; 2^-n is applied as an exact multiplication by a power of two.
+// exp(-a) for a >= 0 (DF), relative error below 1e-13 (the table entries
+// and the two DF products contribute a few 2^-47 each, the series about
+// 1e-15) where the result is a normal FP32 pair (above ~1e-30):
+//   j = floor(256 a.hi), and a.hi - j/256 in [0, 1/256) exactly (the
+//   fractional part of the exactly scaled 256 a.hi); s = that + a.lo,
+//   renormalised by TwoSum so that s.lo is below 2^-32;
+//   exp(-a) = exp(-j/256) exp(-s), the first factor from the two tables;
+//   exp(-s) = 1 - s + s^2/2 - s^3/6 + s^4/24 - s^5/120 (the next term is
+//   below 1e-14): 1 - s.hi exactly as a pair, s.hi^2 exactly as a product
+//   pair, the small rest in FP32.
+// Arguments at or above 88, and NaN, give 0 by selection rather than an
+// early return, so that several evaluations can interleave.
 __device__ __forceinline__ dfl df_exp_neg(dfl a, const DfConsts& K) {
-  const bool in_range = a.hi < 87.0f;
-  if (!in_range) a = {87.0f, 0.0f};
-  const float nf = rintf(__fmul_rn(a.hi, 1.4426950408889634f));
-  const float r1 = __fsub_rn(a.hi, __fmul_rn(nf, K.ln2_1));  // exact
-  const dfl p2 = df_two_prod(nf, K.ln2_2);                    // n ln2_2 exactly
-  const dfl c = df_two_sum(a.lo, -p2.hi);                     // a.lo - n ln2_2 (hi part)
-  const float cl = __fsub_rn(__fsub_rn(c.lo, p2.lo), __fmul_rn(nf, K.ln2_3));
-  dfl r = df_two_sum(r1, c.hi);
-  r = df_quick(r.hi, __fadd_rn(r.lo, cl));
-  int j = (int)rintf(__fmul_rn(r.hi, 64.0f));
-  j = max(-24, min(24, j));
-  const dfl s = df_quick(__fsub_rn(r.hi, (float)j * 0.015625f), r.lo);  // exact difference
-  const dfl s2 = df_sqr(s);
-  const dfl h1 = df_quick(1.0f, -s.hi);                   // 1 - s.hi, exact as a pair
-  const dfl h2 = df_two_sum(h1.hi, __fmul_rn(0.5f, s2.hi));
-  const float t = s.hi;
-  const float tail =
-      t * t * t *
-      (-0.16666667f + t * (0.041666668f + t * (-0.008333334f + t * 0.0013888889f)));
-  const float lo = __fadd_rn(__fadd_rn(__fsub_rn(__fadd_rn(h2.lo, h1.lo), s.lo),
-                                       __fmul_rn(0.5f, s2.lo)), tail);
-  const dfl e = df_quick(h2.hi, lo);
-  dfl v = df_mul(dfl{K.e_hi[j + 24], K.e_lo[j + 24]}, e);
-  const int ni = (int)nf;  // 0 <= ni <= 126
-  const float sc = __int_as_float((127 - ni) << 23);
-  return {in_range ? __fmul_rn(v.hi, sc) : 0.0f, in_range ? __fmul_rn(v.lo, sc) : 0.0f};
+  const bool in_range = a.hi < (float)kDfExpRange;  // false for NaN
+  const float ah = in_range ? fmaxf(a.hi, 0.0f) : 0.0f;      // table indices stay in range
+  const float al = in_range ? a.lo : 0.0f;
+  const int j = (int)__fmul_rz(ah, 256.0f);                  // ah * 256 is exact
+  const float sh = __fmaf_rn((float)j, -0.00390625f, ah);   // exact: frac(256 ah) / 256
+  const dfl sv = df_two_sum(sh, al);                         // s, |sv.lo| <= 2^-33
+  const dfl q = df_two_prod(sv.hi, sv.hi);                   // s.hi^2 = q.hi + q.lo
+  const dfl h = df_quick(1.0f, -sv.hi);                      // 1 - s.hi
+  const dfl t = df_two_sum(h.hi, __fmul_rn(0.5f, q.hi));     // + s.hi^2 / 2
+  float lo = __fadd_rn(h.lo, t.lo);
+  lo = __fmaf_rn(0.5f, q.lo, lo);
+  lo = __fsub_rn(lo, sv.lo);                                 // - s.lo
+  lo = __fmaf_rn(sv.hi, sv.lo, lo);                          // + s.hi s.lo (s^2 / 2)
+  const float x = sv.hi;
+  const float poly = x * (-0.16666667f + x * (0.041666668f - x * 0.008333334f));
+  lo = __fmaf_rn(q.hi, poly, lo);                            // -s^3/6 + s^4/24 - s^5/120
+  const dfl e = df_quick(t.hi, lo);
+  const float2 u = K.e4[j >> 6], w = K.e256[j & 63];
+  const dfl v = df_mul(df_mul(dfl{u.x, u.y}, dfl{w.x, w.y}), e);
+  return {in_range ? v.hi : 0.0f, in_range ? v.lo : 0.0f};
 }
 
 __device__ __forceinline__ double df_to_double(dfl x) { return (double)x.hi + (double)x.lo; }

@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kMaxSlots = kMaxK / 32;
 constexpr int kMaxRefine = 6;
-constexpr size_t kMixedHead = 512;  // per-CTA shared memory before the warps' areas
+constexpr size_t kMixedHead = 3584;  // per-CTA shared memory before the warps' areas
 static_assert(sizeof(DfConsts) <= kMixedHead, "the staged exponential table must fit the head");
 
 // The mixed kernels work with correlations phi (sigma^2 factored out): the
@@ -64,18 +64,21 @@ const DfConsts& df_consts() {
   static DfConsts c;
   static std::once_flag once;
   std::call_once(once, []() {
-    const double ln2 = 0.69314718055994530942;
-    c.ln2_1 = 0.693145751953125f;  // 14 significant bits
-    const double rem = ln2 - (double)c.ln2_1;
-    c.ln2_2 = (float)rem;
-    c.ln2_3 = (float)(rem - (double)c.ln2_2);
-    for (int j = -24; j <= 24; ++j) {
-      const double v = exp(-(double)j / 64.0);
-      c.e_hi[j + 24] = (float)v;
-      c.e_lo[j + 24] = (float)(v - (double)c.e_hi[j + 24]);
-    }
+    auto put = [](float2& dst, double v) {
+      const float hi = (float)v;
+      dst = make_float2(hi, (float)(v - (double)hi));
+    };
+    for (int i = 0; i < kDfExpRange * 4; ++i) put(c.e4[i], exp(-(double)i / 4.0));
+    for (int i = 0; i < 64; ++i) put(c.e256[i], exp(-(double)i / 256.0));
   });
   return c;
+}
+
+// Stage the exponential's tables in shared memory (lanes index them with
+// different entries, which the constant bank would serialise).
+__device__ __forceinline__ void stage_df_consts(DfConsts& dst, const DfConsts& src) {
+  for (int t = threadIdx.x; t < kDfExpRange * 4; t += blockDim.x) dst.e4[t] = src.e4[t];
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) dst.e256[t] = src.e256[t];
 }
 
 // Correlation phi at DF squared distance D (Eq. 3 closed forms / RBF).
@@ -93,10 +96,13 @@ __device__ __forceinline__ dfl corr_df(const KParamsDF& p, dfl D, const DfConsts
   return ph;
 }
 
+// Squared distance in DF; the first coordinate's square starts the sum (d >= 1).
 __device__ __forceinline__ dfl sqdist_df(const float2* a, const float2* b, int d) {
-  dfl s = {0.0f, 0.0f};
-  for (int t = 0; t < d; ++t) {
-    const float2 u = a[t], v = b[t];
+  float2 u = a[0], v = b[0];
+  dfl s = df_sqr(df_add_fast(dfl{u.x, u.y}, dfl{-v.x, -v.y}));
+  for (int t = 1; t < d; ++t) {
+    u = a[t];
+    v = b[t];
     const dfl diff = df_add_fast(dfl{u.x, u.y}, dfl{-v.x, -v.y});
     s = df_add_fast(s, df_sqr(diff));
   }
@@ -111,8 +117,11 @@ __device__ __forceinline__ void corr_df_multi(const KParamsDF& p, const float2* 
                                               dfl* out) {
   dfl D[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) D[u] = {0.0f, 0.0f};
-  for (int t = 0; t < d; ++t) {
+  for (int u = 0; u < U; ++u) {
+    const float2 x = XS[aa[u] * d], y = XS[bb[u] * d];
+    D[u] = df_sqr(df_add_fast(dfl{x.x, x.y}, dfl{-y.x, -y.y}));
+  }
+  for (int t = 1; t < d; ++t) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const float2 x = XS[aa[u] * d + t], y = XS[bb[u] * d + t];
@@ -278,15 +287,7 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
   // the exponential's constants, staged once per CTA: lanes index the table
   // with different j, which the constant bank would serialise
   DfConsts& Ks = *reinterpret_cast<DfConsts*>(smem);
-  if (threadIdx.x == 0) {
-    Ks.ln2_1 = mx.K.ln2_1;
-    Ks.ln2_2 = mx.K.ln2_2;
-    Ks.ln2_3 = mx.K.ln2_3;
-  }
-  for (int t = threadIdx.x; t < 49; t += blockDim.x) {
-    Ks.e_hi[t] = mx.K.e_hi[t];
-    Ks.e_lo[t] = mx.K.e_lo[t];
-  }
+  stage_df_consts(Ks, mx.K);
   __syncthreads();
   unsigned char* base = smem + kMixedHead + (size_t)wid * lay.bytes;
   float* M = (float*)(base + lay.off_L);
@@ -358,20 +359,24 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
     }
     for (int a = lane; a < k; a += 32) M[a * ldl + a] = kp.diag.hi;
     __syncwarp();
-    // FP32 Cholesky of the lower triangle of M, left-looking in blocks of four
-    // columns: the dot products of every row with the block's four columns
-    // over the finished prefix are formed in one pass (each row chunk read
-    // once for four columns), then the 4-column panel is factored in Crout
-    // order with pivots broadcast by shuffle.  Lane l owns rows l, l+32, ...
+    // FP32 Cholesky of the lower triangle of M, left-looking in panels of CB
+    // columns: the dot products of every row with the panel's columns over
+    // the finished prefix are formed in one pass (each row chunk read once
+    // for CB columns), then the panel is factored in Crout order with pivots
+    // broadcast by shuffle.  Rows are counted from the panel's first column:
+    // lane l owns rows j0 + l, j0 + l + 32, ..., so the rows still active
+    // fill the low lanes and a panel needs only ceil((k - j0) / 32) slots,
+    // and the pivot row of panel column c is always lane c's first slot.
     bool fail = false;
     for (int j0 = 0; j0 < k; j0 += CB) {
       const int nb = min(CB, k - j0);
+      const int ns = (k - j0 + 31) >> 5;  // slots in use (warp-uniform)
       float acc[NS][CB];
       bool act[NS];
 #pragma unroll
       for (int s4 = 0; s4 < NS; ++s4) {
-        const int r = lane + 32 * s4;
-        act[s4] = r >= j0 && r < k;
+        const int r = j0 + lane + 32 * s4;
+        act[s4] = s4 < ns && r < k;
 #pragma unroll
         for (int c = 0; c < CB; ++c)
           acc[s4][c] = (act[s4] && c < nb && j0 + c <= r) ? M[r * ldl + j0 + c] : 0.0f;
@@ -384,8 +389,9 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
                          : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int s4 = 0; s4 < NS; ++s4) {
+          if (s4 >= ns) break;
           if (!act[s4]) continue;
-          const float4 a4 = *reinterpret_cast<const float4*>(M + (lane + 32 * s4) * ldl + p);
+          const float4 a4 = *reinterpret_cast<const float4*>(M + (j0 + lane + 32 * s4) * ldl + p);
 #pragma unroll
           for (int c = 0; c < CB; ++c) {
             float t = acc[s4][c];
@@ -407,29 +413,25 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
       for (int c = 0; c < CB; ++c) {
         if (c >= nb) break;
         const int col = j0 + c;
-        const int owner = col & 31, os = col >> 5;
-        // the pivot row's finished entries L[col][j0 .. col-1] and its reduced diagonal
-        float lc[CB], dv = 0.0f;
+        // the pivot row's finished entries L[col][j0 .. col-1] and its reduced
+        // diagonal, from lane c's first slot
+        float lc[CB];
 #pragma unroll
-        for (int s4 = 0; s4 < NS; ++s4) {
-          if (s4 == os) {
-#pragma unroll
-            for (int c2 = 0; c2 < CB; ++c2) lc[c2] = __shfl_sync(kFull, lr[s4][c2], owner);
-            dv = __shfl_sync(kFull, acc[s4][c], owner);
-          }
-        }
+        for (int c2 = 0; c2 < CB; ++c2) lc[c2] = c2 < c ? __shfl_sync(kFull, lr[0][c2], c) : 0.0f;
+        float dv = __shfl_sync(kFull, acc[0][c], c);
 #pragma unroll
         for (int c2 = 0; c2 < CB; ++c2)
           if (c2 < c) dv = fmaf(-lc[c2], lc[c2], dv);
         if (!(dv > 0.0f)) { fail = true; break; }
         const float inv = rsqrtf(dv);
-        if (lane == owner) {
+        if (lane == c) {
           M[col * ldl + col] = dv * inv;
           invd[col] = inv;
         }
 #pragma unroll
         for (int s4 = 0; s4 < NS; ++s4) {
-          const int r = lane + 32 * s4;
+          if (s4 >= ns) break;
+          const int r = j0 + lane + 32 * s4;
           if (act[s4] && r > col) {
             float t = acc[s4][c];
 #pragma unroll
@@ -438,8 +440,6 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
             t *= inv;
             lr[s4][c] = t;
             M[r * ldl + col] = t;
-          } else if (act[s4] && r == col) {
-            lr[s4][c] = dv * inv;
           }
         }
       }
@@ -594,15 +594,7 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
   // the exponential's constants in shared memory (lanes index the table
   // with different j, which the constant bank would serialise)
   __shared__ DfConsts Ks;
-  if (threadIdx.x == 0) {
-    Ks.ln2_1 = K.ln2_1;
-    Ks.ln2_2 = K.ln2_2;
-    Ks.ln2_3 = K.ln2_3;
-  }
-  for (int t = threadIdx.x; t < 49; t += blockDim.x) {
-    Ks.e_hi[t] = K.e_hi[t];
-    Ks.e_lo[t] = K.e_lo[t];
-  }
+  stage_df_consts(Ks, K);
   __syncthreads();
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -647,6 +639,22 @@ __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
 }
 
 }  // namespace
+
+// Evaluate a double-float primitive on FP64 inputs split into DF pairs:
+// fn 0: exp(-x) (df_exp_neg), fn 1: sqrt(x) (df_sqrt).
+__global__ void df_eval_kernel(int fn, const double* x, int64_t n, double* y, DfConsts K) {
+  __shared__ DfConsts Ks;
+  stage_df_consts(Ks, K);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float hi = (float)v;
+    const dfl a = {hi, (float)(v - (double)hi)};
+    const dfl r = fn == 0 ? df_exp_neg(a, Ks) : df_sqrt(a);
+    y[i] = df_to_double(r);
+  }
+}
 
 template <typename T>
 __global__ void to_df_kernel(const T* in, float2* out, int64_t count) {
@@ -766,3 +774,19 @@ int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const in
 }
 
 }  // namespace fmgp
+
+using namespace fmgp;
+
+extern "C" int fmgp_df_eval(int32_t fn, const double* x, int64_t n, double* y, void* stream) {
+  clear_error();
+  if ((fn != 0 && fn != 1) || n < 0 || (n > 0 && (!x || !y))) {
+    set_error("fmgp_df_eval: fn must be 0 or 1, x and y non-NULL");
+    return FMGP_EINVAL;
+  }
+  if (n == 0) return FMGP_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
+  FMGP_LAUNCH(df_eval_kernel<<<blocks, 256, 0, s>>>(fn, x, n, y, df_consts()));
+  FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
