@@ -16,7 +16,8 @@
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *    enqueued asynchronously on it unless the entry point says otherwise.
  *    Internal workspace is taken stream-ordered from the device's default
- *    memory pool (cudaMallocAsync) and returned on the same stream.
+ *    memory pool (cudaMallocAsync), or from the context bound to the calling
+ *    thread (fmgp_context_bind), and returned on the same stream.
  *  - Argument errors are detected on the host before anything is launched:
  *    the call returns FMGP_EINVAL and launches nothing.  fmgp_last_error()
  *    returns a thread-local message describing the most recent failure.
@@ -43,7 +44,8 @@ typedef enum {
   FMGP_ECUDA = 3,        /* a CUDA call failed (message in fmgp_last_error) */
   FMGP_ENOTSPD = 4,      /* at least one kernel block was not positive definite */
   FMGP_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
-  FMGP_EUNSUPPORTED = 6  /* valid request outside what this build implements */
+  FMGP_EUNSUPPORTED = 6, /* valid request outside what this build implements */
+  FMGP_EIO = 7           /* a model file could not be read or written, or is damaged */
 } fmgp_status;
 
 typedef enum { FMGP_F32 = 0, FMGP_F64 = 1 } fmgp_dtype;
@@ -273,6 +275,39 @@ int fmgp_model_predict(fmgp_model* model, const void* Z, int64_t m, double* Yhat
 /* Free the model's own buffers (waits for the device to go idle first). */
 int fmgp_model_destroy(fmgp_model* model);
 
+/* What a model was fitted with. */
+typedef struct {
+  int64_t n;
+  int32_t d, r, k, nbr_ld;
+  int32_t dtype;      /* fmgp_dtype of X */
+  int32_t precision;  /* fmgp_precision of C */
+  fmgp_kernel kernel;
+} fmgp_model_info;
+int fmgp_model_get_info(const fmgp_model* model, fmgp_model_info* out);
+
+/*
+ * fmgp_model_save / fmgp_model_load -- the fitted model of Algorithm 2 (X,
+ * the neighbour table, the precomputed coefficients C of Eq. 6, k, the kernel
+ * hyperparameters and the precision form) in a file, so that the online
+ * phase (Eq. 7) can run in another process.
+ * File: a 128-byte little-endian header (magic "FMGPMODL", version 1, shapes,
+ * dtype, precision, kernel, the byte size of each array, a 64-bit FNV-1a
+ * checksum over the header and the data), then X (n x d), the neighbour table
+ * (n x nbr_ld int32; absent when k = 1) and C (n x k x r, 8 bytes each) as
+ * stored on the device.  Arrays pass through a pinned host buffer of at most
+ * 64 MB.
+ * fmgp_model_save synchronises `stream`.  fmgp_model_load allocates device
+ * memory for X, the table and C (owned by the model and freed by
+ * fmgp_model_destroy), checks the header and the checksum, builds the model
+ * as fmgp_model_create does, and synchronises `stream`.  A loaded model
+ * predicts bit-identically to the one that was saved.
+ * Returns FMGP_OK, FMGP_EINVAL (NULL arguments), FMGP_EIO (file cannot be
+ * opened, read or written; not a model file; unsupported version;
+ * inconsistent sizes; checksum mismatch), FMGP_ENOMEM or FMGP_ECUDA.
+ */
+int fmgp_model_save(const fmgp_model* model, const char* path, void* stream);
+int fmgp_model_load(const char* path, fmgp_model** out, void* stream);
+
 /* Device bytes owned by the model (grid and copies of X), -1 for NULL. */
 int64_t fmgp_model_device_bytes(const fmgp_model* model);
 
@@ -402,6 +437,31 @@ int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, const double* 
                                  double* Q_out, double* resid_out, void* stream);
 
 /*
+ * Workspace contexts (the paper has no counterpart: memory management).
+ * fmgp_context_create reserves `bytes` (rounded up to a multiple of 2 MiB) of
+ * device memory on the current device in a private stream-ordered pool whose
+ * size can never exceed that.
+ * After fmgp_context_bind(ctx), every entry point called from this thread on
+ * that device takes its internal workspace from the context instead of the
+ * device's default pool, so the library's device memory use is bounded and
+ * allocated up front; a call whose workspace does not fit returns
+ * FMGP_ENOMEM with nothing launched that would need it.  The binding is per
+ * thread (a server's scheduler thread does not inherit it); bind NULL to
+ * return to the default pool.  Buffers a resident model keeps (grid, copies
+ * of X) come from the context bound when it is created: destroy such models
+ * before the context.
+ * fmgp_context_bytes_in_use: bytes the library's buffers currently hold from
+ * the context (each allocation counted in whole 256-byte units; -1 for NULL).
+ * An allocation that would take it past the context's size fails.  fmgp_context_destroy waits for the device to go idle, unbinds
+ * the context from the calling thread and releases its memory.
+ */
+typedef struct fmgp_context fmgp_context;
+int fmgp_context_create(int64_t bytes, fmgp_context** out);
+int fmgp_context_bind(fmgp_context* ctx);
+int64_t fmgp_context_bytes_in_use(const fmgp_context* ctx);
+int fmgp_context_destroy(fmgp_context* ctx);
+
+/*
  * fmgp_peak_probe -- measured throughput of an arithmetic pipe on the current
  * device, the denominator of the roofline fractions of the neighbourhood
  * kernels (the paper has no counterpart: measurement support).
@@ -431,7 +491,8 @@ const char* fmgp_last_error(void);
 const char* fmgp_version(void);
 
 /*
- * Launch-shape and path controls (results never depend on them):
+ * Launch-shape and path controls (results never depend on them) and two
+ * checking / testing switches (check_finite, fail_alloc_after):
  *   "grid_target"  mean training points per grid cell of the d <= 3 search (default 12)
  *   "block_warps"  warps per CTA of the neighbourhood kernels, 0 = automatic
  *   "tensor_cores" 1 = tcgen05 candidate search for kNN at d >= 16 (default), 0 = off
@@ -449,6 +510,17 @@ const char* fmgp_version(void);
  *                  re-rank of the tensor-core search (2..4, default 4; at
  *                  least 32; at most 128 per query, or 2 kq where that is
  *                  larger, up to 320)
+ *   "check_finite" 1 = every entry point first scans its floating-point
+ *                  device inputs (X, Y, Z) on `stream`, synchronises it, and
+ *                  returns FMGP_EINVAL naming the array if one holds a NaN or
+ *                  an infinity (not while the stream is being captured into a
+ *                  CUDA graph); 0 = no scan (default: the entry points stay
+ *                  asynchronous; non-finite inputs then give unspecified
+ *                  values, never an out-of-bounds access).  Kernel
+ *                  hyperparameters are always checked on the host.
+ *   "fail_alloc_after" failure injection for tests: the next N workspace
+ *                  allocations succeed and every later one fails as if the
+ *                  device were out of memory (FMGP_ENOMEM); -1 = off (default)
  *   "tc_chunk_queries" queries per pass of the fused tensor-core selection
  *                  (rounded down to whole blocks of 128, at least one block;
  *                  0 = as many as keep its per-range lists within ~1 GB,

@@ -11,7 +11,8 @@ import torch
 
 from . import build as _build
 
-FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM, FMGP_ECUDA, FMGP_ENOTSPD, FMGP_ETIMEOUT, FMGP_EUNSUPPORTED = range(7)
+(FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM, FMGP_ECUDA, FMGP_ENOTSPD, FMGP_ETIMEOUT, FMGP_EUNSUPPORTED,
+ FMGP_EIO) = range(8)
 F32, F64 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 KERNEL_MATERN, KERNEL_RBF = 0, 1
@@ -37,6 +38,12 @@ class Kernel(ctypes.Structure):
 def make_kernel(kind="matern", nu=1.5, length_scale=0.1, variance=1.0, nugget=1e-4):
     return Kernel(KERNEL_MATERN if kind == "matern" else KERNEL_RBF, float(nu),
                   float(length_scale), float(variance), float(nugget))
+
+
+class ModelInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("nbr_ld", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("kernel", Kernel)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -85,6 +92,20 @@ def load(build_if_missing=True):
     lib.fmgp_peak_probe.argtypes = [I32, ctypes.POINTER(ctypes.c_double), P]
     lib.fmgp_df_eval.argtypes = [I32, P, I64, P, P]
     lib.fmgp_df_eval.restype = I32
+    lib.fmgp_model_get_info.argtypes = [P, ctypes.POINTER(ModelInfo)]
+    lib.fmgp_model_get_info.restype = I32
+    lib.fmgp_model_save.argtypes = [P, ctypes.c_char_p, P]
+    lib.fmgp_model_save.restype = I32
+    lib.fmgp_model_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p), P]
+    lib.fmgp_model_load.restype = I32
+    lib.fmgp_context_create.argtypes = [I64, ctypes.POINTER(ctypes.c_void_p)]
+    lib.fmgp_context_create.restype = I32
+    lib.fmgp_context_bind.argtypes = [P]
+    lib.fmgp_context_bind.restype = I32
+    lib.fmgp_context_bytes_in_use.argtypes = [P]
+    lib.fmgp_context_bytes_in_use.restype = I64
+    lib.fmgp_context_destroy.argtypes = [P]
+    lib.fmgp_context_destroy.restype = I32
     lib.fmgp_peak_probe.restype = I32
     lib.fmgp_kernel_launches.restype = ctypes.c_uint64
     lib.fmgp_muygps_predict.argtypes = [P, I32, P, I64, I32, I32, P, I64, I32, KP, I32, P, P, P]
@@ -371,6 +392,27 @@ class FmgpModel:
                                         _stream(stream)))
         self.handle = h
 
+    @classmethod
+    def load(cls, path, stream=None):
+        """fmgp_model_load: a model read from a file (it owns its X, table and C)."""
+        h = ctypes.c_void_p()
+        _check(load().fmgp_model_load(os.fsencode(path), ctypes.byref(h), _stream(stream)))
+        self = cls.__new__(cls)
+        self.handle = h
+        self.X = self.nbr = self.C = None
+        info = ModelInfo()
+        _check(load().fmgp_model_get_info(h, ctypes.byref(info)))
+        self.n, self.d, self.r, self.k = int(info.n), int(info.d), int(info.r), int(info.k)
+        self.kernel = Kernel(info.kernel.kind, info.kernel.nu, info.kernel.length_scale,
+                             info.kernel.variance, info.kernel.nugget)
+        self.precision = int(info.precision)
+        self.dtype = torch.float64 if info.dtype == F64 else torch.float32
+        return self
+
+    def save(self, path, stream=None):
+        """fmgp_model_save: write the fitted model to a file."""
+        _check(load().fmgp_model_save(self.handle, os.fsencode(path), _stream(stream)))
+
     def predict(self, Z, Yhat_out=None, nearest_out=None, with_nearest=True, stream=None):
         _dev(Z, "Z")
         m = Z.shape[0]
@@ -426,6 +468,38 @@ class FmgpModel:
             self.close()
         except Exception:
             pass
+
+
+class Context:
+    """fmgp_context_*: a reserved, size-capped workspace pool on the current
+    device; `with ctx:` binds it to this thread for the block."""
+
+    def __init__(self, nbytes):
+        h = ctypes.c_void_p()
+        _check(load().fmgp_context_create(int(nbytes), ctypes.byref(h)))
+        self.handle = h
+
+    def bind(self):
+        _check(load().fmgp_context_bind(self.handle))
+
+    @staticmethod
+    def unbind():
+        _check(load().fmgp_context_bind(None))
+
+    def bytes_in_use(self):
+        return int(load().fmgp_context_bytes_in_use(self.handle))
+
+    def __enter__(self):
+        self.bind()
+        return self
+
+    def __exit__(self, *exc):
+        Context.unbind()
+
+    def close(self):
+        if self.handle:
+            _check(load().fmgp_context_destroy(self.handle))
+            self.handle = None
 
 
 class FmgpServer:

@@ -2,8 +2,10 @@
 // and the launch sequence of each step.
 #include <stdarg.h>
 #include <stdio.h>
+#include <string.h>
 #include <math.h>
 #include <atomic>
+#include <initializer_list>
 #include <map>
 #include <tuple>
 #include <string>
@@ -94,16 +96,59 @@ static void keep_pool_memory() {
   });
 }
 
+}  // namespace fmgp
+
+// A workspace context: a private stream-ordered memory pool of fixed maximum
+// size on one device, with that size reserved at creation.
+struct fmgp_context {
+  int device = 0;
+  cudaMemPool_t pool = nullptr;
+  int64_t bytes = 0;
+  std::atomic<int64_t> in_use{0};  // bytes the library's buffers hold from it
+};
+
+namespace fmgp {
+
+static thread_local fmgp_context* t_ctx = nullptr;  // bound by fmgp_context_bind
+// Host-side failure injection (tuning key "fail_alloc_after"): the number of
+// workspace allocations still allowed before every further one fails; < 0 = off.
+static std::atomic<long long> g_alloc_budget{-1};
+
 void* Workspace::alloc(size_t bytes) {
   if (count_ >= 32) {
     set_error("workspace: too many allocations");
     return nullptr;
   }
-  keep_pool_memory();
+  if (g_alloc_budget.load() >= 0 && g_alloc_budget.fetch_sub(1) <= 0) {
+    g_alloc_budget.store(0);
+    set_error("workspace: allocation refused (injected failure)");
+    return nullptr;
+  }
   void* p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, bytes > 0 ? bytes : 16, stream_);
+  cudaError_t e;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (t_ctx && t_ctx->device == dev) {
+    // the context's size is a hard limit on what the library holds from it
+    const int64_t need = (int64_t)((bytes + 255) & ~(size_t)255);
+    if (t_ctx->in_use.fetch_add(need) + need > t_ctx->bytes) {
+      t_ctx->in_use.fetch_sub(need);
+      set_error("workspace: %zu bytes do not fit the bound context (%lld of %lld bytes in use)",
+                bytes, (long long)t_ctx->in_use.load(), (long long)t_ctx->bytes);
+      return nullptr;
+    }
+    e = cudaMallocFromPoolAsync(&p, bytes > 0 ? bytes : 16, t_ctx->pool, stream_);
+    if (e != cudaSuccess) t_ctx->in_use.fetch_sub(need);
+    else {
+      ctx_ = t_ctx;
+      ctx_bytes_ += need;
+    }
+  } else {
+    keep_pool_memory();
+    e = cudaMallocAsync(&p, bytes > 0 ? bytes : 16, stream_);
+  }
   if (e != cudaSuccess) {
-    set_error("workspace: cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    set_error("workspace: allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     cudaGetLastError();
     return nullptr;
   }
@@ -114,6 +159,11 @@ void* Workspace::alloc(size_t bytes) {
 
 Workspace::~Workspace() {
   for (int i = 0; i < count_; ++i) cudaFreeAsync(ptrs_[i], stream_);
+  if (ctx_) context_release(ctx_, ctx_bytes_);
+}
+
+void context_release(fmgp_context* ctx, int64_t bytes) {
+  if (ctx && bytes) ctx->in_use.fetch_sub(bytes);
 }
 
 // ------------------------------------------------------------ validation --
@@ -236,6 +286,57 @@ static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, int mode,
   return run_block_mixed(a, X, dtype, mode, req, kern, ws, s);
 }
 
+// flag = 1 if some value of the array is NaN or +-Inf.
+template <typename T>
+__global__ void nonfinite_kernel(const T* a, int64_t count, int* flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(a[i]);
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+// With the tuning key "check_finite" set: scan the floating-point inputs on
+// the device (stream-ordered), read the result back (synchronising `s`) and
+// return FMGP_EINVAL naming the first array holding a NaN or an infinity.
+// Does nothing while `s` is being captured into a CUDA graph.
+int check_finite(std::initializer_list<FloatArray> arrays, cudaStream_t s) {
+  if (!tune_params().check_finite) return FMGP_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  FMGP_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return FMGP_OK;
+  Workspace ws(s);
+  int* flags = ws.get<int>(arrays.size());
+  if (!flags) return FMGP_ENOMEM;
+  FMGP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * arrays.size(), s));
+  int i = 0;
+  for (const FloatArray& a : arrays) {
+    if (a.p && a.count > 0) {
+      const int blocks = (int)std::max<int64_t>(
+          1, std::min<int64_t>(ceil_div(a.count, 256), (int64_t)num_sms() * 4));
+      if (a.f64)
+        FMGP_LAUNCH(nonfinite_kernel<double><<<blocks, 256, 0, s>>>((const double*)a.p, a.count, flags + i));
+      else
+        FMGP_LAUNCH(nonfinite_kernel<float><<<blocks, 256, 0, s>>>((const float*)a.p, a.count, flags + i));
+    }
+    ++i;
+  }
+  FMGP_CUDA_TRY(cudaGetLastError());
+  int h[8] = {0};
+  const size_t nb = sizeof(int) * std::min<size_t>(arrays.size(), 8);
+  FMGP_CUDA_TRY(cudaMemcpyAsync(h, flags, nb, cudaMemcpyDeviceToHost, s));
+  FMGP_CUDA_TRY(cudaStreamSynchronize(s));
+  i = 0;
+  for (const FloatArray& a : arrays) {
+    if (i < 8 && h[i]) {
+      set_error("%s holds a NaN or an infinity", a.name);
+      return FMGP_EINVAL;
+    }
+    ++i;
+  }
+  return FMGP_OK;
+}
+
 // Deterministic single-CTA sum of the LOOCV residuals: thread t adds
 // entries t, t+1024, ... in order, then a fixed tree.
 __global__ void __launch_bounds__(1024) loocv_reduce(const double* resid, int64_t b, double* out) {
@@ -292,6 +393,78 @@ int grid_for(int64_t count) {
 extern "C" {
 
 const char* fmgp_last_error(void) { return g_err; }
+
+int fmgp_context_create(int64_t bytes, fmgp_context** out) {
+  clear_error();
+  if (!out || bytes < 1) {
+    set_error("out must be non-NULL and bytes >= 1");
+    return FMGP_EINVAL;
+  }
+  *out = nullptr;
+  int dev = 0;
+  FMGP_CUDA_TRY(cudaGetDevice(&dev));
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  // whole 2 MiB chunks: the pool reserves device memory in units of its
+  // allocation granularity
+  bytes = (bytes + (2 << 20) - 1) / (2 << 20) * (2 << 20);
+  props.maxSize = (size_t)bytes;
+  cudaMemPool_t pool;
+  FMGP_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+  // keep what the pool holds between calls, and take the whole size now so
+  // that later calls are served from memory already reserved
+  uint64_t thr = UINT64_MAX;
+  cudaError_t e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  void* p = nullptr;
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&p, (size_t)bytes, pool, 0);
+  if (e == cudaSuccess) e = cudaFreeAsync(p, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaMemPoolDestroy(pool);
+    set_error("context: cannot reserve %lld device bytes: %s", (long long)bytes,
+              cudaGetErrorString(e));
+    return FMGP_ENOMEM;
+  }
+  fmgp_context* c = new fmgp_context();
+  c->device = dev;
+  c->pool = pool;
+  c->bytes = bytes;
+  *out = c;
+  return FMGP_OK;
+}
+
+int fmgp_context_bind(fmgp_context* ctx) {
+  clear_error();
+  t_ctx = ctx;
+  return FMGP_OK;
+}
+
+int64_t fmgp_context_bytes_in_use(const fmgp_context* ctx) {
+  return ctx ? ctx->in_use.load() : -1;
+}
+
+int fmgp_context_destroy(fmgp_context* ctx) {
+  clear_error();
+  if (!ctx) {
+    set_error("context is NULL");
+    return FMGP_EINVAL;
+  }
+  if (t_ctx == ctx) t_ctx = nullptr;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();  // stream-ordered frees into the pool have completed
+  const cudaError_t e = cudaMemPoolDestroy(ctx->pool);
+  cudaSetDevice(prev);
+  delete ctx;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolDestroy");
+  return FMGP_OK;
+}
 const char* fmgp_version(void) { return "0.1.0"; }
 uint64_t fmgp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
@@ -327,6 +500,11 @@ int fmgp_tune_set(const char* key, double value) {
   } else if (k == "tc_oversample") {
     if (!(value >= 2 && value <= 4)) { set_error("tc_oversample out of range [2, 4]"); return FMGP_EINVAL; }
     tp.tc_oversample = (int)value;
+  } else if (k == "check_finite") {
+    tp.check_finite = value != 0.0;
+  } else if (k == "fail_alloc_after") {
+    if (!(value >= -1 && value <= 1e9)) { set_error("fail_alloc_after out of range"); return FMGP_EINVAL; }
+    g_alloc_budget.store((long long)value);
   } else if (k == "tc_chunk_queries") {
     if (!(value >= 0 && value <= 2147483647.0)) { set_error("tc_chunk_queries out of range"); return FMGP_EINVAL; }
     tp.tc_chunk_queries = (int64_t)value;
@@ -349,6 +527,8 @@ double fmgp_tune_get(const char* key) {
   if (k == "count_visits") return tp.count_visits ? 1.0 : 0.0;
   if (k == "tc_fused_r") return tp.tc_fused_r;
   if (k == "tc_chunk_queries") return (double)tp.tc_chunk_queries;
+  if (k == "fail_alloc_after") return (double)g_alloc_budget.load();
+  if (k == "check_finite") return tp.check_finite ? 1.0 : 0.0;
   return -1.0;
 }
 
@@ -363,6 +543,7 @@ int fmgp_build_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_
                kq, kMaxK);
   FMGP_REQUIRE(flags == 0, "flags must be 0");
   cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}}, s)) return fc;
   Workspace ws(s);
   TuneParams tp = tune_params();
   tp.grid_target = grid_target_for(d, kq);
@@ -393,6 +574,7 @@ int fmgp_precompute(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
   FMGP_REQUIRE(k >= 1 && k <= n && k <= kMaxK, "k = %d must be in [1, min(n, %d)]", k, kMaxK);
   FMGP_REQUIRE(nbr_ld >= k - 1 && nbr_ld >= 0, "nbr_ld = %d must be >= k-1 = %d", nbr_ld, k - 1);
   cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Y, true, n * (int64_t)r, "Y"}}, s)) return fc;
   Workspace ws(s);
   int* fails = ws.get<int>(1);
   if (!fails) return FMGP_ENOMEM;
@@ -440,6 +622,7 @@ int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const in
   if (m == 0) return FMGP_OK;
   FMGP_REQUIRE(Z && Yhat_out, "Z and Yhat_out must be non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Z, dtype == FMGP_F64, m * (int64_t)d, "Z"}}, s)) return fc;
   Workspace ws(s);
   int32_t* near = nearest_out;
   if (!near) {
@@ -467,6 +650,7 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
   FMGP_REQUIRE(nbr_ld >= k, "nbr_ld = %d must be >= k = %d", nbr_ld, k);
   FMGP_REQUIRE(b >= 1, "batch size b = %lld must be >= 1", (long long)b);
   cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Y, true, n * (int64_t)r, "Y"}}, s)) return fc;
   Workspace ws(s);
   int* fails = ws.get<int>(1);
   double* qd = ws.get<double>(1);
@@ -515,6 +699,7 @@ int fmgp_muygps_predict(const void* X, fmgp_dtype dtype, const double* Y, int64_
   if (m == 0) return FMGP_OK;
   FMGP_REQUIRE(Z && Yhat_out, "Z and Yhat_out must be non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Y, true, n * (int64_t)r, "Y"}, {Z, dtype == FMGP_F64, m * (int64_t)d, "Z"}}, s)) return fc;
   Workspace ws(s);
   int32_t* nbr = nbr_out ? nbr_out : ws.get<int32_t>((size_t)m * k);
   int* fails = ws.get<int>(1);
@@ -563,6 +748,7 @@ int fmgp_precompute_rows(const void* X, fmgp_dtype dtype, const double* Y, int64
   FMGP_REQUIRE(k >= 1 && k <= n && k <= kMaxK, "k = %d must be in [1, min(n, %d)]", k, kMaxK);
   FMGP_REQUIRE(nbr_ld >= k - 1 && nbr_ld >= 0, "nbr_ld = %d must be >= k-1 = %d", nbr_ld, k - 1);
   cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Y, true, n * (int64_t)r, "Y"}}, s)) return fc;
   Workspace ws(s);
   int* fails = ws.get<int>(1);
   if (!fails) return FMGP_ENOMEM;
@@ -613,6 +799,7 @@ int fmgp_predict_rows(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, con
   if (m == 0) return FMGP_OK;
   FMGP_REQUIRE(Z && Yhat_out, "Z and Yhat_out must be non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Z, dtype == FMGP_F64, m * (int64_t)d, "Z"}}, s)) return fc;
   Workspace ws(s);
   int* flag = ws.get<int>(1);
   const size_t xb = dtype == FMGP_F64 ? 8 : 4;

@@ -1,5 +1,6 @@
 // Shared device/host helpers of libfmgp (CUDA path only).
 #pragma once
+#include <initializer_list>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <limits.h>
@@ -149,11 +150,16 @@ class Workspace {
   // Returns nullptr (and records the error) on failure.
   void* alloc(size_t bytes);
   template <typename T> T* get(size_t count) { return (T*)alloc(count * sizeof(T)); }
-  // Hand every allocation so far to the caller (who then frees them); returns the count.
-  int detach(void** out, int max) {
+  // Hand every allocation so far to the caller (who then frees them, and
+  // returns `*ctx_bytes` to `*ctx` with context_release when ctx is set);
+  // returns the count.
+  int detach(void** out, int max, fmgp_context** ctx, int64_t* ctx_bytes) {
     int c = count_ < max ? count_ : max;
     for (int i = 0; i < c; ++i) out[i] = ptrs_[i];
+    *ctx = ctx_;
+    *ctx_bytes = ctx_bytes_;
     count_ = 0;
+    ctx_bytes_ = 0;
     return c;
   }
   size_t bytes() const { return bytes_; }
@@ -163,9 +169,27 @@ class Workspace {
   cudaStream_t stream_;
   void* ptrs_[32];
   int count_ = 0;
+  fmgp_context* ctx_ = nullptr;  // the context the allocations came from, if any
+  int64_t ctx_bytes_ = 0;        // bytes charged to it
 };
 
+// Give bytes charged to a workspace context back to it (a resident model's
+// buffers when the model is destroyed).
+void context_release(fmgp_context* ctx, int64_t bytes);
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// A floating-point input array for check_finite (FP64 or FP32, `count` values).
+struct FloatArray {
+  const void* p;
+  bool f64;
+  int64_t count;
+  const char* name;
+};
+// With the tuning key "check_finite" set: scan the arrays on the device,
+// synchronise `s`, and return FMGP_EINVAL naming the first one holding a NaN
+// or an infinity; otherwise (and while `s` is being captured) FMGP_OK.
+int check_finite(std::initializer_list<FloatArray> arrays, cudaStream_t s);
 
 // Diagnostics: count a tensor-core kNN call and copy its number of queries
 // that needed the exact fallback (device int) to a host slot read by

@@ -12,43 +12,54 @@ namespace fmgp {
 
 Model::~Model() {
   for (int i = 0; i < nbufs; ++i) cudaFree(bufs[i]);
+  context_release(ctx, ctx_bytes);
 }
 
 }  // namespace fmgp
 
 using namespace fmgp;
 
-extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d,
-                                 const int32_t* nbr, int32_t nbr_ld, const void* C, int32_t k,
-                                 int32_t r, const fmgp_kernel* kernel, fmgp_precision precision,
-                                 fmgp_model** out, void* stream) {
-  if (!out) { set_error("out must be non-NULL"); return FMGP_EINVAL; }
+namespace fmgp {
+
+// Validate a model's arguments and build what its predictions reuse; the
+// buffers in owned[0..nowned) (X, nbr, C of a loaded model) become the
+// model's and are freed with it, also when this fails.
+int model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
+                 int32_t nbr_ld, const void* C, int32_t k, int32_t r, const fmgp_kernel* kernel,
+                 fmgp_precision precision, fmgp_model** out, cudaStream_t s, void* const* owned,
+                 int nowned) {
+  auto release = [&]() {
+    for (int i = 0; i < nowned; ++i) cudaFree(owned[i]);
+  };
+  if (!out) { release(); set_error("out must be non-NULL"); return FMGP_EINVAL; }
   *out = nullptr;
   if (!X || !C || (k > 1 && !nbr) || !kernel) {
     set_error("X, C, kernel (and nbr when k > 1) must be non-NULL");
-    return FMGP_EINVAL;
+    return release(), FMGP_EINVAL;
   }
-  if (dtype != FMGP_F32 && dtype != FMGP_F64) { set_error("dtype unknown"); return FMGP_EINVAL; }
+  if (dtype != FMGP_F32 && dtype != FMGP_F64) { set_error("dtype unknown"); return release(), FMGP_EINVAL; }
   if (precision != FMGP_PREC_FP64 && precision != FMGP_PREC_MIXED) {
     set_error("precision unknown");
-    return FMGP_EINVAL;
+    return release(), FMGP_EINVAL;
   }
   if (n < 1 || n >= INT32_MAX || d < 1 || r < 1 || k < 1 || k > n || k > kMaxK ||
       nbr_ld < k - 1) {
     set_error("shape invalid: n=%lld d=%d r=%d k=%d nbr_ld=%d", (long long)n, d, r, k, nbr_ld);
-    return FMGP_EINVAL;
+    return release(), FMGP_EINVAL;
   }
   if (kernel->kind == FMGP_KERNEL_MATERN &&
       !(kernel->nu == 0.5 || kernel->nu == 1.5 || kernel->nu == 2.5)) {
     set_error("Matern nu = %g unsupported", kernel->nu);
-    return FMGP_EINVAL;
+    return release(), FMGP_EINVAL;
   }
   if (!(kernel->length_scale > 0) || !(kernel->variance > 0) || !(kernel->nugget >= 0)) {
     set_error("kernel hyperparameters invalid");
-    return FMGP_EINVAL;
+    return release(), FMGP_EINVAL;
   }
-  cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}}, s))
+    return release(), fc;
   Model* m = new Model();
+  for (int i = 0; i < nowned && i < Model::kMaxBufs; ++i) m->bufs[m->nbufs++] = owned[i];
   m->X = X; m->dtype = dtype; m->n = n; m->d = d; m->nbr = nbr; m->ld = nbr_ld; m->C = C;
   m->k = k; m->r = r; m->kern = *kernel; m->prec = precision;
   Workspace ws(s);
@@ -76,7 +87,7 @@ extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
   }
   m->bytes = ws.bytes();
-  m->nbufs = ws.detach(m->bufs, Model::kMaxBufs);
+  m->nbufs += ws.detach(m->bufs + m->nbufs, Model::kMaxBufs - m->nbufs, &m->ctx, &m->ctx_bytes);
   if (rc) {
     delete m;
     return rc;
@@ -85,13 +96,28 @@ extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int
   return FMGP_OK;
 }
 
+}  // namespace fmgp
+
+extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d,
+                                 const int32_t* nbr, int32_t nbr_ld, const void* C, int32_t k,
+                                 int32_t r, const fmgp_kernel* kernel, fmgp_precision precision,
+                                 fmgp_model** out, void* stream) {
+  clear_error();
+  return model_create(X, dtype, n, d, nbr, nbr_ld, C, k, r, kernel, precision, out,
+                      (cudaStream_t)stream, nullptr, 0);
+}
+
 extern "C" int fmgp_model_predict(fmgp_model* model, const void* Z, int64_t m, double* Yhat_out,
                                   int32_t* nearest_out, void* stream) {
+  clear_error();
   Model* md = reinterpret_cast<Model*>(model);
   if (!md) { set_error("model is NULL"); return FMGP_EINVAL; }
   if (m < 0) { set_error("m = %lld must be >= 0", (long long)m); return FMGP_EINVAL; }
   if (m == 0) return FMGP_OK;
   if (!Z || !Yhat_out) { set_error("Z and Yhat_out must be non-NULL"); return FMGP_EINVAL; }
+  if (int fc = check_finite({{Z, md->dtype == FMGP_F64, m * (int64_t)md->d, "Z"}},
+                            (cudaStream_t)stream))
+    return fc;
   return model_predict(*md, Z, m, Yhat_out, nearest_out, (cudaStream_t)stream);
 }
 

@@ -26,10 +26,19 @@ struct Model {
   void* bufs[kMaxBufs];
   int nbufs = 0;
   size_t bytes = 0;
+  fmgp_context* ctx = nullptr;  // workspace context the buffers were charged to
+  int64_t ctx_bytes = 0;
   ~Model();
 };
 
 int model_predict(const Model& md, const void* Z, int64_t m, double* Yhat, int32_t* nearest,
                   cudaStream_t s);
+
+// fmgp_model_create with the device buffers owned[0..nowned) handed to the
+// model (freed with it, or at once if creation fails).
+int model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
+                 int32_t nbr_ld, const void* C, int32_t k, int32_t r, const fmgp_kernel* kernel,
+                 fmgp_precision precision, fmgp_model** out, cudaStream_t s, void* const* owned,
+                 int nowned);
 
 }  // namespace fmgp
