@@ -186,6 +186,22 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
                          void* stream);
 
 /*
+ * fmgp_loocv_objective_device -- fmgp_loocv_objective without synchronising:
+ * Q is written to the DEVICE double Q_dev on `stream` (NaN if any block was
+ * not positive definite), the number of such blocks to the device int
+ * fails_dev (or nowhere when it is NULL), so that a whole step including the
+ * objective can be captured into a CUDA graph and replayed.  Other arguments,
+ * the reduction order and the results as fmgp_loocv_objective.  Returns
+ * FMGP_OK, FMGP_EINVAL, FMGP_ENOMEM or FMGP_ECUDA.
+ */
+int fmgp_loocv_objective_device(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                                int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld,
+                                int32_t k, const int64_t* batch, int64_t b,
+                                const fmgp_kernel* kernel, fmgp_precision precision,
+                                double* Q_dev, int32_t* fails_dev, double* resid_out,
+                                void* stream);
+
+/*
  * fmgp_muygps_predict -- plain MuyGPs prediction (Eq. 8), the method
  * FastMuyGPs accelerates: every test point z_t uses its OWN k nearest
  * training points N*_t (canonical key, ties to the lowest index) and one
@@ -495,6 +511,9 @@ const char* fmgp_version(void);
  * checking / testing switches (check_finite, fail_alloc_after):
  *   "grid_target"  mean training points per grid cell of the d <= 3 search (default 12)
  *   "block_warps"  warps per CTA of the neighbourhood kernels, 0 = automatic
+ *   "block_panel"  Cholesky panel width of the mixed neighbourhood kernel for
+ *                  k <= 64: 4 or 8 columns, 0 = the autotuner's choice or the
+ *                  default (8 for k <= 32, 4 above)
  *   "tensor_cores" 1 = tcgen05 candidate search for kNN at d >= 16 (default), 0 = off
  *   "tc_fused_select" 1 = the candidates are selected inside the tcgen05
  *                  distance kernel (default), 0 = distances go through a pass
@@ -533,9 +552,11 @@ double fmgp_tune_get(const char* key);  /* -1 for an unknown key */
 /*
  * Autotuner (the paper has no counterpart: launch-shape selection).
  * fmgp_autotune_precompute times the neighbourhood kernel with each feasible
- * warps-per-CTA on the first sample_rows rows of this problem and caches the
- * fastest for (precision, k, d, r, dtype); later fmgp_precompute /
- * fmgp_loocv_objective calls with that key use it.  fmgp_autotune_knn times
+ * warps-per-CTA (and, for the mixed form with k <= 64, each Cholesky panel
+ * width, 4 or 8 columns) on the first sample_rows rows of this problem and
+ * caches the fastest for (precision, k, d, r, dtype); later fmgp_precompute /
+ * fmgp_loocv_objective calls with that key use it.  fmgp_autotune_choice
+ * reports the cached shape (0 = none cached: the default).  fmgp_autotune_knn times
  * the grid search of fmgp_build_knn at several cell occupancies and caches
  * the fastest for (d, kq) (d <= 3; for larger d it reports 0).  Results of
  * the path never depend on these choices.  Both synchronise `stream`.
@@ -546,6 +567,8 @@ int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const double* Y, i
                              int64_t sample_rows, int32_t* warps_out, void* stream);
 int fmgp_autotune_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
                       double* grid_target_out, void* stream);
+int fmgp_autotune_choice(fmgp_precision precision, int32_t k, int32_t d, int32_t r,
+                         fmgp_dtype dtype, int32_t* warps, int32_t* panel);
 int fmgp_autotune_reset(void);
 
 /* Diagnostic counters: 0 = kernels enqueued, 1 = tensor-core kNN calls,

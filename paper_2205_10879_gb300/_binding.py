@@ -92,6 +92,12 @@ def load(build_if_missing=True):
     lib.fmgp_peak_probe.argtypes = [I32, ctypes.POINTER(ctypes.c_double), P]
     lib.fmgp_df_eval.argtypes = [I32, P, I64, P, P]
     lib.fmgp_df_eval.restype = I32
+    lib.fmgp_loocv_objective_device.argtypes = [P, I32, P, I64, I32, I32, P, I32, I32, P, I64,
+                                                KP, I32, P, P, P, P]
+    lib.fmgp_loocv_objective_device.restype = I32
+    lib.fmgp_autotune_choice.argtypes = [I32, I32, I32, I32, I32, ctypes.POINTER(I32),
+                                         ctypes.POINTER(I32)]
+    lib.fmgp_autotune_choice.restype = I32
     lib.fmgp_model_get_info.argtypes = [P, ctypes.POINTER(ModelInfo)]
     lib.fmgp_model_get_info.restype = I32
     lib.fmgp_model_save.argtypes = [P, ctypes.c_char_p, P]
@@ -292,6 +298,23 @@ def peak_probe(pipe, stream=None):
     return v.value
 
 
+def fmgp_loocv_objective_device(X, Y, nbr, k, batch, kernel, precision=PREC_FP64, Q_out=None,
+                                fails_out=None, resid_out=None, stream=None):
+    """Eq. 5 objective into a 1-element float64 CUDA tensor without
+    synchronising (graph-capturable): (Q, fails or None, residuals or None)."""
+    _dev(X, "X"); _dev(Y, "Y"); _dev(nbr, "nbr"); _dev(batch, "batch")
+    n, d = X.shape
+    r = Y.shape[1]
+    b = batch.shape[0]
+    if Q_out is None:
+        Q_out = torch.empty(1, dtype=torch.float64, device=X.device)
+    _check(load().fmgp_loocv_objective_device(
+        _ptr(X), _dtype_code(X), _ptr(Y), n, d, r, _ptr(nbr), nbr.shape[1], int(k), _ptr(batch),
+        b, ctypes.byref(kernel), int(precision), _ptr(Q_out), _ptr(fails_out), _ptr(resid_out),
+        _stream(stream)))
+    return Q_out, fails_out, resid_out
+
+
 def fmgp_muygps_predict(X, Y, Z, k, kernel, precision=PREC_FP64, Yhat_out=None, nbr_out=None,
                         with_nbr=False, stream=None):
     """MuyGPs prediction (Eq. 8): (Yhat m x r, neighbour table m x k or None)."""
@@ -352,6 +375,16 @@ def fmgp_autotune_knn(X, kq, stream=None):
     _check(load().fmgp_autotune_knn(_ptr(X), _dtype_code(X), n, d, int(kq), ctypes.byref(t),
                                     _stream(stream)))
     return t.value
+
+
+def autotune_choice(k, d, r, precision, dtype=torch.float64):
+    """The cached launch shape for a precompute key: (warps per CTA, Cholesky
+    panel width); 0 where nothing is cached (the default is used)."""
+    w, p = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().fmgp_autotune_choice(int(precision), int(k), int(d), int(r),
+                                       F64 if dtype == torch.float64 else F32,
+                                       ctypes.byref(w), ctypes.byref(p)))
+    return w.value, p.value
 
 
 def autotune_reset():

@@ -283,7 +283,9 @@ static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, int mode,
   int req = tune_params().block_warps;
   if (req == 0) req = tuned_block_warps((int)precision, a.k, a.d, a.r, (int)dtype);
   if (precision == FMGP_PREC_FP64) return launch_block_f64(a, X, dtype, mode, req, s);
-  return run_block_mixed(a, X, dtype, mode, req, kern, ws, s);
+  int panel = tune_params().block_panel;
+  if (panel == 0) panel = tuned_block_panel((int)precision, a.k, a.d, a.r, (int)dtype);
+  return run_block_mixed(a, X, dtype, mode, req, panel, kern, ws, s);
 }
 
 // flag = 1 if some value of the array is NaN or +-Inf.
@@ -488,6 +490,9 @@ int fmgp_tune_set(const char* key, double value) {
   } else if (k == "block_warps") {
     if (!(value >= 0 && value <= 8)) { set_error("block_warps out of range"); return FMGP_EINVAL; }
     tp.block_warps = (int)value;
+  } else if (k == "block_panel") {
+    if (!(value == 0 || value == 4 || value == 8)) { set_error("block_panel must be 0, 4 or 8"); return FMGP_EINVAL; }
+    tp.block_panel = (int)value;
   } else if (k == "tensor_cores") {
     tp.use_tensor_cores = value != 0.0;
   } else if (k == "tc_fused_select") {
@@ -521,6 +526,7 @@ double fmgp_tune_get(const char* key) {
   const std::string k(key);
   if (k == "grid_target") return tp.grid_target;
   if (k == "block_warps") return tp.block_warps;
+  if (k == "block_panel") return tp.block_panel;
   if (k == "tensor_cores") return tp.use_tensor_cores ? 1.0 : 0.0;
   if (k == "tc_fused_select") return tp.tc_fused_select ? 1.0 : 0.0;
   if (k == "tc_oversample") return tp.tc_oversample;
@@ -635,27 +641,16 @@ int fmgp_predict(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const in
                     precision, Z, m, near, Yhat_out, ws, s);
 }
 
-int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
-                         int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+// Enqueue the LOOCV objective: residuals, then Q (the mean over the batch,
+// in a fixed order) into the device double qd and the number of failed blocks
+// into the device int fails (both written on `s`).
+static int loocv_enqueue(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                         int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
                          const int64_t* batch, int64_t b, const fmgp_kernel* kernel,
-                         fmgp_precision precision, double* Q_out, double* resid_out,
-                         void* stream) {
-  clear_error();
-  int rc = validate_block_args(X, dtype, Y, n, d, r, nbr, nbr_ld, kernel, precision);
-  if (rc) return rc;
-  FMGP_REQUIRE(Q_out && batch, "Q_out and batch must be non-NULL");
-  FMGP_REQUIRE(n >= 2, "LOOCV needs n >= 2");
-  FMGP_REQUIRE(k >= 1 && k <= n - 1 && k <= kMaxK, "k = %d must be in [1, min(n-1, %d)]", k,
-               kMaxK);
-  FMGP_REQUIRE(nbr_ld >= k, "nbr_ld = %d must be >= k = %d", nbr_ld, k);
-  FMGP_REQUIRE(b >= 1, "batch size b = %lld must be >= 1", (long long)b);
-  cudaStream_t s = (cudaStream_t)stream;
-  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Y, true, n * (int64_t)r, "Y"}}, s)) return fc;
-  Workspace ws(s);
-  int* fails = ws.get<int>(1);
-  double* qd = ws.get<double>(1);
+                         fmgp_precision precision, double* qd, int* fails, double* resid_out,
+                         Workspace& ws, cudaStream_t s) {
   double* resid = resid_out ? resid_out : ws.get<double>(b);
-  if (!fails || !qd || !resid) return FMGP_ENOMEM;
+  if (!resid) return FMGP_ENOMEM;
   FMGP_CUDA_TRY(cudaMemsetAsync(fails, 0, sizeof(int), s));
   BlockArgs a{};
   a.Y = Y;
@@ -670,10 +665,45 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
   a.ld = nbr_ld;
   a.k = k;
   a.kp = make_kparams(*kernel);
-  rc = run_blocks(a, X, dtype, kModeLoocv, *kernel, precision, ws, s);
+  int rc = run_blocks(a, X, dtype, kModeLoocv, *kernel, precision, ws, s);
   if (rc) return rc;
   FMGP_LAUNCH(loocv_reduce<<<1, 1024, 0, s>>>(resid, b, qd));
   FMGP_CUDA_TRY(cudaGetLastError());
+  return FMGP_OK;
+}
+
+static int loocv_validate(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,
+                          int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                          const int64_t* batch, int64_t b, const fmgp_kernel* kernel,
+                          fmgp_precision precision, const double* Q_out) {
+  int rc = validate_block_args(X, dtype, Y, n, d, r, nbr, nbr_ld, kernel, precision);
+  if (rc) return rc;
+  FMGP_REQUIRE(Q_out && batch, "Q_out and batch must be non-NULL");
+  FMGP_REQUIRE(n >= 2, "LOOCV needs n >= 2");
+  FMGP_REQUIRE(k >= 1 && k <= n - 1 && k <= kMaxK, "k = %d must be in [1, min(n-1, %d)]", k,
+               kMaxK);
+  FMGP_REQUIRE(nbr_ld >= k, "nbr_ld = %d must be >= k = %d", nbr_ld, k);
+  FMGP_REQUIRE(b >= 1, "batch size b = %lld must be >= 1", (long long)b);
+  return FMGP_OK;
+}
+
+int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                         int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld, int32_t k,
+                         const int64_t* batch, int64_t b, const fmgp_kernel* kernel,
+                         fmgp_precision precision, double* Q_out, double* resid_out,
+                         void* stream) {
+  clear_error();
+  int rc = loocv_validate(X, dtype, Y, n, d, r, nbr, nbr_ld, k, batch, b, kernel, precision, Q_out);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Y, true, n * (int64_t)r, "Y"}}, s)) return fc;
+  Workspace ws(s);
+  int* fails = ws.get<int>(1);
+  double* qd = ws.get<double>(1);
+  if (!fails || !qd) return FMGP_ENOMEM;
+  rc = loocv_enqueue(X, dtype, Y, n, d, r, nbr, nbr_ld, k, batch, b, kernel, precision, qd, fails,
+                     resid_out, ws, s);
+  if (rc) return rc;
   int h = 0;
   FMGP_CUDA_TRY(cudaMemcpyAsync(Q_out, qd, sizeof(double), cudaMemcpyDeviceToHost, s));
   FMGP_CUDA_TRY(cudaMemcpyAsync(&h, fails, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -683,6 +713,24 @@ int fmgp_loocv_objective(const void* X, fmgp_dtype dtype, const double* Y, int64
     return FMGP_ENOTSPD;
   }
   return FMGP_OK;
+}
+
+int fmgp_loocv_objective_device(const void* X, fmgp_dtype dtype, const double* Y, int64_t n,
+                                int32_t d, int32_t r, const int32_t* nbr, int32_t nbr_ld,
+                                int32_t k, const int64_t* batch, int64_t b,
+                                const fmgp_kernel* kernel, fmgp_precision precision,
+                                double* Q_dev, int32_t* fails_dev, double* resid_out,
+                                void* stream) {
+  clear_error();
+  int rc = loocv_validate(X, dtype, Y, n, d, r, nbr, nbr_ld, k, batch, b, kernel, precision, Q_dev);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int fc = check_finite({{X, dtype == FMGP_F64, n * (int64_t)d, "X"}, {Y, true, n * (int64_t)r, "Y"}}, s)) return fc;
+  Workspace ws(s);
+  int* fails = fails_dev ? (int*)fails_dev : ws.get<int>(1);
+  if (!fails) return FMGP_ENOMEM;
+  return loocv_enqueue(X, dtype, Y, n, d, r, nbr, nbr_ld, k, batch, b, kernel, precision, Q_dev,
+                       fails, resid_out, ws, s);
 }
 
 int fmgp_muygps_predict(const void* X, fmgp_dtype dtype, const double* Y, int64_t n, int32_t d,

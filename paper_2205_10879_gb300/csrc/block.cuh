@@ -53,7 +53,8 @@ int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mo
 
 // Mixed-precision form (FP32 factor + double-float refinement + FP64 fallback).
 size_t mixed_bytes_per_warp(int k, int d, int r);
-int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps,
+// panel: Cholesky panel width 4 or 8 (k <= 64 only), 0 = the default for k.
+int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps, int panel,
                     const fmgp_kernel& kern, Workspace& ws, cudaStream_t s);
 
 }  // namespace fmgp

@@ -677,7 +677,7 @@ int to_df(const void* in, bool f64, int64_t count, float2* out, cudaStream_t s) 
 
 size_t mixed_bytes_per_warp(int k, int d, int r) { return mixed_layout(k, d, r).bytes; }
 
-int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps,
+int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps, int panel,
                     const fmgp_kernel& kern, Workspace& ws, cudaStream_t s) {
   const bool loo = mode != kModePrecompute;
   MixedArgs mx;
@@ -697,20 +697,26 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   mx.K = df_consts();
   mx.kdf = make_kparams_df(a.kp, kern);
   const MixedLayout lay = mixed_layout(a.k, a.d, a.r);
-  // rows per lane (k <= 32 S) and Cholesky block width are compile-time
-  auto pick = [&](auto sconst) {
+  // rows per lane (k <= 32 S) and the Cholesky panel width are compile-time:
+  // 8 columns for k <= 32 and 4 above by default; for k <= 64 the other
+  // width is instantiated too (panel = 4 or 8 picks it, 0 the default)
+  auto pick = [&](auto sconst, auto cbconst) {
     constexpr int SS = decltype(sconst)::value;
-    constexpr int CB = SS <= 1 ? 8 : 4;
+    constexpr int CB = decltype(cbconst)::value;
     return mode == kModeLoocv    ? block_mixed_kernel<kModeLoocv, SS, CB>
            : mode == kModeMuygps ? block_mixed_kernel<kModeMuygps, SS, CB>
                                  : block_mixed_kernel<kModePrecompute, SS, CB>;
   };
+  using I4 = std::integral_constant<int, 4>;
+  using I8 = std::integral_constant<int, 8>;
   const int S = (a.k + 31) / 32;
-  auto kern_fn = S == 1 ? pick(std::integral_constant<int, 1>{})
-               : S == 2 ? pick(std::integral_constant<int, 2>{})
-               : S == 3 ? pick(std::integral_constant<int, 3>{})
-               : S == 4 ? pick(std::integral_constant<int, 4>{})
-                        : pick(std::integral_constant<int, 5>{});
+  auto kern_fn = S == 1 ? (panel == 4 ? pick(std::integral_constant<int, 1>{}, I4{})
+                                      : pick(std::integral_constant<int, 1>{}, I8{}))
+               : S == 2 ? (panel == 8 ? pick(std::integral_constant<int, 2>{}, I8{})
+                                      : pick(std::integral_constant<int, 2>{}, I4{}))
+               : S == 3 ? pick(std::integral_constant<int, 3>{}, I4{})
+               : S == 4 ? pick(std::integral_constant<int, 4>{}, I4{})
+                        : pick(std::integral_constant<int, 5>{}, I4{});
   int nb = 0;
   {
     // the 2-slot instantiation is compiled for at most 192 threads (6 warps)

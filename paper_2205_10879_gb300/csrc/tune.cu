@@ -15,6 +15,7 @@ namespace {
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_warps;
+std::map<std::tuple<int, int, int, int, int>, int> g_panel;
 std::map<std::tuple<int, int>, double> g_grid;
 
 }  // namespace
@@ -23,6 +24,12 @@ int tuned_block_warps(int prec, int k, int d, int r, int dtype) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_warps.find({prec, k, d, r, dtype});
   return it == g_warps.end() ? 0 : it->second;
+}
+
+int tuned_block_panel(int prec, int k, int d, int r, int dtype) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_panel.find({prec, k, d, r, dtype});
+  return it == g_panel.end() ? 0 : it->second;
 }
 
 double grid_target_for(int d, int kq) {
@@ -98,18 +105,25 @@ extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const d
   a.layout = block_layout(k, d, r, dtype == FMGP_F64 ? 8 : 4, false);
   const size_t bytes = precision == FMGP_PREC_FP64 ? a.layout.bytes_per_warp
                                                    : mixed_bytes_per_warp(k, d, r);
-  int best = 0;
+  int best = 0, best_panel = 0;
   float best_ms = 1e30f;
-  for (int w : {1, 2, 4, 6, 8}) {
-    if ((size_t)w * bytes > 200 * 1024) continue;
-    float ms = 0.f;
-    int rc = time_ms(s, 2, [&]() {
-      Workspace inner(s);
-      return precision == FMGP_PREC_FP64 ? launch_block_f64(a, X, dtype, kModePrecompute, w, s)
-                                         : run_block_mixed(a, X, dtype, kModePrecompute, w, *kernel, inner, s);
-    }, &ms);
-    if (rc) return rc;
-    if (ms < best_ms) { best_ms = ms; best = w; }
+  // the mixed kernel's Cholesky panel width: both instantiated widths for k <= 64
+  const bool panels = precision == FMGP_PREC_MIXED && k <= 64;
+  for (int panel : {0, 4, 8}) {
+    if (panel && !panels) continue;
+    if (!panel && panels) continue;
+    for (int w : {1, 2, 4, 6, 8}) {
+      if ((size_t)w * bytes > 200 * 1024) continue;
+      float ms = 0.f;
+      int rc = time_ms(s, 2, [&]() {
+        Workspace inner(s);
+        return precision == FMGP_PREC_FP64
+                   ? launch_block_f64(a, X, dtype, kModePrecompute, w, s)
+                   : run_block_mixed(a, X, dtype, kModePrecompute, w, panel, *kernel, inner, s);
+      }, &ms);
+      if (rc) return rc;
+      if (ms < best_ms) { best_ms = ms; best = w; best_panel = panel; }
+    }
   }
   if (!best) {
     set_error("autotune: no feasible warps-per-CTA for k=%d d=%d r=%d", k, d, r);
@@ -118,8 +132,20 @@ extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const d
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_warps[{(int)precision, k, d, r, (int)dtype}] = best;
+    g_panel[{(int)precision, k, d, r, (int)dtype}] = best_panel;
   }
   *warps_out = best;
+  return FMGP_OK;
+}
+
+extern "C" int fmgp_autotune_choice(fmgp_precision precision, int32_t k, int32_t d, int32_t r,
+                                    fmgp_dtype dtype, int32_t* warps, int32_t* panel) {
+  if (!warps || !panel) {
+    set_error("warps and panel must be non-NULL");
+    return FMGP_EINVAL;
+  }
+  *warps = tuned_block_warps((int)precision, k, d, r, (int)dtype);
+  *panel = tuned_block_panel((int)precision, k, d, r, (int)dtype);
   return FMGP_OK;
 }
 
@@ -162,6 +188,7 @@ extern "C" int fmgp_autotune_knn(const void* X, fmgp_dtype dtype, int64_t n, int
 extern "C" int fmgp_autotune_reset(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_warps.clear();
+  g_panel.clear();
   g_grid.clear();
   return FMGP_OK;
 }
