@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serving-requests", type=int, default=300)
+    p.add_argument("--serving-piece", type=int, default=8192,
+                   help="test points per piece of a request / per launched batch")
     p.add_argument("--n", type=int, default=150_000)
     p.add_argument("--m", type=int, default=50_000)
     p.add_argument("--k", type=int, default=50)
@@ -835,16 +837,17 @@ def serving_bench(a, dev):
         fits.append(tm)
     fit_s = time.perf_counter() - t0
     srv = fb.FmgpServer(models, device_budget_bytes=4 << 30, host_staging_bytes=2 << 30,
-                        streams=4)
+                        streams=4, max_batch_points=a.serving_piece)
     # saturation: a burst of requests all at once
-    lat, pts, wall = serving.run_poisson(srv, models, 0.0, max(40, a.serving_requests // 4), 11)
-    sat = serving.latency_summary(lat, pts, wall)
+    lat, pts, wall, sz = serving.run_poisson(srv, models, 0.0, max(40, a.serving_requests // 4), 11)
+    sat = serving.latency_summary(lat, pts, wall, sz)
     req_rate = sat["requests"] / sat["wall_s"]
-    out = {"models": fits, "fit_seconds": fit_s, "saturation": sat}
+    out = {"models": fits, "fit_seconds": fit_s, "streams": 4, "piece_points": a.serving_piece,
+           "saturation": sat}
     for frac in (0.25, 0.5, 0.75, 0.9):
-        lat, pts, wall = serving.run_poisson(srv, models, frac * req_rate, a.serving_requests,
-                                             12 + int(frac * 100))
-        out[f"load_{int(frac * 100)}"] = serving.latency_summary(lat, pts, wall)
+        lat, pts, wall, sz = serving.run_poisson(srv, models, frac * req_rate, a.serving_requests,
+                                                 12 + int(frac * 100))
+        out[f"load_{int(frac * 100)}"] = serving.latency_summary(lat, pts, wall, sz)
     out["server"] = srv.stats()
     srv.close()
     for m in models:

@@ -368,25 +368,31 @@ typedef struct {
   int64_t device_budget_bytes;  /* admitted requests' device bytes (inputs + outputs) */
   int64_t host_staging_bytes;   /* pinned staging arena; >= the largest request */
   int32_t streams;              /* batches in flight at once (1..16) */
-  int32_t max_batch_points;     /* cap on test points per launched batch */
+  int32_t max_batch_points;     /* cap on test points per launched batch; larger
+                                   requests are split into pieces of this size */
 } fmgp_server_config;
 
 typedef struct {
   int64_t submitted, completed, rejected;
   int64_t batches;              /* launched batches */
   int64_t points;               /* completed test points */
-  double mean_batch_requests;   /* requests per batch */
+  double mean_batch_requests;   /* request pieces per batch */
 } fmgp_server_stats;
 
 /*
  * fmgp_server_create -- a continuous-batching prediction service over
  * `count` resident models (borrowed; they must outlive the server).  A
  * scheduler thread admits queued requests first-come-first-served while
- * their device bytes fit the budget, launches every admitted request of a
- * model as one batch on the next free stream (so batches of different
- * models and later arrivals overlap on the device), and completes requests
- * from event polling.  Each prediction depends only on its own test point,
- * so a request's result is bit-identical alone or inside any batch.
+ * their device bytes fit the budget, splits each into pieces of at most
+ * max_batch_points test points, launches the pending pieces of a model (up
+ * to max_batch_points points) as one batch on the next free stream (so
+ * batches of different models, later arrivals and the pieces of a large
+ * request overlap on the device, and a small request waits behind at most
+ * one piece of a large one), and completes a request from event polling
+ * when its last piece has finished.  Staging copies and CUDA calls are made
+ * outside the lock that submitters take.  Each prediction depends only on
+ * its own test point, so a request's result is bit-identical alone, inside
+ * any batch, or split into pieces.
  * The device current at creation is used by the scheduler thread.
  */
 int fmgp_server_create(fmgp_model* const* models, int32_t count, const fmgp_server_config* cfg,

@@ -6,6 +6,7 @@
 //   nearest point only, 4 <= d <= 15: one thread per query over slices of
 //            the training points, then a minimum over the slices.
 // Both rank on the canonical FP64 key; FP32 is used only for lower bounds.
+#include <algorithm>
 #include "knn.cuh"
 #include "topk.cuh"
 
@@ -309,8 +310,8 @@ __global__ void __launch_bounds__(256) merge_parts_kernel(
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t pos = pos0 + w;
-  if (pos >= min((int64_t)*qcount, pos_end)) return;
-  const int64_t q = qlist[pos];
+  if (pos >= (qlist ? min((int64_t)*qcount, pos_end) : pos_end)) return;
+  const int64_t q = qlist ? (int64_t)qlist[pos] : pos;
   const int tot = ny * kq;
   const int32_t* pi = part_idx + w * tot;
   const unsigned long long* pk = reinterpret_cast<const unsigned long long*>(part_key) + w * tot;
@@ -371,6 +372,25 @@ int launch_brute_t(const T* X, const float* Xf, int64_t n, int d, const T* Q, in
   auto kern = knn_brute_kernel<T, L>;
   FMGP_CUDA_TRY(ensure_smem((const void*)kern, smem));
   if (!qlist) {
+    // few queries: split the candidate rows over CTAs so that about four
+    // waves of CTAs scan them, then merge each query's partial lists
+    const int64_t qblocks = ceil_div(m, kBfWarps);
+    const int64_t tiles = ceil_div(n, kBfTile);
+    const int64_t want = 4ll * num_sms();
+    if (ws && qblocks * 2 <= want && tiles >= 4) {
+      const int64_t ny0 = std::min<int64_t>({tiles, 1024, std::max<int64_t>(2, want / qblocks)});
+      const int64_t range_rows = (int64_t)ceil_div(ceil_div(n, ny0), kBfTile) * kBfTile;
+      const int ny = ceil_div(n, range_rows);
+      int32_t* pidx = ws->get<int32_t>((size_t)m * ny * kq);
+      double* pkey = ws->get<double>((size_t)m * ny * kq);
+      if (!pidx || !pkey) return FMGP_ENOMEM;
+      FMGP_LAUNCH(kern<<<dim3((unsigned)qblocks, (unsigned)ny), kBfWarps * 32, smem, s>>>(
+          X, Xf, n, d, Q, m, kq, excl, mx, idx, key, nullptr, nullptr, 0, m, range_rows, pidx, pkey));
+      FMGP_LAUNCH(merge_parts_kernel<L><<<ceil_div(m * 32, 256), 256, 0, s>>>(
+          pidx, pkey, ny, kq, nullptr, nullptr, 0, m, idx, key));
+      FMGP_CUDA_TRY(cudaGetLastError());
+      return FMGP_OK;
+    }
     FMGP_LAUNCH(kern<<<ceil_div(m, kBfWarps), kBfWarps * 32, smem, s>>>(
         X, Xf, n, d, Q, m, kq, excl, mx, idx, key, nullptr, nullptr, 0, m, 0, nullptr, nullptr));
     FMGP_CUDA_TRY(cudaGetLastError());

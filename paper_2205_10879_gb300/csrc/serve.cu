@@ -2,19 +2,25 @@
 //
 // Submitters enqueue requests (host test points, host result buffers).  One
 // scheduler thread per server:
-//   1. completes in-flight batches whose CUDA event has fired: copies each
-//      request's results from the pinned staging arena to the caller's
-//      buffers and releases its reservation;
+//   1. completes in-flight batches whose CUDA event has fired; a request is
+//      finished when the last of its pieces is (its results are then copied
+//      from the pinned staging arena to the caller's buffers and its
+//      reservation released);
 //   2. admits queued requests first-come-first-served while their device
-//      bytes fit the budget and their staging fits the pinned arena (their
-//      test points are copied into the arena at admission);
-//   3. while a stream is free, launches all admitted requests of the model of
-//      the oldest admitted request as one batch: host-to-device copies into
-//      one stream-ordered allocation, nearest-point lookup + gather-dot over
-//      the concatenated points, device-to-host copies of the results, an event;
+//      bytes fit the budget and their staging fits the pinned arena, and
+//      splits each into pieces of at most max_batch_points test points;
+//   3. while a stream is free, launches the pending pieces of the model of the
+//      oldest pending piece, up to max_batch_points points, as one batch:
+//      host-to-device copies into one stream-ordered allocation,
+//      nearest-point lookup + gather-dot over the concatenated points,
+//      device-to-host copies of the results, an event;
 //   4. sleeps briefly while work is in flight, or waits for a submission.
-// Batches on different streams overlap on the device, and requests arriving
-// while others run join the next batch of their model.
+// Batches on different streams overlap on the device; requests arriving
+// while others run join the next batch of their model, and a large request
+// occupies a stream for one piece at a time, so small requests behind it
+// wait for at most one piece.  The server mutex guards only the queues and
+// the request table: copies into the staging arena and every CUDA call are
+// made by the scheduler thread without it, so submitters never wait on them.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -80,13 +86,22 @@ struct Request {
   size_t zbytes = 0, ybytes = 0, nbytes = 0, dev_bytes = 0, stage_bytes = 0, stage_off = 0;
   Clock::time_point t_submit, t_launch, t_done;
   int status = FMGP_OK;
+  int pending = 0;     // pieces not yet completed
+  bool launched = false;
   bool done = false;
+};
+
+// Test points [off, off + cnt) of a request.
+struct Piece {
+  Request* r;
+  int64_t off, cnt;
 };
 
 struct Batch {
   int model = 0;
   int stream = 0;
-  std::vector<Request*> reqs;
+  std::vector<Piece> pieces;
+  int status = FMGP_OK;
 };
 
 }  // namespace
@@ -103,7 +118,7 @@ struct Server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> queue;
-  std::vector<Request*> admitted;
+  std::deque<Piece> admitted;  // pieces of admitted requests, oldest first
   std::unordered_map<uint64_t, Request*> requests;
   int64_t reserved = 0;
   uint64_t next_id = 1;
@@ -122,20 +137,23 @@ struct Server {
   }
 };
 
+// Called with mu held.
 void Server::complete(int s) {
   Batch* b = slot[s];
   cudaError_t e = cudaEventQuery(events[s]);
   if (e == cudaErrorNotReady) return;
-  const int status = e == cudaSuccess ? FMGP_OK : FMGP_ECUDA;
+  const int status = e == cudaSuccess ? b->status : FMGP_ECUDA;
   if (e != cudaSuccess) cudaGetLastError();
   const auto now = Clock::now();
-  for (Request* r : b->reqs) {
-    if (status == FMGP_OK) {
+  for (const Piece& pc : b->pieces) {
+    Request* r = pc.r;
+    if (r->status == FMGP_OK) r->status = status;
+    if (--r->pending > 0) continue;
+    if (r->status == FMGP_OK) {
       std::memcpy(r->Y_host, pinned + r->stage_off + r->zbytes, r->ybytes);
       if (r->N_host) std::memcpy(r->N_host, pinned + r->stage_off + r->zbytes + r->ybytes, r->nbytes);
       stats.points += r->m;
     }
-    if (r->status == FMGP_OK) r->status = status;
     r->t_done = now;
     r->done = true;
     stage->release(r->stage_off, r->stage_bytes);
@@ -147,14 +165,17 @@ void Server::complete(int s) {
   cv_done.notify_all();
 }
 
+// Called without mu: only the scheduler thread uses the streams, events and
+// the staging ranges of admitted requests.
 void Server::launch(int s, Batch* b) {
   Model& md = *models[b->model];
   cudaStream_t st = streams[s];
   int64_t M = 0;
-  for (Request* r : b->reqs) M += r->m;
+  for (const Piece& pc : b->pieces) M += pc.cnt;
   const size_t elem = md.dtype == FMGP_F64 ? 8 : 4;
-  const size_t zb = RangeAlloc::round((size_t)M * md.d * elem);
-  const size_t yb = RangeAlloc::round((size_t)M * md.r * 8);
+  const size_t zrow = (size_t)md.d * elem, yrow = (size_t)md.r * 8;
+  const size_t zb = RangeAlloc::round((size_t)M * zrow);
+  const size_t yb = RangeAlloc::round((size_t)M * yrow);
   const size_t nb = RangeAlloc::round((size_t)M * 4);
   unsigned char* dev = nullptr;
   int rc = FMGP_OK;
@@ -163,71 +184,97 @@ void Server::launch(int s, Batch* b) {
     cudaGetLastError();
     rc = FMGP_ENOMEM;
   }
-  const auto now = Clock::now();
   if (rc == FMGP_OK) {
     size_t zo = 0;
-    for (Request* r : b->reqs) {
-      cudaMemcpyAsync(dev + zo, pinned + r->stage_off, r->zbytes, cudaMemcpyHostToDevice, st);
-      zo += r->zbytes;
+    for (const Piece& pc : b->pieces) {
+      cudaMemcpyAsync(dev + zo, pinned + pc.r->stage_off + pc.off * zrow, pc.cnt * zrow,
+                      cudaMemcpyHostToDevice, st);
+      zo += pc.cnt * zrow;
     }
     double* Yd = (double*)(dev + zb);
     int32_t* Nd = (int32_t*)(dev + zb + yb);
     rc = model_predict(md, dev, M, Yd, Nd, st);
-    size_t p = 0;
-    for (Request* r : b->reqs) {
+    int64_t p = 0;
+    for (const Piece& pc : b->pieces) {
+      Request* r = pc.r;
       unsigned char* h = pinned + r->stage_off + r->zbytes;
-      cudaMemcpyAsync(h, Yd + p * md.r, r->ybytes, cudaMemcpyDeviceToHost, st);
-      if (r->N_host) cudaMemcpyAsync(h + r->ybytes, Nd + p, r->nbytes, cudaMemcpyDeviceToHost, st);
-      p += r->m;
+      cudaMemcpyAsync(h + pc.off * yrow, Yd + p * md.r, pc.cnt * yrow, cudaMemcpyDeviceToHost, st);
+      if (r->N_host)
+        cudaMemcpyAsync(h + r->ybytes + pc.off * 4, Nd + p, pc.cnt * 4, cudaMemcpyDeviceToHost, st);
+      p += pc.cnt;
     }
     cudaFreeAsync(dev, st);
   }
-  for (Request* r : b->reqs) {
-    r->t_launch = now;
-    if (rc != FMGP_OK) r->status = rc;
-  }
+  b->status = rc;
   cudaEventRecord(events[s], st);
-  slot[s] = b;
-  stats.batches += 1;
-  batched_requests += (int64_t)b->reqs.size();
 }
 
 void Server::run() {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lk(mu);
+  std::vector<Request*> to_stage;
+  std::vector<Batch*> to_launch;
   for (;;) {
     for (int s = 0; s < (int)slot.size(); ++s)
       if (slot[s]) complete(s);
     // admission, first come first served, by device bytes and staging space
+    to_stage.clear();
     while (!queue.empty()) {
       Request* r = queue.front();
       if (reserved + (int64_t)r->dev_bytes > cfg.device_budget_bytes) break;
       size_t off = 0;
       if (!stage->alloc(r->stage_bytes, &off)) break;
       r->stage_off = off;
-      std::memcpy(pinned + off, r->Z_host, r->zbytes);
       reserved += (int64_t)r->dev_bytes;
-      admitted.push_back(r);
+      to_stage.push_back(r);
       queue.pop_front();
     }
-    // launches: one batch per free stream, model of the oldest admitted request
+    if (!to_stage.empty()) {
+      lk.unlock();  // the arena range is this thread's: copy without the lock
+      for (Request* r : to_stage) std::memcpy(pinned + r->stage_off, r->Z_host, r->zbytes);
+      lk.lock();
+      for (Request* r : to_stage) {
+        const int64_t piece = cfg.max_batch_points;
+        for (int64_t off = 0; off < r->m; off += piece) {
+          admitted.push_back(Piece{r, off, std::min<int64_t>(piece, r->m - off)});
+          ++r->pending;
+        }
+      }
+    }
+    // batches: per free stream, pending pieces of the model of the oldest
+    // pending piece, up to max_batch_points points
+    to_launch.clear();
     for (int s = 0; s < (int)slot.size() && !admitted.empty(); ++s) {
       if (slot[s]) continue;
       Batch* b = new Batch();
-      b->model = admitted.front()->model;
+      b->model = admitted.front().r->model;
       b->stream = s;
       int64_t pts = 0;
-      std::vector<Request*> rest;
-      for (Request* r : admitted) {
-        if (r->model == b->model && (b->reqs.empty() || pts + r->m <= cfg.max_batch_points)) {
-          b->reqs.push_back(r);
-          pts += r->m;
+      std::deque<Piece> rest;
+      for (const Piece& pc : admitted) {
+        if (pc.r->model == b->model && (b->pieces.empty() || pts + pc.cnt <= cfg.max_batch_points)) {
+          b->pieces.push_back(pc);
+          pts += pc.cnt;
         } else {
-          rest.push_back(r);
+          rest.push_back(pc);
         }
       }
       admitted.swap(rest);
-      launch(s, b);
+      const auto now = Clock::now();
+      for (const Piece& pc : b->pieces)
+        if (!pc.r->launched) {
+          pc.r->launched = true;
+          pc.r->t_launch = now;
+        }
+      slot[s] = b;
+      stats.batches += 1;
+      batched_requests += (int64_t)b->pieces.size();
+      to_launch.push_back(b);
+    }
+    if (!to_launch.empty()) {
+      lk.unlock();
+      for (Batch* b : to_launch) launch(b->stream, b);
+      lk.lock();
     }
     if (stop && queue.empty() && admitted.empty() && !inflight()) break;
     if (inflight()) {

@@ -37,7 +37,8 @@ def run_poisson(server, models, rate_hz, count, seed, max_points=65_536):
     """Submit `count` requests with exponential inter-arrival times at
     `rate_hz`; sizes log-uniform in [1, max_points], points uniform in the
     unit cube of the model's dimension.  Returns per-request latencies (ms),
-    total points and the wall time from first submission to last completion."""
+    total points, the wall time from first submission to last completion and
+    the per-request sizes."""
     rng = np.random.default_rng(seed)
     plan = []
     for _ in range(count):
@@ -64,10 +65,25 @@ def run_poisson(server, models, rate_hz, count, seed, max_points=65_536):
     for rid in ids:
         server.release(rid)
     pts = sum(Z.shape[0] for _, Z in plan)
-    return np.array(lat), pts, wall
+    return np.array(lat), pts, wall, np.array([Z.shape[0] for _, Z in plan])
 
 
-def latency_summary(lat, pts, wall):
-    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "requests": int(len(lat)),
-            "predictions_per_s": pts / wall, "points": int(pts), "wall_s": wall}
+SIZE_BUCKETS = ((1, 255), (256, 4095), (4096, 65536))
+
+
+def latency_summary(lat, pts, wall, sizes=None):
+    """p50 / p99 / mean latency and throughput; with the request sizes, the
+    same percentiles per size bucket (1-255, 256-4095, 4096-65536 points)."""
+    out = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_ms": float(lat.mean()), "requests": int(len(lat)),
+           "predictions_per_s": pts / wall, "points": int(pts), "wall_s": wall}
+    if sizes is not None:
+        by = {}
+        for lo, hi in SIZE_BUCKETS:
+            sel = (sizes >= lo) & (sizes <= hi)
+            if sel.any():
+                by[f"{lo}-{hi}"] = {"p50_ms": float(np.percentile(lat[sel], 50)),
+                                    "p99_ms": float(np.percentile(lat[sel], 99)),
+                                    "requests": int(sel.sum())}
+        out["by_size"] = by
+    return out

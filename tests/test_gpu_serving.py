@@ -138,3 +138,55 @@ def test_server_admission_by_memory(cuda):
     assert srv.stats()["rejected"] == 1
     srv.close()
     md.close()
+
+
+def test_split_requests_same_as_whole(cuda):
+    """With pieces of 700 points, requests of up to 3,000 points are split
+    and their pieces batched and overlapped with other requests on four
+    streams; every result equals the unsplit one-stream result bit for bit."""
+    models = _models()
+    reqs = _requests(models, 30, 8)
+    whole = fb.FmgpServer(models, streams=1)
+    ref = []
+    for j, Z in reqs:
+        rid = whole.submit(j, Z, with_nearest=True)
+        assert whole.wait(rid, 60_000)
+        Y, N = whole.result(rid)
+        ref.append((Y.copy(), N.copy()))
+    whole.close()
+    srv = fb.FmgpServer(models, streams=4, max_batch_points=700)
+    ids = [srv.submit(j, Z, with_nearest=True) for j, Z in reqs]
+    for q, rid in enumerate(ids):
+        assert srv.wait(rid, 60_000)
+        Y, N = srv.result(rid)
+        assert np.array_equal(Y, ref[q][0]) and np.array_equal(N, ref[q][1]), q
+    st = srv.stats()
+    pieces = st["batches"] * st["mean_batch_requests"]
+    assert round(pieces) == sum(-(-Z.shape[0] // 700) for _, Z in reqs) > len(reqs)
+    srv.close()
+
+
+def test_served_mixed_model_matches_the_oracle(cuda):
+    """A mixed-precision model served through the batching server, checked
+    directly against the FP64 oracle (its own neighbour rows, coefficients and
+    nearest points) within the mixed path's tolerance."""
+    import oracle
+    from gpu_helpers import MIXED_TOL, rel_rms
+    W = wl.tiny(n=3000, m=600, k=30)
+    ok, _ = kern_pair(W.kernel)
+    md = _fit(W, 30, fb.PREC_MIXED)
+    srv = fb.FmgpServer([md], streams=3, max_batch_points=128)
+    parts = np.array_split(np.arange(W.m), 7)
+    ids = [srv.submit(0, W.Z[p], with_nearest=True) for p in parts]
+    got_y, got_n = np.zeros((W.m, 1)), np.zeros(W.m, np.int32)
+    for p, rid in zip(parts, ids):
+        assert srv.wait(rid, 60_000)
+        Y, N = srv.result(rid)
+        got_y[p], got_n[p] = Y, N
+    srv.close()
+    ref_nb, _ = oracle.self_knn(W.X, 29)
+    Cr, _ = oracle.precompute(W.X, W.Y, ref_nb, 30, ok)
+    yr, nr = oracle.predict(W.X, ref_nb, Cr, ok, W.Z)
+    np.testing.assert_array_equal(got_n, nr)
+    assert rel_rms(got_y, yr) < MIXED_TOL
+    md.close()
