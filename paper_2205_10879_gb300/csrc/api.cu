@@ -272,7 +272,7 @@ static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, int mode,
   const int xb = dtype == FMGP_F64 ? 8 : 4;
   a.layout = block_layout(a.k, a.d, a.r, xb, false);
   const size_t bytes = precision == FMGP_PREC_FP64 ? a.layout.bytes_per_warp
-                                                   : mixed_bytes_per_warp(a.k, a.d, a.r);
+                                                   : mixed_bytes_per_warp(a.k, a.d, a.r, xb);
   if (bytes > 200 * 1024 || a.layout.bytes_per_warp > 200 * 1024) {
     set_error("neighbourhood k=%d d=%d r=%d needs %zu bytes of shared memory per warp", a.k, a.d,
               a.r, std::max(bytes, a.layout.bytes_per_warp));

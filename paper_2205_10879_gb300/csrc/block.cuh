@@ -52,7 +52,9 @@ int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mo
                      cudaStream_t stream, int blocks = 0);
 
 // Mixed-precision form (FP32 factor + double-float refinement + FP64 fallback).
-size_t mixed_bytes_per_warp(int k, int d, int r);
+// Shared memory of one neighbourhood in the mixed form (the one-warp layout,
+// or the CTA layout the large ones use; xbytes = 4 for FP32 inputs).
+size_t mixed_bytes_per_warp(int k, int d, int r, int xbytes);
 // panel: Cholesky panel width 4 or 8 (k <= 64 only), 0 = the default for k.
 int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps, int panel,
                     const fmgp_kernel& kern, Workspace& ws, cudaStream_t s);

@@ -26,6 +26,9 @@ namespace {
 
 constexpr int kMaxSlots = kMaxK / 32;
 constexpr int kMaxRefine = 6;
+// one-warp layouts above this size (fewer than about four neighbourhoods per
+// SM) go to the CTA-per-neighbourhood kernel
+constexpr size_t kMixedCtaAbove = 56 * 1024;
 constexpr size_t kMixedHead = 3584;  // per-CTA shared memory before the warps' areas
 static_assert(sizeof(DfConsts) <= kMixedHead, "the staged exponential table must fit the head");
 
@@ -585,6 +588,289 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
   }
 }
 
+// ---------------------------------------------------------------------------
+// One CTA per neighbourhood, for neighbourhoods whose one-warp layout would
+// leave few warps per SM (large k, or many features): the same method as
+// block_mixed_kernel with the work spread over kCtaWarps warps.
+//   assembly: all threads, one kernel entry at a time, staged rows in shared
+//     memory as FP32 (FP32 inputs: differences formed exactly by TwoSum) or
+//     as double-float pairs (FP64 inputs);
+//   FP32 Cholesky in Crout order: thread t forms row t of column j (a float4
+//     dot product over the finished prefix), two barriers per column;
+//   triangular solves: warp 0 (shuffle sweeps, as in the one-warp kernel);
+//   refinement residual: thread t forms row t as a compensated dot product;
+//   the stopping rule, the FP64 fallback list and the outputs as the one-warp
+//   kernel.
+constexpr int kCtaWarps = 8;
+
+__device__ __forceinline__ void pair_index(int p, int& a, int& b) {
+  int x = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
+  while (x * (x - 1) / 2 > p) --x;
+  while ((x + 1) * x / 2 <= p) ++x;
+  a = x;
+  b = p - x * (x - 1) / 2;
+}
+
+// a - b as an exact pair, for FP32 or double-float coordinates.
+__device__ __forceinline__ dfl coord_diff(float a, float b) { return df_two_sum(a, -b); }
+__device__ __forceinline__ dfl coord_diff(float2 a, float2 b) {
+  return df_add_fast(dfl{a.x, a.y}, dfl{-b.x, -b.y});
+}
+__device__ __forceinline__ dfl coord_diff(float2 a, float b) {
+  return df_add_fast(dfl{a.x, a.y}, dfl{-b, 0.0f});
+}
+
+template <typename A, typename B>
+__device__ __forceinline__ dfl sqdist_any(const A* a, const B* b, int d) {
+  dfl s = df_sqr(coord_diff(a[0], b[0]));
+  for (int t = 1; t < d; ++t) s = df_add_fast(s, df_sqr(coord_diff(a[t], b[t])));
+  return s;
+}
+
+struct MixedCtaLayout {
+  int ldl;  // multiple of 4, = 4 (mod 8): float4 row reads conflict-free
+  size_t off_L, off_LO, off_X, off_Y, off_V, off_R, off_inv, off_S, off_red, bytes;
+};
+
+MixedCtaLayout mixed_cta_layout(int k, int d, int r, size_t xelem) {
+  MixedCtaLayout l;
+  int ldl = (k + 3) & ~3;
+  if (ldl % 8 == 0) ldl += 4;
+  l.ldl = ldl;
+  auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  size_t o = 0;
+  l.off_L = o;   o += up((size_t)k * ldl * 4);
+  l.off_LO = o;  o += up((size_t)k * (k - 1) / 2 * 4 + 4);
+  l.off_X = o;   o += up((size_t)k * d * xelem);
+  l.off_Y = o;   o += up((size_t)k * r * 8);
+  l.off_V = o;   o += up((size_t)k * r * 8);
+  l.off_R = o;   o += up((size_t)k * r * 4);
+  l.off_inv = o; o += up((size_t)k * 4);
+  l.off_S = o;   o += up((size_t)k * 4);
+  l.off_red = o; o += up(2 * kCtaWarps * 4 + 16);
+  l.bytes = o;
+  return l;
+}
+
+template <int MODE, typename XT, int NW>
+__global__ void __launch_bounds__(NW * 32, 2) block_mixed_cta_kernel(
+    BlockArgs args, MixedArgs mx, MixedCtaLayout lay, const XT* __restrict__ Xrows) {
+  constexpr bool LOO = MODE == kModeLoocv;
+  constexpr int NT = NW * 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  DfConsts& Ks = *reinterpret_cast<DfConsts*>(smem);
+  stage_df_consts(Ks, mx.K);
+  unsigned char* base = smem + kMixedHead;
+  float* M = (float*)(base + lay.off_L);
+  float* LO = (float*)(base + lay.off_LO);
+  XT* XS = (XT*)(base + lay.off_X);
+  dfl* YS = (dfl*)(base + lay.off_Y);
+  dfl* XV = (dfl*)(base + lay.off_V);
+  float* RV = (float*)(base + lay.off_R);
+  float* invd = (float*)(base + lay.off_inv);
+  int* S = (int*)(base + lay.off_S);
+  float* red = (float*)(base + lay.off_red);
+  volatile int* flag = (int*)(red + 2 * NW);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int k = args.k, d = args.d, r = args.r, ldl = lay.ldl;
+  const KParamsDF kp = mx.kdf;
+
+  for (int64_t item = blockIdx.x; item < args.count; item += gridDim.x) {
+    __syncthreads();  // the previous neighbourhood is finished with shared memory
+    int64_t i = LOO ? args.batch[item]
+                    : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
+    const int64_t orow = MODE == kModePrecompute && args.rows ? item : i;
+    bool bad = false;
+    if (MODE != kModeMuygps && (i < 0 || i >= args.n)) { bad = true; i = 0; }
+    if (tid < k) {
+      int64_t idx = MODE != kModePrecompute ? (int64_t)args.nbr[i * args.ld + tid]
+                                            : (tid == 0 ? i : (int64_t)args.nbr[i * args.ld + tid - 1]);
+      if (idx < 0 || idx >= args.n) { bad = true; idx = 0; }
+      S[tid] = (int)idx;
+    }
+    if (tid == 0) *flag = 0;
+    bad = __syncthreads_or(bad) != 0;
+    for (int e = tid; e < k * d; e += NT) {
+      const int a = e / d, t = e - a * d;
+      XS[e] = Xrows[(int64_t)S[a] * d + t];
+    }
+    for (int e = tid; e < k * r; e += NT) {
+      const int a = e / r, c = e - a * r;
+      const float2 y = mx.Ydf[(int64_t)S[a] * r + c];
+      YS[e] = dfl{y.x, y.y};
+    }
+    __syncthreads();
+    // assembly: entry p = a(a-1)/2 + b (a > b) per thread
+    const int npairs = k * (k - 1) / 2;
+    for (int p = tid; p < npairs; p += NT) {
+      int a, b;
+      pair_index(p, a, b);
+      const dfl kv = corr_df(kp, sqdist_any(XS + a * d, XS + b * d, d), Ks);
+      M[a * ldl + b] = kv.hi;
+      M[b * ldl + a] = kv.hi;
+      LO[p] = kv.lo;
+    }
+    if (tid < k) M[tid * ldl + tid] = kp.diag.hi;
+    __syncthreads();
+    // FP32 Cholesky, Crout order: thread t forms row t of column j
+    for (int j = 0; j < k; ++j) {
+      float dd = 0.0f;
+      if (tid >= j && tid < k) {
+        const float* lr = M + tid * ldl;
+        const float* lj = M + j * ldl;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int p = 0;
+        for (; p + 4 <= j; p += 4) {
+          const float4 u = *reinterpret_cast<const float4*>(lr + p);
+          const float4 v = *reinterpret_cast<const float4*>(lj + p);
+          s0 = fmaf(u.x, v.x, s0); s1 = fmaf(u.y, v.y, s1);
+          s2 = fmaf(u.z, v.z, s2); s3 = fmaf(u.w, v.w, s3);
+        }
+        for (; p < j; ++p) s0 = fmaf(lr[p], lj[p], s0);
+        dd = (s0 + s1) + (s2 + s3);
+      }
+      if (tid == j) {
+        const float v = M[j * ldl + j] - dd;
+        if (!(v > 0.0f)) {
+          *flag = 1;
+        } else {
+          const float iv = rsqrtf(v);
+          M[j * ldl + j] = v * iv;
+          invd[j] = iv;
+        }
+      }
+      __syncthreads();
+      if (*flag) break;
+      if (tid > j && tid < k) M[tid * ldl + j] = (M[tid * ldl + j] - dd) * invd[j];
+      __syncthreads();
+    }
+    bool ok = (*flag == 0) && !bad;
+    if (ok) {
+      for (int e = tid; e < k * r; e += NT) RV[e] = YS[e].hi;
+      __syncthreads();
+      if (wid == 0) solve_f32(M, ldl, invd, RV, k, r, lane);
+      __syncthreads();
+      for (int e = tid; e < k * r; e += NT) XV[e] = dfl{RV[e], 0.0f};
+      __syncthreads();
+      float prev = 1.0f;
+      bool conv = false;
+      for (int step = 1; step <= kMaxRefine; ++step) {
+        // residual y - K x, row `tid`, compensated (Dot2) as in the one-warp kernel
+        if (tid < k) {
+          const int row = tid;
+          const int rb = row * (row - 1) / 2;
+          for (int c = 0; c < r; ++c) {
+            const dfl a0 = df_add(YS[row * r + c], df_neg(df_mul(kp.diag, XV[row * r + c])));
+            float pp = a0.hi, ee = a0.lo;
+            int cb = 0;
+            for (int b = 0; b < k; ++b) {
+              if (b != row) {
+                const dfl xb = XV[b * r + c];
+                const bool below = b < row;
+                const float hi = below ? M[b * ldl + row] : M[row * ldl + b];
+                const float lo = below ? LO[rb + b] : LO[cb + row];
+                const float h = __fmul_rn(hi, xb.hi);
+                const float hr = __fmaf_rn(hi, xb.hi, -h);
+                const float t = __fadd_rn(pp, -h);
+                const float bv = __fsub_rn(t, pp);
+                const float q = __fadd_rn(__fsub_rn(pp, __fsub_rn(t, bv)), __fsub_rn(-h, bv));
+                pp = t;
+                float es = __fsub_rn(ee, hr);
+                es = __fadd_rn(es, q);
+                es = __fmaf_rn(-hi, xb.lo, es);
+                ee = __fmaf_rn(-lo, xb.hi, es);
+              }
+              cb += b;
+            }
+            RV[row * r + c] = __fadd_rn(pp, ee);
+          }
+        }
+        __syncthreads();
+        if (wid == 0) solve_f32(M, ldl, invd, RV, k, r, lane);
+        __syncthreads();
+        float dmax = 0.0f, xmax = 0.0f;
+        for (int e = tid; e < k * r; e += NT) {
+          const dfl v = df_add_f(XV[e], RV[e]);
+          XV[e] = v;
+          dmax = fmaxf(dmax, fabsf(RV[e]));
+          xmax = fmaxf(xmax, fabsf(v.hi));
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+          dmax = fmaxf(dmax, __shfl_xor_sync(kFull, dmax, off));
+          xmax = fmaxf(xmax, __shfl_xor_sync(kFull, xmax, off));
+        }
+        if (lane == 0) {
+          red[wid] = dmax;
+          red[NW + wid] = xmax;
+        }
+        __syncthreads();
+        dmax = 0.0f;
+        xmax = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          dmax = fmaxf(dmax, red[w]);
+          xmax = fmaxf(xmax, red[NW + w]);
+        }
+        __syncthreads();  // red is rewritten by the next step
+        const float ratio = xmax > 0.0f ? dmax / xmax : 0.0f;
+        if (ratio <= 1e-7f || ratio * ratio <= 1e-6f * prev) { conv = true; break; }
+        if (step >= 2 && ratio > 0.5f * prev) break;  // corrections no longer contract
+        prev = ratio;
+      }
+      ok = conv;
+    }
+    if (!ok) {
+      if (tid == 0) {
+        const int pos = atomicAdd(mx.fb_count, 1);
+        mx.fb_list[pos] = (int)item;
+      }
+    } else if (MODE == kModePrecompute) {
+      float2* Ci = (float2*)args.C + orow * (int64_t)k * r;
+      for (int e = tid; e < k * r; e += NT) {
+        const dfl cv = df_mul(XV[e], kp.inv_var);
+        Ci[e] = make_float2(cv.hi, cv.lo);
+      }
+      if (args.status && tid == 0) args.status[orow] = FMGP_BLOCK_OK;
+    } else {
+      // cross-covariance of the query point with row `lane` (+32 s) in warp 0
+      if (wid == 0) {
+        constexpr int NSL = kMaxK / 32;
+        dfl kx[NSL];
+        const float2* xi = MODE == kModeMuygps ? args.Zdf + i * d : mx.Xdf + i * d;
+#pragma unroll
+        for (int s2 = 0; s2 < NSL; ++s2) {
+          const int a = lane + 32 * s2;
+          kx[s2] = dfl{0.0f, 0.0f};
+          if (a < k) kx[s2] = corr_df(kp, sqdist_any(xi, XS + a * d, d), Ks);
+        }
+        dfl e2 = {0.0f, 0.0f};
+        for (int c = 0; c < r; ++c) {
+          dfl acc = {0.0f, 0.0f};
+#pragma unroll
+          for (int s2 = 0; s2 < NSL; ++s2) {
+            const int a = lane + 32 * s2;
+            if (a < k) acc = df_add(acc, df_mul(kx[s2], XV[a * r + c]));
+          }
+#pragma unroll
+          for (int off = 16; off; off >>= 1) {
+            const dfl o = {__shfl_xor_sync(kFull, acc.hi, off), __shfl_xor_sync(kFull, acc.lo, off)};
+            acc = df_add(acc, o);
+          }
+          if (MODE == kModeMuygps) {
+            if (lane == 0) args.yhat[i * r + c] = df_to_double(acc);
+          } else {
+            const float2 y = mx.Ydf[i * r + c];
+            const dfl e = df_add(dfl{y.x, y.y}, df_neg(acc));
+            e2 = df_add_fast(e2, df_sqr(e));
+          }
+        }
+        if (lane == 0 && MODE == kModeLoocv) args.resid[item] = df_to_double(e2);
+      }
+    }
+  }
+}
+
 // A5 in DF: lane a evaluates sigma^2 phi(||z - x_{S[a]}||) in DF; the k-term
 // dot products with C[j*] are reduced by a fixed xor-butterfly in DF.
 __global__ void __launch_bounds__(256) gather_dot_mixed_kernel(
@@ -675,7 +961,23 @@ int to_df(const void* in, bool f64, int64_t count, float2* out, cudaStream_t s) 
   return FMGP_OK;
 }
 
-size_t mixed_bytes_per_warp(int k, int d, int r) { return mixed_layout(k, d, r).bytes; }
+size_t mixed_bytes_per_warp(int k, int d, int r, int xbytes) {
+  const size_t w = mixed_layout(k, d, r).bytes;
+  return w > kMixedCtaAbove ? mixed_cta_layout(k, d, r, xbytes == 4 ? 4 : 8).bytes : w;
+}
+
+// FP64 fallback over the blocks the mixed kernels listed (count read on the device).
+static int mixed_fallback(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mode, bool loo,
+                          int* fb_list, int* fb_count, cudaStream_t s) {
+  BlockArgs f = a;
+  f.list = fb_list;
+  f.list_count = fb_count;
+  f.c_df = !loo;
+  f.layout = block_layout(a.k, a.d, a.r, dtype == FMGP_F64 ? 8 : 4, false);
+  int fw = (int)((200 * 1024) / f.layout.bytes_per_warp);
+  fw = fw > 4 ? 4 : (fw < 1 ? 1 : fw);
+  return launch_block_f64(f, X, dtype, mode, fw, s, num_sms() * 2);
+}
 
 int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int warps, int panel,
                     const fmgp_kernel& kern, Workspace& ws, cudaStream_t s) {
@@ -697,6 +999,35 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   mx.K = df_consts();
   mx.kdf = make_kparams_df(a.kp, kern);
   const MixedLayout lay = mixed_layout(a.k, a.d, a.r);
+  if (lay.bytes > kMixedCtaAbove) {
+    // few one-warp neighbourhoods would fit an SM: one CTA per neighbourhood
+    const bool f32 = dtype == FMGP_F32;
+    const MixedCtaLayout cl = mixed_cta_layout(a.k, a.d, a.r, f32 ? 4 : 8);
+    const size_t smem = kMixedHead + cl.bytes;
+    auto pick = [&](auto xt) {
+      using XT = typename decltype(xt)::type;
+      return mode == kModeLoocv    ? block_mixed_cta_kernel<kModeLoocv, XT, kCtaWarps>
+             : mode == kModeMuygps ? block_mixed_cta_kernel<kModeMuygps, XT, kCtaWarps>
+                                   : block_mixed_cta_kernel<kModePrecompute, XT, kCtaWarps>;
+    };
+    struct TF { using type = float; };
+    struct TD { using type = float2; };
+    const void* fn = f32 ? (const void*)pick(TF{}) : (const void*)pick(TD{});
+    const int fit = active_ctas(fn, kCtaWarps * 32, smem);
+    if (!fit) {
+      set_error("neighbourhood blocks of %zu bytes do not fit an SM", cl.bytes);
+      return FMGP_EUNSUPPORTED;
+    }
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit * 8));
+    FMGP_CUDA_TRY(ensure_smem(fn, smem));
+    if (f32)
+      FMGP_LAUNCH(pick(TF{})<<<blocks, kCtaWarps * 32, smem, s>>>(a, mx, cl, (const float*)X));
+    else
+      FMGP_LAUNCH(pick(TD{})<<<blocks, kCtaWarps * 32, smem, s>>>(a, mx, cl, (const float2*)Xdf));
+    FMGP_CUDA_TRY(cudaGetLastError());
+    return mixed_fallback(a, X, dtype, mode, loo, fb_list, fb_count, s);
+  }
   // rows per lane (k <= 32 S) and the Cholesky panel width are compile-time:
   // 8 columns for k <= 32 and 4 above by default; for k <= 64 the other
   // width is instantiated too (panel = 4 or 8 picks it, 0 the default)
@@ -747,15 +1078,7 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
   FMGP_LAUNCH(kern_fn<<<blocks, warps * 32, smem, s>>>(a, mx, lay));
   FMGP_CUDA_TRY(cudaGetLastError());
-  // FP64 fallback over the listed blocks (count read on the device)
-  BlockArgs f = a;
-  f.list = fb_list;
-  f.list_count = fb_count;
-  f.c_df = !loo;
-  f.layout = block_layout(a.k, a.d, a.r, dtype == FMGP_F64 ? 8 : 4, false);
-  int fw = (int)((200 * 1024) / f.layout.bytes_per_warp);
-  fw = fw > 4 ? 4 : (fw < 1 ? 1 : fw);
-  return launch_block_f64(f, X, dtype, mode, fw, s, num_sms() * 2);
+  return mixed_fallback(a, X, dtype, mode, loo, fb_list, fb_count, s);
 }
 
 int gather_dot_mixed(const void* X, fmgp_dtype dtype, int64_t n, int d, const int32_t* nbr, int ld,

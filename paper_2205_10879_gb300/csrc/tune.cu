@@ -104,7 +104,7 @@ extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const d
   a.kp = make_kparams(*kernel);
   a.layout = block_layout(k, d, r, dtype == FMGP_F64 ? 8 : 4, false);
   const size_t bytes = precision == FMGP_PREC_FP64 ? a.layout.bytes_per_warp
-                                                   : mixed_bytes_per_warp(k, d, r);
+                                                   : mixed_bytes_per_warp(k, d, r, dtype == FMGP_F64 ? 8 : 4);
   int best = 0, best_panel = 0;
   float best_ms = 1e30f;
   // the mixed kernel's Cholesky panel width: both instantiated widths for k <= 64

@@ -389,3 +389,36 @@ def test_grid_knn_visit_counters(cuda):
     assert torch.equal(nbr, ref)
     assert nq == W.n
     assert 29 * nq <= keys <= exam <= W.n * (W.n - 1)
+
+
+@pytest.mark.parametrize("d,dtype", [(2, np.float64), (64, np.float32)])
+def test_mixed_cta_kernel_all_modes(cuda, d, dtype):
+    """Neighbourhoods of k = 100 (too large for one warp's share of an SM): the
+    mixed form runs one CTA per neighbourhood.  Precompute, prediction, LOOCV
+    and plain MuyGPs prediction, r = 3, against the oracle's own tables."""
+    rng = np.random.default_rng(d)
+    n, m, k = 4_000, 300, 100
+    X = rng.random((n, d)).astype(dtype)
+    Z = rng.random((m, d)).astype(dtype)
+    Xo, Zo = X.astype(np.float64), Z.astype(np.float64)
+    Y = np.stack([np.sin(3 * Xo[:, 0]), np.cos(2 * Xo[:, -1]), Xo[:, 0] * Xo[:, -1]], axis=1)
+    spec = wl.KernelSpec("matern", 1.5, 0.35 * np.sqrt(d), 1.0, 1e-3)
+    ok, gk = kern_pair(spec)
+    Xd, Yd, Zd = dev(X), dev(Y), dev(Z)
+    nbr, _ = fb.fmgp_build_knn(Xd, k)
+    nb, _ = oracle.self_knn(Xo, k)
+    np.testing.assert_array_equal(nbr.cpu().numpy(), nb)
+    C, st = fb.fmgp_precompute(Xd, Yd, nbr, k, gk, fb.PREC_MIXED)
+    Cr, _ = oracle.precompute(Xo, Y, nb, k, ok)
+    assert rel_rms(coeffs_to_f64(C, fb.PREC_MIXED), Cr) < 1e-6
+    yh, _ = fb.fmgp_predict(Xd, nbr, C, k, gk, Zd, fb.PREC_MIXED)
+    yr, _ = oracle.predict(Xo, nb, Cr, ok, Zo)
+    assert rel_rms(yh.cpu().numpy(), yr) < MIXED_TOL
+    batch = np.arange(0, n, 7).astype(np.int64)
+    Q, res = fb.fmgp_loocv_objective(Xd, Yd, nbr, k, dev(batch), gk, fb.PREC_MIXED)
+    Qr, resr = oracle.loocv(Xo, Y, nb, k, batch, ok)
+    assert abs(Q - Qr) / abs(Qr) < MIXED_TOL
+    assert rel_rms(res.cpu().numpy(), resr) < MIXED_TOL
+    ym, _ = fb.fmgp_muygps_predict(Xd, Yd, Zd, k, gk, fb.PREC_MIXED)
+    ymr, _ = oracle.muygps_predict(Xo, Y, Zo, k, ok)
+    assert rel_rms(ym.cpu().numpy(), ymr) < MIXED_TOL
