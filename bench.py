@@ -13,8 +13,15 @@ are reported beside it.  Inputs are resident in HBM before timing; L2 (129 MB)
 is flushed between timed steps by writing a 512 MB buffer.  e2e repeats the
 step from pinned host buffers with the copies inside the timed region.
 
---impl reference times the FP64 CPU oracle (OpenMP, all host cores) on a
-bounded sample of the same workload and extrapolates to the same metric.
+--workload selects another configuration: tiny (n = 2,000, m = 500, k = 30,
+Matern 3/2, the oracle's sanity case), large (n = 10^7, m = 10^6, d = 3, k = 64,
+Matern 5/2, nugget 1e-5), highdim (the 784-D ten-response leg alone),
+highdim-knn (its kNN table alone) or nearest-d64 (tensor-core nearest-point
+lookup).
+
+--impl reference times the FP64 CPU oracle (OpenMP, all host cores): one
+whole pass over the workload per step (for the 10^7-point workload a bounded
+sample of rows, extrapolated per point).
 """
 import argparse
 import json
@@ -52,7 +59,7 @@ def parse():
     p.add_argument("--k", type=int, default=50)
     p.add_argument("--b", type=int, default=10_000)
     p.add_argument("--nu", type=float, default=1.5)
-    p.add_argument("--workload", default="spatial", choices=["spatial", "large", "highdim", "highdim-knn", "nearest-d64"])
+    p.add_argument("--workload", default="spatial", choices=["spatial", "tiny", "large", "highdim", "highdim-knn", "nearest-d64"])
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-muygps", action="store_true")
     p.add_argument("--no-highdim", action="store_true")
@@ -88,6 +95,10 @@ def max_over_ranks(value, device=None):
 
 
 def workload_config(a):
+    if a.workload == "tiny":
+        return {"workload": "tiny-2d", "n_train": 2_000, "m_test": 500, "d": 2, "k": 30, "r": 1,
+                "kernel": "matern nu=1.5 rho=0.1 tau2=1e-4", "loocv_batch": 500,
+                "l2": "flushed between steps (512 MB write)"}
     if a.workload == "large":
         return {"workload": "large-3d", "n_train": 10_000_000, "m_test": 1_000_000, "d": 3,
                 "k": 64, "r": 1, "kernel": "matern nu=2.5 rho=0.1 tau2=1e-5", "loocv_batch": 10_000,
@@ -101,6 +112,8 @@ def make_workload(a):
     from paper_2205_10879_gb300 import workloads as wl
     if a.workload == "large":
         return wl.large()
+    if a.workload == "tiny":
+        return wl.tiny(n=2_000, m=500, k=30, b=500)
     return wl.spatial(n=a.n, m=a.m, k=a.k, nu=a.nu, b=a.b)
 
 
@@ -283,10 +296,10 @@ def run_ours(a):
     if not a.no_autotune:
         fb.fmgp_build_knn(X, kq, nbr_out=nbr)
         gt = fb.fmgp_autotune_knn(X, kq)
-        fb.fmgp_autotune_precompute(X, Y, nbr, k, gk, prec, sample_rows=min(n, 40_000))
+        fb.fmgp_autotune_precompute(X, Y, nbr, k, gk, prec, sample_rows=min(n, 200_000))
         w, pw = fb.autotune_choice(k, W.d, 1, prec, X.dtype)
         tuned = {"grid_target": gt if gt > 0 else None, "block_warps": w,
-                 "cholesky_panel": pw or None, "sample_rows": min(n, 40_000)}
+                 "cholesky_panel": pw or None, "sample_rows": min(n, 200_000)}
     C = torch.empty(fb.coeff_shape(n, k, 1, prec),
                     dtype=torch.float64 if prec == fb.PREC_FP64 else torch.float32, device=dev)
     st = torch.empty(n, dtype=torch.int8, device=dev)
@@ -899,7 +912,7 @@ def oracle_sample(W, a, samples):
     training rows, 1-NN + prediction for s2 test points, LOOCV for s3 batch
     points; extrapolate each phase to the full workload."""
     import oracle
-    s1, s2, s3 = samples
+    s1, s2, s3 = min(samples[0], W.n), min(samples[1], W.m), min(samples[2], samples[0], W.n)
     rng = np.random.default_rng(7)
     ok = oracle.kernel(W.kernel.kind, W.kernel.nu, W.kernel.length_scale, W.kernel.variance,
                        W.kernel.nugget)

@@ -106,17 +106,22 @@ __device__ __forceinline__ dfl df_sqrt(dfl x) {
 }
 
 // Tables of the DF exponential, filled on the host from FP64 values (each
-// entry the DF rounding of the FP64 exp): e4[i] = exp(-i/4) for i < 352 and
-// e256[i] = exp(-i/256) for i < 64, so exp(-j/256) = e4[j >> 6] * e256[j & 63].
+// entry the DF rounding of the FP64 exp): e4[i] = exp(-i/4) for i < 128 and
+// e256[i] = exp(-i/256) for i < 64, so exp(-j/256) = e4[j >> 6] * e256[j & 63]
+// for j/256 < 32.
 constexpr int kDfExpRange = 88;  // arguments at or above give 0 (exp(-88) < FLT_MIN)
+constexpr int kDfExpTable = 32;  // arguments below use the tables
 struct DfConsts {
-  float2 e4[kDfExpRange * 4];
+  float2 e4[kDfExpTable * 4];
   float2 e256[64];
 };
 
-// exp(-a) for a >= 0 (DF), relative error below 1e-13 (the table entries
-// and the two DF products contribute a few 2^-47 each, the series about
-// 1e-15) where the result is a normal FP32 pair (above ~1e-30):
+// exp(-a) for a >= 0 (DF).  For a < 32 the relative error is below 1e-13
+// (the table entries and the two DF products contribute a few 2^-47 each,
+// the series about 1e-15); from 32 on, where exp(-a) < 1.3e-14, the value is
+// the FP32 exp2f of -a log2(e) (relative error below 2e-5 from the FP32
+// product and the dropped a.lo, absolute below 5e-19),
+// which keeps every kernel entry's absolute error far below 1e-13.  For a < 32:
 //   j = floor(256 a.hi), and a.hi - j/256 in [0, 1/256) exactly (the
 //   fractional part of the exactly scaled 256 a.hi); s = that + a.lo,
 //   renormalised by TwoSum so that s.lo is below 2^-32;
@@ -128,8 +133,11 @@ struct DfConsts {
 // early return, so that several evaluations can interleave.
 __device__ __forceinline__ dfl df_exp_neg(dfl a, const DfConsts& K) {
   const bool in_range = a.hi < (float)kDfExpRange;  // false for NaN
-  const float ah = in_range ? fmaxf(a.hi, 0.0f) : 0.0f;      // table indices stay in range
-  const float al = in_range ? a.lo : 0.0f;
+  const bool tail = a.hi >= (float)kDfExpTable;
+  float tail_v = 0.0f;
+  if (tail && in_range) tail_v = exp2f(-1.44269504f * a.hi);  // rare: a branch, not a select
+  const float ah = in_range && !tail ? fmaxf(a.hi, 0.0f) : 0.0f;  // table indices stay in range
+  const float al = in_range && !tail ? a.lo : 0.0f;
   const int j = (int)__fmul_rz(ah, 256.0f);                  // ah * 256 is exact
   const float sh = __fmaf_rn((float)j, -0.00390625f, ah);   // exact: frac(256 ah) / 256
   const dfl sv = df_two_sum(sh, al);                         // s, |sv.lo| <= 2^-33
@@ -146,7 +154,8 @@ __device__ __forceinline__ dfl df_exp_neg(dfl a, const DfConsts& K) {
   const dfl e = df_quick(t.hi, lo);
   const float2 u = K.e4[j >> 6], w = K.e256[j & 63];
   const dfl v = df_mul(df_mul(dfl{u.x, u.y}, dfl{w.x, w.y}), e);
-  return {in_range ? v.hi : 0.0f, in_range ? v.lo : 0.0f};
+  if (!in_range) return {0.0f, 0.0f};
+  return tail ? dfl{tail_v, 0.0f} : v;
 }
 
 __device__ __forceinline__ double df_to_double(dfl x) { return (double)x.hi + (double)x.lo; }

@@ -29,7 +29,7 @@ constexpr int kMaxRefine = 6;
 // one-warp layouts above this size (fewer than about four neighbourhoods per
 // SM) go to the CTA-per-neighbourhood kernel
 constexpr size_t kMixedCtaAbove = 56 * 1024;
-constexpr size_t kMixedHead = 3584;  // per-CTA shared memory before the warps' areas
+constexpr size_t kMixedHead = 1536;  // per-CTA shared memory before the warps' areas
 static_assert(sizeof(DfConsts) <= kMixedHead, "the staged exponential table must fit the head");
 
 // The mixed kernels work with correlations phi (sigma^2 factored out): the
@@ -71,7 +71,7 @@ const DfConsts& df_consts() {
       const float hi = (float)v;
       dst = make_float2(hi, (float)(v - (double)hi));
     };
-    for (int i = 0; i < kDfExpRange * 4; ++i) put(c.e4[i], exp(-(double)i / 4.0));
+    for (int i = 0; i < kDfExpTable * 4; ++i) put(c.e4[i], exp(-(double)i / 4.0));
     for (int i = 0; i < 64; ++i) put(c.e256[i], exp(-(double)i / 256.0));
   });
   return c;
@@ -80,7 +80,7 @@ const DfConsts& df_consts() {
 // Stage the exponential's tables in shared memory (lanes index them with
 // different entries, which the constant bank would serialise).
 __device__ __forceinline__ void stage_df_consts(DfConsts& dst, const DfConsts& src) {
-  for (int t = threadIdx.x; t < kDfExpRange * 4; t += blockDim.x) dst.e4[t] = src.e4[t];
+  for (int t = threadIdx.x; t < kDfExpTable * 4; t += blockDim.x) dst.e4[t] = src.e4[t];
   for (int t = threadIdx.x; t < 64; t += blockDim.x) dst.e256[t] = src.e256[t];
 }
 
