@@ -513,8 +513,8 @@ const char* fmgp_last_error(void);
 const char* fmgp_version(void);
 
 /*
- * Launch-shape and path controls (results never depend on them) and two
- * checking / testing switches (check_finite, fail_alloc_after):
+ * Launch-shape and path controls (results never depend on them) and three
+ * checking / testing switches (check_finite, fail_alloc_after, tc_wait_ns):
  *   "grid_target"  mean training points per grid cell of the d <= 3 search (default 12)
  *   "block_warps"  warps per CTA of the neighbourhood kernels, 0 = automatic
  *   "block_panel"  Cholesky panel width of the mixed neighbourhood kernel for
@@ -543,6 +543,13 @@ const char* fmgp_version(void);
  *                  asynchronous; non-finite inputs then give unspecified
  *                  values, never an out-of-bounds access).  Kernel
  *                  hyperparameters are always checked on the host.
+ *   "tc_wait_ns"   limit in ns of the waits in the main loop of the tensor-core
+ *                  distance kernel (0 = 2 s, default).  A wait that runs out
+ *                  makes the kernel stop, wait (up to 2 s) for its own copies
+ *                  and matrix operations in flight, release its tensor memory
+ *                  and report the abort; every query of that call is then
+ *                  answered by the exhaustive exact scan (same table).  For
+ *                  tests of that path.
  *   "fail_alloc_after" failure injection for tests: the next N workspace
  *                  allocations succeed and every later one fails as if the
  *                  device were out of memory (FMGP_ENOMEM); -1 = off (default)

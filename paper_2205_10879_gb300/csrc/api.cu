@@ -505,6 +505,9 @@ int fmgp_tune_set(const char* key, double value) {
   } else if (k == "tc_oversample") {
     if (!(value >= 2 && value <= 4)) { set_error("tc_oversample out of range [2, 4]"); return FMGP_EINVAL; }
     tp.tc_oversample = (int)value;
+  } else if (k == "tc_wait_ns") {
+    if (!(value >= 0 && value <= 2e9)) { set_error("tc_wait_ns out of range [0, 2e9]"); return FMGP_EINVAL; }
+    tp.tc_wait_ns = (int64_t)value;
   } else if (k == "check_finite") {
     tp.check_finite = value != 0.0;
   } else if (k == "fail_alloc_after") {
@@ -535,6 +538,7 @@ double fmgp_tune_get(const char* key) {
   if (k == "tc_chunk_queries") return (double)tp.tc_chunk_queries;
   if (k == "fail_alloc_after") return (double)g_alloc_budget.load();
   if (k == "check_finite") return tp.check_finite ? 1.0 : 0.0;
+  if (k == "tc_wait_ns") return (double)tp.tc_wait_ns;
   return -1.0;
 }
 

@@ -15,6 +15,7 @@ struct TuneParams {
   int tc_fused_r = 0;            // per-range list length of the fused selection (0 = by kq)
   int64_t tc_chunk_queries = 0;  // queries per chunk of the fused selection (0 = ~1 GB of lists)
   bool check_finite = false;     // entry points scan X, Y, Z for NaN / Inf first (synchronising)
+  int64_t tc_wait_ns = 0;        // limit of the tensor-core kernel's main-loop waits (0 = 2 s)
   bool count_visits = false;     // grid kNN counts candidates examined and FP64 keys formed
 };
 

@@ -77,9 +77,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Wait for the phase of `parity` to complete; gives up after ~2 s or when
+// Limit of the bounded waits after an abort (the drains below), in ns.
+constexpr uint64_t kDrainWaitNs = 2000000000ull;
+
+// Wait for the phase of `parity` to complete; gives up after limit_ns or when
 // another role has raised the abort flag.  Returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          uint64_t limit_ns = kDrainWaitNs) {
   const uint32_t addr = smem_u32(bar);
   const uint64_t t0 = global_timer();
   for (;;) {
@@ -90,7 +94,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
         : "=r"(done) : "r"(addr), "r"(parity) : "memory");
     if (done) return true;
     if (abort && *abort) return false;
-    if (global_timer() - t0 > 2000000000ull) return false;
+    if (global_timer() - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
     const float* __restrict__ qnorm, const float* __restrict__ xnorm, int qb0, int tile0,
     int tile_end, int tpc, int k_chunks, int64_t ld_out, float* __restrict__ out,
     int64_t n_valid, int self, float* __restrict__ pkey, int32_t* __restrict__ pidx,
-    int* __restrict__ err) {
+    int* __restrict__ err, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + (size_t)kStages * kStageBytes);
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
         for (int kc = 0; kc < k_chunks; ++kc, ++it) {
           const int s = it % kStages;
           const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, abort)) { *abort = 1; break; }
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort, wait_ns)) { *abort = 1; break; }
           unsigned char* a = smem + (size_t)s * kStageBytes;
           mbar_expect_tx(&full[s], kStageBytes);
           tma_load_2d(a, &tmQ, &full[s], kc * kTK, qb * kTM);
@@ -332,13 +336,13 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
       for (int t = 0; t < n_tiles && !*abort; ++t) {
         const int b = t & 1;
         const uint32_t u = (uint32_t)(t >> 1);
-        if (!mbar_wait(&tempty[b], (u & 1u) ^ 1u, abort)) { *abort = 1; break; }
+        if (!mbar_wait(&tempty[b], (u & 1u) ^ 1u, abort, wait_ns)) { *abort = 1; break; }
         tc_fence_after();
         const uint32_t dacc = tmem + (uint32_t)(b * kTN);
         for (int kc = 0; kc < k_chunks; ++kc, ++it) {
           const int s = it % kStages;
           const uint32_t ph = (uint32_t)(it / kStages) & 1u;
-          if (!mbar_wait(&full[s], ph, abort)) { *abort = 1; break; }
+          if (!mbar_wait(&full[s], ph, abort, wait_ns)) { *abort = 1; break; }
           tc_fence_after();
           const uint32_t a = smem_u32(smem + (size_t)s * kStageBytes);
           const uint64_t ad = sw128_desc(a), bd = sw128_desc(a + kABytes);
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
     for (int t = 0; t < n_tiles; ++t) {
       const int b = t & 1;
       const uint32_t u = (uint32_t)(t >> 1);
-      const bool ok = mbar_wait(&tfull[b], u & 1u, abort);
+      const bool ok = mbar_wait(&tfull[b], u & 1u, abort, wait_ns);
       if (!__all_sync(kFull, ok)) { *abort = 1; break; }
       tc_fence_after();
       const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN);
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(R > 0 ? kTcSelThreads : kTcThreads, 1) tc_dist
     for (int t = 0; t < n_tiles; ++t) {
       const int b = t & 1;
       const uint32_t u = (uint32_t)(t >> 1);
-      if (!mbar_wait(&tfull[b], u & 1u, abort)) { *abort = 1; break; }
+      if (!mbar_wait(&tfull[b], u & 1u, abort, wait_ns)) { *abort = 1; break; }
       tc_fence_after();
       for (int c = 0; c < kTN / 32; ++c) {
         uint32_t v[32];
@@ -897,6 +901,10 @@ __global__ void __launch_bounds__(kRrWarps * 32, 1) rerank_kernel(
   }
   const float U = ub.full() ? __uint_as_float((unsigned int)ub.tk) : __int_as_float(0x7f800000);
   __syncwarp();
+  // Below, a slot can hold a candidate only if a < nsurv (the survivors were
+  // packed to the front): testing lo <= U alone would admit the empty slots
+  // (lo = U = +inf) when fewer than kq candidates survive, e.g. after a
+  // distance pass that gave up.
   // Without requested distances, FP64 keys are needed only when the FP32
   // intervals leave membership or order open.  If exactly kq candidates have
   // lower bound <= U (the kq-th smallest upper bound) and, ordered by
@@ -905,14 +913,14 @@ __global__ void __launch_bounds__(kRrWarps * 32, 1) rerank_kernel(
     int cnt = 0;
 #pragma unroll
     for (int g = 0; g < S; ++g)
-      cnt += __popc(__ballot_sync(kFull, 32 * g + lane < L && lo[g] <= U));
+      cnt += __popc(__ballot_sync(kFull, 32 * g + lane < nsurv && lo[g] <= U));
     if (cnt == kq) {
       WarpTopK<KS> ord;
       ord.init(kq);
 #pragma unroll
       for (int g = 0; g < S; ++g) {
         const int a = 32 * g + lane;
-        const bool in = a < L && lo[g] <= U;
+        const bool in = a < nsurv && lo[g] <= U;
         const float mid = 0.5f * lo[g] + 0.5f * hi[g];
         ord.offer(in ? (unsigned long long)__float_as_uint(mid) : ~0ull, in ? a : INT_MAX, lane);
       }
@@ -964,13 +972,13 @@ __global__ void __launch_bounds__(kRrWarps * 32, 1) rerank_kernel(
     int cnt = 0;
 #pragma unroll
     for (int g = 0; g < S; ++g)
-      cnt += __popc(__ballot_sync(kFull, 32 * g + lane < L && lo[g] <= U));
+      cnt += __popc(__ballot_sync(kFull, 32 * g + lane < nsurv && lo[g] <= U));
     if (cnt <= 32) {
       int my_slot = -1, base = 0;
 #pragma unroll
       for (int g = 0; g < S; ++g) {
         const int a = 32 * g + lane;
-        const bool in = a < L && lo[g] <= U;
+        const bool in = a < nsurv && lo[g] <= U;
         const unsigned bal = __ballot_sync(kFull, in);
         const int pos = base + __popc(bal & ((1u << lane) - 1u));
         // member with position pos is held by lane pos
@@ -1037,7 +1045,7 @@ __global__ void __launch_bounds__(kRrWarps * 32, 1) rerank_kernel(
 #pragma unroll
   for (int g = 0; g < S; ++g) {
     const int a = 32 * g + lane;
-    const bool take = a < L && lo[g] <= U;
+    const bool take = a < nsurv && lo[g] <= U;
     const unsigned bal = __ballot_sync(kFull, take);
     const int cj = take ? keep[a] : 0;
     __syncwarp();
@@ -1283,6 +1291,10 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
   FMGP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   FMGP_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(int), s));
   const int sblocks = ceil_div(m * 32, 256);
+  // limit of the distance kernel's main-loop waits (the drains after an
+  // abort keep kDrainWaitNs)
+  const uint64_t main_wait = tune_params().tc_wait_ns > 0 ? (uint64_t)tune_params().tc_wait_ns
+                                                          : kDrainWaitNs;
   const int R = tc_fused_r(kq);
   if (R > 0) {
     // candidate ranges per query block: the split with the shortest
@@ -1327,15 +1339,15 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
       if (R == 8)
         FMGP_LAUNCH(tc_dist_kernel<8><<<grid, kTcSelThreads, kTcSelSmem, s>>>(
             tmQ, tmX, qn2, xn2, (int)qb0, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0,
-            pkey, pidx, err));
+            pkey, pidx, err, main_wait));
       else if (R == 16)
         FMGP_LAUNCH(tc_dist_kernel<16><<<grid, kTcSelThreads, kTcSelSmem, s>>>(
             tmQ, tmX, qn2, xn2, (int)qb0, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0,
-            pkey, pidx, err));
+            pkey, pidx, err, main_wait));
       else
         FMGP_LAUNCH(tc_dist_kernel<32><<<grid, kTcSelThreads, kTcSelSmem, s>>>(
             tmQ, tmX, qn2, xn2, (int)qb0, 0, n_tiles, tpc, k_chunks, 0, nullptr, n, self ? 1 : 0,
-            pkey, pidx, err));
+            pkey, pidx, err, main_wait));
       const int cblocks = (int)ceil_div(mc * 32, 256);
       int32_t* cc = cand + q0 * L;
       float* ck = ckey + q0 * L;
@@ -1371,7 +1383,7 @@ int tc_knn_t(const T* X, int64_t n, int d, const T* Q, int64_t m, int kq, bool s
     for (int t0 = 0; t0 < n_tiles; t0 += chunk_tiles) {
       const int t1 = std::min(n_tiles, t0 + chunk_tiles);
       FMGP_LAUNCH(tc_dist_kernel<0><<<dim3((unsigned)qblocks, (unsigned)ysplit), kTcThreads, kTcSmem, s>>>(
-          tmQ, tmX, qn2, xn2, 0, t0, t1, tpc, k_chunks, ldc, Dc, n, 0, nullptr, nullptr, err));
+          tmQ, tmX, qn2, xn2, 0, t0, t1, tpc, k_chunks, ldc, Dc, n, 0, nullptr, nullptr, err, main_wait));
       const int64_t col0 = (int64_t)t0 * kTN, ncols = (int64_t)(t1 - t0) * kTN;
       const int first = t0 == 0 ? 1 : 0;
       switch (S <= 4 ? S : S <= 6 ? 6 : S <= 8 ? 8 : 10) {  // list slots per lane >= L / 32

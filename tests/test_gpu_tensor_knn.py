@@ -252,3 +252,33 @@ def test_fused_selection_in_query_chunks(cuda, kq):
         fb.tune_set("tc_chunk_queries", prev)
     ref_q, _ = oracle.knn(X, Z, k)
     np.testing.assert_array_equal(nb_q.cpu().numpy(), ref_q)
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+def test_distance_pass_that_gives_up_falls_back_to_the_exact_scan(cuda, fused):
+    """With the main-loop wait limit of the tcgen05 distance kernel cut to 1 ns
+    its waits run out: the kernel stops, drains its own copies and matrix
+    operations (those waits keep their 2 s limit), frees its tensor memory and
+    reports the abort, so no query is certified and every one is answered by
+    the exhaustive exact scan.  The table is still the oracle's, and a later
+    call with the normal limit runs normally."""
+    X = _data("u32", 6000, 64, 12)
+    ref, ref_d = fb.fmgp_build_knn(dev(X), 20, with_dist=True)
+    torch.cuda.synchronize()
+    prev = fb.tune_get("tc_wait_ns")
+    try:
+        fb.tune_set("tc_wait_ns", 1)
+        with _Fused(fused):
+            nbr, dist = fb.fmgp_build_knn(dev(X), 20, with_dist=True)
+            torch.cuda.synchronize()
+            redone = fb.diag_counter(2)
+    finally:
+        fb.tune_set("tc_wait_ns", prev)
+    assert redone == 6000, redone  # the aborted pass certified nothing
+    assert torch.equal(nbr, ref) and torch.equal(dist, ref_d)
+    rows = np.arange(0, 6000, 61)
+    ref_i, _ = oracle.knn(X.astype(np.float64), X.astype(np.float64)[rows], 20, rows)
+    np.testing.assert_array_equal(nbr.cpu().numpy()[rows], ref_i)
+    again, _ = fb.fmgp_build_knn(dev(X), 20)
+    torch.cuda.synchronize()
+    assert fb.diag_counter(2) < 600 and torch.equal(again, ref)
