@@ -202,14 +202,16 @@ __device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* 
                                           int k, int r, int lane) {
   const int nblk = (k + 31) >> 5;
   for (int c = 0; c < r; ++c) {
-    // forward
+    // forward (branch-free across lanes: a row past the end works on the
+    // last row, and its value is never broadcast or stored)
     for (int q = 0; q < nblk; ++q) {
       const int row = 32 * q + lane;
       const bool valid = row < k;
+      const int rc = min(row, k - 1);
       float v = valid ? R[row * r + c] : 0.0f;
       const float iv = valid ? invd[row] : 0.0f;
-      if (valid && q > 0) {
-        const float* mr = M + row * ldl;
+      if (q > 0) {
+        const float* mr = M + rc * ldl;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         if (r == 1) {
           for (int p = 0; p < 32 * q; p += 4) {
@@ -223,18 +225,20 @@ __device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* 
         }
         v -= (s0 + s1) + (s2 + s3);
       }
-      const float* mb = M + row * ldl + 32 * q;
+      const float* mb = M + rc * ldl + 32 * q;
       if (32 * q + 32 <= k) {
 #pragma unroll 8
         for (int t = 0; t < 32; ++t) {
-          const float m = (lane > t && valid) ? mb[t] : 0.0f;
+          const float mv = mb[t];
+          const float m = (lane > t && valid) ? mv : 0.0f;
           const float xt = __shfl_sync(kFull, v * iv, t);
           v = (lane == t) ? xt : fmaf(-m, xt, v);
         }
       } else {
         const int tmax = k - 32 * q;
         for (int t = 0; t < tmax; ++t) {
-          const float m = (lane > t && valid) ? mb[t] : 0.0f;
+          const float mv = mb[t];
+          const float m = (lane > t && valid) ? mv : 0.0f;
           const float xt = __shfl_sync(kFull, v * iv, t);
           v = (lane == t) ? xt : fmaf(-m, xt, v);
         }
@@ -246,29 +250,32 @@ __device__ __forceinline__ void solve_f32(const float* M, int ldl, const float* 
     for (int q = nblk - 1; q >= 0; --q) {
       const int row = 32 * q + lane;
       const bool valid = row < k;
+      const int rc = min(row, k - 1);
       float v = valid ? R[row * r + c] : 0.0f;
       const float iv = valid ? invd[row] : 0.0f;
-      if (valid) {
+      {
         float s0 = 0.f, s1 = 0.f;
         int p = 32 * (q + 1);
         for (; p + 1 < k; p += 2) {
-          s0 = fmaf(M[p * ldl + row], R[p * r + c], s0);
-          s1 = fmaf(M[(p + 1) * ldl + row], R[(p + 1) * r + c], s1);
+          s0 = fmaf(M[p * ldl + rc], R[p * r + c], s0);
+          s1 = fmaf(M[(p + 1) * ldl + rc], R[(p + 1) * r + c], s1);
         }
-        if (p < k) s0 = fmaf(M[p * ldl + row], R[p * r + c], s0);
+        if (p < k) s0 = fmaf(M[p * ldl + rc], R[p * r + c], s0);
         v -= s0 + s1;
       }
       const int tmax = min(32, k - 32 * q);
       if (tmax == 32) {
 #pragma unroll 8
         for (int t = 31; t >= 0; --t) {
-          const float m = (lane < t && valid) ? M[(32 * q + t) * ldl + row] : 0.0f;
+          const float mv = M[(32 * q + t) * ldl + rc];
+          const float m = (lane < t && valid) ? mv : 0.0f;
           const float xt = __shfl_sync(kFull, v * iv, t);
           v = (lane == t) ? xt : fmaf(-m, xt, v);
         }
       } else {
         for (int t = tmax - 1; t >= 0; --t) {
-          const float m = (lane < t && valid) ? M[(32 * q + t) * ldl + row] : 0.0f;
+          const float mv = M[(32 * q + t) * ldl + rc];
+          const float m = (lane < t && valid) ? mv : 0.0f;
           const float xt = __shfl_sync(kFull, v * iv, t);
           v = (lane == t) ? xt : fmaf(-m, xt, v);
         }
@@ -370,31 +377,36 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
     // lane l owns rows j0 + l, j0 + l + 32, ..., so the rows still active
     // fill the low lanes and a panel needs only ceil((k - j0) / 32) slots,
     // and the pivot row of panel column c is always lane c's first slot.
+    // The loops below are branch-free across lanes: rows past the end are
+    // clamped to the last row (their values are computed and never stored),
+    // and only the warp-uniform slot count ns guards a slot.
     bool fail = false;
     for (int j0 = 0; j0 < k; j0 += CB) {
       const int nb = min(CB, k - j0);
       const int ns = (k - j0 + 31) >> 5;  // slots in use (warp-uniform)
       float acc[NS][CB];
       bool act[NS];
+      int rr[NS];  // row of each slot, clamped into the matrix
 #pragma unroll
       for (int s4 = 0; s4 < NS; ++s4) {
         const int r = j0 + lane + 32 * s4;
         act[s4] = s4 < ns && r < k;
+        rr[s4] = min(r, k - 1);
 #pragma unroll
-        for (int c = 0; c < CB; ++c)
-          acc[s4][c] = (act[s4] && c < nb && j0 + c <= r) ? M[r * ldl + j0 + c] : 0.0f;
+        for (int c = 0; c < CB; ++c) {
+          const float v = M[rr[s4] * ldl + min(j0 + c, k - 1)];
+          acc[s4][c] = (c < nb && j0 + c <= r) ? v : 0.0f;
+        }
       }
       for (int p = 0; p < j0; p += 4) {
         float4 bc[CB];
 #pragma unroll
         for (int c = 0; c < CB; ++c)
-          bc[c] = c < nb ? *reinterpret_cast<const float4*>(M + (j0 + c) * ldl + p)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
+          bc[c] = *reinterpret_cast<const float4*>(M + min(j0 + c, k - 1) * ldl + p);
 #pragma unroll
         for (int s4 = 0; s4 < NS; ++s4) {
           if (s4 >= ns) break;
-          if (!act[s4]) continue;
-          const float4 a4 = *reinterpret_cast<const float4*>(M + (j0 + lane + 32 * s4) * ldl + p);
+          const float4 a4 = *reinterpret_cast<const float4*>(M + rr[s4] * ldl + p);
 #pragma unroll
           for (int c = 0; c < CB; ++c) {
             float t = acc[s4][c];
@@ -435,15 +447,13 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
         for (int s4 = 0; s4 < NS; ++s4) {
           if (s4 >= ns) break;
           const int r = j0 + lane + 32 * s4;
-          if (act[s4] && r > col) {
-            float t = acc[s4][c];
+          float t = acc[s4][c];
 #pragma unroll
-            for (int c2 = 0; c2 < CB; ++c2)
-              if (c2 < c) t = fmaf(-lr[s4][c2], lc[c2], t);
-            t *= inv;
-            lr[s4][c] = t;
-            M[r * ldl + col] = t;
-          }
+          for (int c2 = 0; c2 < CB; ++c2)
+            if (c2 < c) t = fmaf(-lr[s4][c2], lc[c2], t);
+          t *= inv;
+          lr[s4][c] = t;  // rows at or above the pivot never read it
+          if (act[s4] && r > col) M[r * ldl + col] = t;
         }
       }
       __syncwarp();
@@ -489,13 +499,19 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
             const dfl xb = XV[b * r + c];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
+              // branch-free across lanes: a row past the end reads the last
+              // row, and it and the diagonal term contribute exact zeros
               const int row = lane + 32 * s;
-              if (row < k && b != row) {
+              const int rc = min(row, k - 1);
+              const bool use = row < k && b != row;
+              {
                 // K_row,b = (M[b][row], LO[row(row-1)/2 + b]) below the diagonal,
                 // (M[row][b], LO[b(b-1)/2 + row]) above it
-                const bool below = b < row;
-                const float hi = below ? M[b * ldl + row] : M[row * ldl + b];
-                const float lo = below ? LO[row * (row - 1) / 2 + b] : LO[cb + row];
+                const bool below = b < rc;
+                float hi = below ? M[b * ldl + rc] : M[rc * ldl + b];
+                float lo = below ? LO[rc * (rc - 1) / 2 + b] : LO[cb + rc];
+                hi = use ? hi : 0.0f;
+                lo = use ? lo : 0.0f;
                 const float h = __fmul_rn(hi, xb.hi);
                 const float hr = __fmaf_rn(hi, xb.hi, -h);  // hi * x.hi = h + hr exactly
                 const float t = __fadd_rn(p[s], -h);        // TwoSum(p, -h) = t + q
