@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
       const int npairs = k * (k - 1) / 2;
       int a = 1, b = lane;
       while (b >= a) { b -= a; ++a; }
-      // two entries per iteration, evaluated together for instruction-level
+      // three entries per iteration, evaluated together for instruction-level
       // parallelism (out-of-range slots evaluate a dummy pair and are dropped)
-      constexpr int U = 2;
+      constexpr int U = 3;
       for (int p = lane; p < npairs; p += 32 * U) {
         int aa[U], bb[U];
 #pragma unroll
