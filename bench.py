@@ -297,9 +297,10 @@ def run_ours(a):
         fb.fmgp_build_knn(X, kq, nbr_out=nbr)
         gt = fb.fmgp_autotune_knn(X, kq)
         fb.fmgp_autotune_precompute(X, Y, nbr, k, gk, prec, sample_rows=min(n, 200_000))
-        w, pw = fb.autotune_choice(k, W.d, 1, prec, X.dtype)
+        w, pw, pers = fb.autotune_choice(k, W.d, 1, prec, X.dtype)
         tuned = {"grid_target": gt if gt > 0 else None, "block_warps": w,
-                 "cholesky_panel": pw or None, "sample_rows": min(n, 200_000)}
+                 "cholesky_panel": pw or None, "persistent": pers,
+                 "sample_rows": min(n, 200_000)}
     C = torch.empty(fb.coeff_shape(n, k, 1, prec),
                     dtype=torch.float64 if prec == fb.PREC_FP64 else torch.float32, device=dev)
     st = torch.empty(n, dtype=torch.int8, device=dev)

@@ -520,6 +520,12 @@ const char* fmgp_version(void);
  *   "block_panel"  Cholesky panel width of the mixed neighbourhood kernel for
  *                  k <= 64: 4 or 8 columns, 0 = the autotuner's choice or the
  *                  default (8 for k <= 32, 4 above)
+ *   "block_persistent" launch form of the neighbourhood kernels: 1 = persistent
+ *                  (one wave of the CTAs the SMs hold at once; each warp, or
+ *                  CTA, claims its next neighbourhood from a device counter as
+ *                  it becomes free), 0 = eight waves of grid-stride CTAs that
+ *                  the hardware's block scheduler replaces as they finish,
+ *                  -1 = the autotuner's choice, else persistent (default)
  *   "tensor_cores" 1 = tcgen05 candidate search for kNN at d >= 16 (default), 0 = off
  *   "tc_fused_select" 1 = the candidates are selected inside the tcgen05
  *                  distance kernel (default), 0 = distances go through a pass
@@ -566,10 +572,12 @@ double fmgp_tune_get(const char* key);  /* -1 for an unknown key */
  * Autotuner (the paper has no counterpart: launch-shape selection).
  * fmgp_autotune_precompute times the neighbourhood kernel with each feasible
  * warps-per-CTA (and, for the mixed form with k <= 64, each Cholesky panel
- * width, 4 or 8 columns) on the first sample_rows rows of this problem and
- * caches the fastest for (precision, k, d, r, dtype); later fmgp_precompute /
- * fmgp_loocv_objective calls with that key use it.  fmgp_autotune_choice
- * reports the cached shape (0 = none cached: the default).  fmgp_autotune_knn times
+ * width, 4 or 8 columns), each both persistent and as eight waves (unless the
+ * tuning key "block_persistent" fixes the form), on the first sample_rows
+ * rows of this problem and caches the fastest for (precision, k, d, r,
+ * dtype); later fmgp_precompute / fmgp_loocv_objective calls with that key
+ * use it.  fmgp_autotune_choice reports the cached shape (warps and panel 0,
+ * persistent -1 when none is cached: the defaults).  fmgp_autotune_knn times
  * the grid search of fmgp_build_knn at several cell occupancies and caches
  * the fastest for (d, kq) (d <= 3; for larger d it reports 0).  Results of
  * the path never depend on these choices.  Both synchronise `stream`.
@@ -581,7 +589,7 @@ int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const double* Y, i
 int fmgp_autotune_knn(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, int32_t kq,
                       double* grid_target_out, void* stream);
 int fmgp_autotune_choice(fmgp_precision precision, int32_t k, int32_t d, int32_t r,
-                         fmgp_dtype dtype, int32_t* warps, int32_t* panel);
+                         fmgp_dtype dtype, int32_t* warps, int32_t* panel, int32_t* persistent);
 int fmgp_autotune_reset(void);
 
 /* Diagnostic counters: 0 = kernels enqueued, 1 = tensor-core kNN calls,

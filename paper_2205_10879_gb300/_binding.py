@@ -96,7 +96,7 @@ def load(build_if_missing=True):
                                                 KP, I32, P, P, P, P]
     lib.fmgp_loocv_objective_device.restype = I32
     lib.fmgp_autotune_choice.argtypes = [I32, I32, I32, I32, I32, ctypes.POINTER(I32),
-                                         ctypes.POINTER(I32)]
+                                         ctypes.POINTER(I32), ctypes.POINTER(I32)]
     lib.fmgp_autotune_choice.restype = I32
     lib.fmgp_model_get_info.argtypes = [P, ctypes.POINTER(ModelInfo)]
     lib.fmgp_model_get_info.restype = I32
@@ -379,12 +379,13 @@ def fmgp_autotune_knn(X, kq, stream=None):
 
 def autotune_choice(k, d, r, precision, dtype=torch.float64):
     """The cached launch shape for a precompute key: (warps per CTA, Cholesky
-    panel width); 0 where nothing is cached (the default is used)."""
-    w, p = ctypes.c_int32(0), ctypes.c_int32(0)
+    panel width, persistent 1 / eight waves 0); 0, 0, -1 where nothing is
+    cached (the defaults are used)."""
+    w, p, q = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     _check(load().fmgp_autotune_choice(int(precision), int(k), int(d), int(r),
                                        F64 if dtype == torch.float64 else F32,
-                                       ctypes.byref(w), ctypes.byref(p)))
-    return w.value, p.value
+                                       ctypes.byref(w), ctypes.byref(p), ctypes.byref(q)))
+    return w.value, p.value, q.value
 
 
 def autotune_reset():

@@ -278,6 +278,13 @@ static int run_blocks(BlockArgs& a, const void* X, fmgp_dtype dtype, int mode,
               a.r, std::max(bytes, a.layout.bytes_per_warp));
     return FMGP_EUNSUPPORTED;
   }
+  // persistent launch (one wave of CTAs claiming neighbourhoods from a
+  // counter) unless the tuning key or the autotuner chose eight waves
+  a.queue = nullptr;
+  if (block_persistent_for((int)precision, a.k, a.d, a.r, (int)dtype)) {
+    a.queue = ws.get<unsigned long long>(1);
+    if (!a.queue) return FMGP_ENOMEM;
+  }
   // warps per CTA: the user's or the autotuner's choice, else (0) the
   // launchers pick the one with the most resident warps per SM
   int req = tune_params().block_warps;
@@ -493,6 +500,9 @@ int fmgp_tune_set(const char* key, double value) {
   } else if (k == "block_panel") {
     if (!(value == 0 || value == 4 || value == 8)) { set_error("block_panel must be 0, 4 or 8"); return FMGP_EINVAL; }
     tp.block_panel = (int)value;
+  } else if (k == "block_persistent") {
+    if (!(value == -1 || value == 0 || value == 1)) { set_error("block_persistent must be -1, 0 or 1"); return FMGP_EINVAL; }
+    tp.block_persistent = (int)value;
   } else if (k == "tensor_cores") {
     tp.use_tensor_cores = value != 0.0;
   } else if (k == "tc_fused_select") {
@@ -530,6 +540,7 @@ double fmgp_tune_get(const char* key) {
   if (k == "grid_target") return tp.grid_target;
   if (k == "block_warps") return tp.block_warps;
   if (k == "block_panel") return tp.block_panel;
+  if (k == "block_persistent") return tp.block_persistent;
   if (k == "tensor_cores") return tp.use_tensor_cores ? 1.0 : 0.0;
   if (k == "tc_fused_select") return tp.tc_fused_select ? 1.0 : 0.0;
   if (k == "tc_oversample") return tp.tc_oversample;

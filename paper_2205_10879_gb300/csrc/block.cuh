@@ -45,9 +45,29 @@ struct BlockArgs {
   // Precompute over centres (subsampled precompute): item p factors the block
   // of training point rows[p] and writes C row p and status p.
   const int32_t* rows = nullptr;
+  // Persistent launches: a device work counter, zero when the kernel starts.
+  // The grid is then one wave of the CTAs the SMs hold at once, and every warp
+  // (or CTA) claims its next neighbourhood from the counter; without one the
+  // grid is several waves and the items are grid-strided.
+  unsigned long long* queue = nullptr;
 };
 
-// blocks = 0 picks a grid covering `count`; the list mode needs an explicit grid.
+// Work distribution of the block kernels.  A warp (or CTA) starts with item
+// `first` = its index in the grid and moves on to item `stride` + claim, where
+// claim is the value it took from the counter (one atomic, issued when an item
+// starts and read when it ends, so that its latency is hidden by the item's
+// work), or its current item when there is no counter (grid stride).  With a
+// counter, items are handed out in order as warps become free, so that the
+// kernel ends with no wave tail.
+__device__ __forceinline__ unsigned long long block_claim(unsigned long long* queue, int64_t item,
+                                                          bool leader) {
+  if (!queue) return (unsigned long long)item;
+  return leader ? atomicAdd(queue, 1ull) : 0ull;
+}
+
+// blocks = 0 picks the grid: one wave of resident CTAs when a.queue is set (the
+// launcher zeroes the counter first), else eight waves; the list mode needs an
+// explicit grid and no queue.
 int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mode, int warps,
                      cudaStream_t stream, int blocks = 0);
 

@@ -9,6 +9,7 @@ struct TuneParams {
   double grid_target = 12.0;     // mean training points per grid cell
   int block_warps = 0;           // warps per CTA for block kernels (0 = automatic)
   int block_panel = 0;           // Cholesky panel width of the mixed kernel (0 = tuned / default)
+  int block_persistent = -1;     // block kernels: 1 = persistent, 0 = 8 waves, -1 = tuned / default
   bool use_tensor_cores = true;  // tcgen05 candidate search for d >= 16
   bool tc_fused_select = true;   // candidate selection inside the tcgen05 epilogue (kq <= 32)
   int tc_oversample = 4;         // re-rank candidates per requested neighbour (2..4)
@@ -24,6 +25,10 @@ TuneParams& tune_params();
 // Autotuner caches (0 / the default when nothing was tuned for the key).
 int tuned_block_warps(int prec, int k, int d, int r, int dtype);
 int tuned_block_panel(int prec, int k, int d, int r, int dtype);  // 0 = default width
+// Whether the block kernels of this key run persistent (one wave of CTAs
+// claiming neighbourhoods from a counter) or as eight waves of grid-stride
+// CTAs: the tuning key, else the autotuner's choice, else persistent.
+bool block_persistent_for(int prec, int k, int d, int r, int dtype);
 double grid_target_for(int d, int kq);
 
 // Self kNN table (A1): nbr (n x kq), dist (n x kq canonical keys, or null).

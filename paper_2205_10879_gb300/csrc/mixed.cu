@@ -312,8 +312,13 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
   const int k = args.k, d = args.d, r = args.r, ldl = lay.ldl;
   const KParamsDF kp = mx.kdf;
 
+  // the next item is claimed once the factorisation is done: the claim's
+  // latency hides behind the solves and the refinement, and it holds no
+  // registers through the assembly and the Cholesky
+  const int64_t stride = (int64_t)gridDim.x * wpb;
+  unsigned long long claim = 0;
   for (int64_t item = (int64_t)blockIdx.x * wpb + wid; item < args.count;
-       item += (int64_t)gridDim.x * wpb) {
+       item = stride + (int64_t)__shfl_sync(kFull, claim, 0)) {
     int64_t i = LOO ? args.batch[item]
                     : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
     const int64_t orow = MODE == kModePrecompute && args.rows ? item : i;  // row of C / status
@@ -460,6 +465,7 @@ __global__ void __launch_bounds__(NS == 2 ? 192 : 256, NS >= 5 ? 1 : 2) block_mi
       if (fail) break;
     }
     if (lane == 0) *flag = fail ? 1 : 0;
+    claim = block_claim(args.queue, item, lane == 0);
     __syncwarp();
     bool ok = (*flag == 0) && !bad;
     if (ok) {
@@ -691,8 +697,11 @@ __global__ void __launch_bounds__(NW * 32, 2) block_mixed_cta_kernel(
   const int k = args.k, d = args.d, r = args.r, ldl = lay.ldl;
   const KParamsDF kp = mx.kdf;
 
-  for (int64_t item = blockIdx.x; item < args.count; item += gridDim.x) {
-    __syncthreads();  // the previous neighbourhood is finished with shared memory
+  __shared__ unsigned long long next_item;
+  for (int64_t item = blockIdx.x; item < args.count; item = (int64_t)next_item) {
+    __syncthreads();  // the previous neighbourhood is finished with shared memory and next_item
+    unsigned long long claim = 0;
+    if (tid == 0) claim = block_claim(args.queue, item, true);
     int64_t i = LOO ? args.batch[item]
                     : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
     const int64_t orow = MODE == kModePrecompute && args.rows ? item : i;
@@ -884,6 +893,8 @@ __global__ void __launch_bounds__(NW * 32, 2) block_mixed_cta_kernel(
         if (lane == 0 && MODE == kModeLoocv) args.resid[item] = df_to_double(e2);
       }
     }
+    if (tid == 0) next_item = (unsigned long long)gridDim.x + claim;
+    __syncthreads();
   }
 }
 
@@ -988,6 +999,7 @@ static int mixed_fallback(const BlockArgs& a, const void* X, fmgp_dtype dtype, i
   BlockArgs f = a;
   f.list = fb_list;
   f.list_count = fb_count;
+  f.queue = nullptr;  // a fixed grid over the device-counted list
   f.c_df = !loo;
   f.layout = block_layout(a.k, a.d, a.r, dtype == FMGP_F64 ? 8 : 4, false);
   int fw = (int)((200 * 1024) / f.layout.bytes_per_warp);
@@ -1008,6 +1020,10 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   if (!rc) rc = to_df(a.Y, true, a.n * a.r, Ydf, s);
   if (rc) return rc;
   FMGP_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(int), s));
+  // persistent (one wave, claimed items) with a work counter, else eight
+  // whole waves of the CTAs the SMs hold at once (grid stride)
+  const int waves = a.queue ? 1 : 8;
+  if (a.queue) FMGP_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
   mx.Xdf = Xdf;
   mx.Ydf = Ydf;
   mx.fb_list = fb_list;
@@ -1035,7 +1051,7 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
       return FMGP_EUNSUPPORTED;
     }
     const int blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit * 8));
+        1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit * waves));
     FMGP_CUDA_TRY(ensure_smem(fn, smem));
     if (f32)
       FMGP_LAUNCH(pick(TF{})<<<blocks, kCtaWarps * 32, smem, s>>>(a, mx, cl, (const float*)X));
@@ -1088,9 +1104,8 @@ int run_block_mixed(BlockArgs a, const void* X, fmgp_dtype dtype, int mode, int 
   }
   const size_t smem = kMixedHead + lay.bytes * warps;
   const int64_t need = (a.count + warps - 1) / warps;
-  // a whole number of waves (8) of the CTAs the SMs hold at once: no partial
-  // last wave, and CTAs that finish early are replaced
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * std::max(nb, 1) * 8));
+  // whole waves of the CTAs the SMs hold at once: no partial last wave
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * std::max(nb, 1) * waves));
   FMGP_CUDA_TRY(ensure_smem((const void*)kern_fn, smem));
   FMGP_LAUNCH(kern_fn<<<blocks, warps * 32, smem, s>>>(a, mx, lay));
   FMGP_CUDA_TRY(cudaGetLastError());

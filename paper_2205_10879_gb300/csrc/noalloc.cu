@@ -19,6 +19,7 @@ constexpr int64_t kNoAllocMaxBatch = 65536;
 struct NoAllocScratch {
   double resid[kNoAllocMaxBatch];  // per-point squared residuals
   double q;                        // the objective
+  unsigned long long queue;        // work counter of the persistent block kernel
   int fails;                       // blocks whose Cholesky failed
 };
 
@@ -123,6 +124,7 @@ extern "C" int fmgp_loocv_objective_noalloc(const void* X, fmgp_dtype dtype, con
   a.batch = batch;
   a.resid = resid_out ? resid_out : sc->resid;
   a.fail_count = &sc->fails;
+  a.queue = block_persistent_for((int)FMGP_PREC_FP64, k, d, r, (int)dtype) ? &sc->queue : nullptr;
   a.n = n;
   a.count = b;
   a.d = d;

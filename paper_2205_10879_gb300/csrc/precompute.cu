@@ -40,8 +40,11 @@ __global__ void __launch_bounds__(256, 2) block_f64_kernel(BlockArgs args, const
   const KParams kp = args.kp;
 
   const int64_t total = args.list ? (int64_t)*args.list_count : args.count;
+  const int64_t stride = (int64_t)gridDim.x * wpb;
+  unsigned long long claim = 0;
   for (int64_t it = (int64_t)blockIdx.x * wpb + wid; it < total;
-       it += (int64_t)gridDim.x * wpb) {
+       it = stride + (int64_t)__shfl_sync(kFull, claim, 0)) {
+    claim = block_claim(args.queue, it, lane == 0);
     const int64_t item = args.list ? (int64_t)args.list[it] : it;
     int64_t i = LOO ? args.batch[item]
                     : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
@@ -242,8 +245,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1) block_f64_cta_kernel(BlockArgs
   const KParams kp = args.kp;
 
   const int64_t total = args.list ? (int64_t)*args.list_count : args.count;
-  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-    __syncthreads();  // the previous neighbourhood is finished with shared memory
+  __shared__ unsigned long long next_it;
+  for (int64_t it = blockIdx.x; it < total; it = (int64_t)next_it) {
+    __syncthreads();  // the previous neighbourhood is finished with shared memory and next_it
+    unsigned long long claim = 0;
+    if (tid == 0) claim = block_claim(args.queue, it, true);
     const int64_t item = args.list ? (int64_t)args.list[it] : it;
     int64_t i = LOO ? args.batch[item]
                     : (MODE == kModePrecompute && args.rows ? (int64_t)args.rows[item] : item);
@@ -377,6 +383,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1) block_f64_cta_kernel(BlockArgs
         if (fail) atomicAdd(args.fail_count, 1);
       }
     }
+    if (tid == 0) next_it = (unsigned long long)gridDim.x + claim;
+    __syncthreads();
   }
 }
 
@@ -405,9 +413,12 @@ constexpr size_t kCtaBlockBytes = 56 * 1024;
 
 int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mode, int warps,
                      cudaStream_t stream, int blocks) {
+  // persistent (one wave, claimed items) with a work counter, else eight whole
+  // waves of the CTAs the SMs hold at once (grid stride)
+  const int waves = a.queue ? 1 : 8;
+  if (a.queue) FMGP_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream));
   if (a.layout.bytes_per_warp > kCtaBlockBytes) {
     const size_t smem = a.layout.bytes_per_warp;
-    // eight whole waves of the CTAs the SMs hold at once
     const void* fk = dtype == FMGP_F64
                          ? (mode == kModeLoocv    ? (const void*)block_f64_cta_kernel<double, kModeLoocv>
                             : mode == kModeMuygps ? (const void*)block_f64_cta_kernel<double, kModeMuygps>
@@ -417,7 +428,7 @@ int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mo
                                                   : (const void*)block_f64_cta_kernel<float, kModePrecompute>);
     const int fit = std::max(1, active_ctas(fk, kCtaThreads, smem));
     const int grid = blocks > 0 ? blocks
-                                : (int)std::max<int64_t>(1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit * 8));
+                                : (int)std::max<int64_t>(1, std::min<int64_t>(a.count, (int64_t)num_sms() * fit * waves));
     if (dtype == FMGP_F64) {
       auto kern = mode == kModeLoocv    ? block_f64_cta_kernel<double, kModeLoocv>
                   : mode == kModeMuygps ? block_f64_cta_kernel<double, kModeMuygps>
@@ -460,10 +471,9 @@ int launch_block_f64(const BlockArgs& a, const void* X, fmgp_dtype dtype, int mo
   }
   const size_t smem = per_warp * warps;
   const int64_t need = (a.count + warps - 1) / warps;
-  // a whole number of waves (8) of the CTAs the SMs hold at once: no partial
-  // last wave, and CTAs that finish early are replaced
+  // whole waves of the CTAs the SMs hold at once: no partial last wave
   if (blocks <= 0)
-    blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * std::max(nb, 1) * 8));
+    blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * std::max(nb, 1) * waves));
   FMGP_CUDA_TRY(ensure_smem(kern, smem));
   if (dtype == FMGP_F64)
     FMGP_LAUNCH(((void (*)(BlockArgs, const double*))kern)<<<blocks, warps * 32, smem, stream>>>(a, (const double*)X));

@@ -1,7 +1,8 @@
 // Autotuner: times candidate launch shapes on the caller's own data and
 // caches the fastest per problem key.  Only speed depends on the choice:
 // every shape computes identical results.
-//   block kernels (precompute / LOOCV): warps per CTA, key (precision, k, d, r, dtype)
+//   block kernels (precompute / LOOCV): warps per CTA, Cholesky panel width
+//     (mixed, k <= 64) and persistent or multi-wave grid, key (precision, k, d, r, dtype)
 //   grid kNN (d <= 3): mean points per cell, key (d, kq)
 #include <map>
 #include <mutex>
@@ -16,6 +17,7 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_warps;
 std::map<std::tuple<int, int, int, int, int>, int> g_panel;
+std::map<std::tuple<int, int, int, int, int>, int> g_persist;
 std::map<std::tuple<int, int>, double> g_grid;
 
 }  // namespace
@@ -30,6 +32,14 @@ int tuned_block_panel(int prec, int k, int d, int r, int dtype) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_panel.find({prec, k, d, r, dtype});
   return it == g_panel.end() ? 0 : it->second;
+}
+
+bool block_persistent_for(int prec, int k, int d, int r, int dtype) {
+  const int p = tune_params().block_persistent;
+  if (p >= 0) return p != 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_persist.find({prec, k, d, r, dtype});
+  return it == g_persist.end() ? true : it->second != 0;
 }
 
 double grid_target_for(int d, int kq) {
@@ -89,7 +99,8 @@ extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const d
   const int64_t cnt = sample_rows < n ? sample_rows : n;
   void* Ctmp = ws.alloc((size_t)cnt * k * r * 8);
   int* fails = ws.get<int>(1);
-  if (!Ctmp || !fails) return FMGP_ENOMEM;
+  unsigned long long* queue = ws.get<unsigned long long>(1);
+  if (!Ctmp || !fails || !queue) return FMGP_ENOMEM;
   BlockArgs a{};
   a.Y = Y;
   a.nbr = nbr;
@@ -105,24 +116,31 @@ extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const d
   a.layout = block_layout(k, d, r, dtype == FMGP_F64 ? 8 : 4, false);
   const size_t bytes = precision == FMGP_PREC_FP64 ? a.layout.bytes_per_warp
                                                    : mixed_bytes_per_warp(k, d, r, dtype == FMGP_F64 ? 8 : 4);
-  int best = 0, best_panel = 0;
+  int best = 0, best_panel = 0, best_persist = 1;
   float best_ms = 1e30f;
   // the mixed kernel's Cholesky panel width: both instantiated widths for k <= 64
   const bool panels = precision == FMGP_PREC_MIXED && k <= 64;
-  for (int panel : {0, 4, 8}) {
-    if (panel && !panels) continue;
-    if (!panel && panels) continue;
-    for (int w : {1, 2, 4, 6, 8}) {
-      if ((size_t)w * bytes > 200 * 1024) continue;
-      float ms = 0.f;
-      int rc = time_ms(s, 2, [&]() {
-        Workspace inner(s);
-        return precision == FMGP_PREC_FP64
-                   ? launch_block_f64(a, X, dtype, kModePrecompute, w, s)
-                   : run_block_mixed(a, X, dtype, kModePrecompute, w, panel, *kernel, inner, s);
-      }, &ms);
-      if (rc) return rc;
-      if (ms < best_ms) { best_ms = ms; best = w; best_panel = panel; }
+  // persistent (one wave claiming items from a counter) or eight waves of
+  // grid-stride CTAs, unless the tuning key fixes it
+  const int fixed = tune_params().block_persistent;
+  for (int persist : {1, 0}) {
+    if (fixed >= 0 && persist != (fixed != 0)) continue;
+    a.queue = persist ? queue : nullptr;
+    for (int panel : {0, 4, 8}) {
+      if (panel && !panels) continue;
+      if (!panel && panels) continue;
+      for (int w : {1, 2, 4, 6, 8}) {
+        if ((size_t)w * bytes > 200 * 1024) continue;
+        float ms = 0.f;
+        int rc = time_ms(s, 2, [&]() {
+          Workspace inner(s);
+          return precision == FMGP_PREC_FP64
+                     ? launch_block_f64(a, X, dtype, kModePrecompute, w, s)
+                     : run_block_mixed(a, X, dtype, kModePrecompute, w, panel, *kernel, inner, s);
+        }, &ms);
+        if (rc) return rc;
+        if (ms < best_ms) { best_ms = ms; best = w; best_panel = panel; best_persist = persist; }
+      }
     }
   }
   if (!best) {
@@ -133,19 +151,24 @@ extern "C" int fmgp_autotune_precompute(const void* X, fmgp_dtype dtype, const d
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_warps[{(int)precision, k, d, r, (int)dtype}] = best;
     g_panel[{(int)precision, k, d, r, (int)dtype}] = best_panel;
+    g_persist[{(int)precision, k, d, r, (int)dtype}] = best_persist;
   }
   *warps_out = best;
   return FMGP_OK;
 }
 
 extern "C" int fmgp_autotune_choice(fmgp_precision precision, int32_t k, int32_t d, int32_t r,
-                                    fmgp_dtype dtype, int32_t* warps, int32_t* panel) {
-  if (!warps || !panel) {
-    set_error("warps and panel must be non-NULL");
+                                    fmgp_dtype dtype, int32_t* warps, int32_t* panel,
+                                    int32_t* persistent) {
+  if (!warps || !panel || !persistent) {
+    set_error("warps, panel and persistent must be non-NULL");
     return FMGP_EINVAL;
   }
   *warps = tuned_block_warps((int)precision, k, d, r, (int)dtype);
   *panel = tuned_block_panel((int)precision, k, d, r, (int)dtype);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_persist.find({(int)precision, k, d, r, (int)dtype});
+  *persistent = it == g_persist.end() ? -1 : it->second;
   return FMGP_OK;
 }
 
@@ -189,6 +212,7 @@ extern "C" int fmgp_autotune_reset(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_warps.clear();
   g_panel.clear();
+  g_persist.clear();
   g_grid.clear();
   return FMGP_OK;
 }

@@ -94,13 +94,15 @@ def test_tuning_keys_are_host_only_and_range_checked():
     lib.fmgp_tune_set.argtypes = [ctypes.c_char_p, ctypes.c_double]
     lib.fmgp_tune_get.argtypes = [ctypes.c_char_p]
     defaults = {b"tensor_cores": 1.0, b"tc_fused_select": 1.0, b"tc_oversample": 4.0,
-                b"block_warps": 0.0, b"count_visits": 0.0, b"tc_fused_r": 0.0}
+                b"block_warps": 0.0, b"count_visits": 0.0, b"tc_fused_r": 0.0,
+                b"block_persistent": -1.0}
     for key, v in defaults.items():
         assert lib.fmgp_tune_get(key) == v, key
     assert lib.fmgp_tune_get(b"no_such_key") == -1.0
     assert lib.fmgp_tune_set(b"no_such_key", 1.0) == b.FMGP_EINVAL
     for key, bad in ((b"tc_oversample", 1.0), (b"tc_oversample", 5.0), (b"block_warps", 9.0),
-                     (b"grid_target", 0.5), (b"tc_fused_r", 12.0)):
+                     (b"grid_target", 0.5), (b"tc_fused_r", 12.0), (b"block_persistent", 2.0),
+                     (b"block_persistent", 0.5)):
         assert lib.fmgp_tune_set(key, bad) == b.FMGP_EINVAL, key
         assert lib.fmgp_tune_get(key) == defaults.get(key, 12.0)
     try:
@@ -108,6 +110,9 @@ def test_tuning_keys_are_host_only_and_range_checked():
         assert lib.fmgp_tune_get(b"tc_oversample") == 3.0
         assert lib.fmgp_tune_set(b"tc_fused_select", 0.0) == 0
         assert lib.fmgp_tune_get(b"tc_fused_select") == 0.0
+        assert lib.fmgp_tune_set(b"block_persistent", 0.0) == 0
+        assert lib.fmgp_tune_get(b"block_persistent") == 0.0
     finally:
         lib.fmgp_tune_set(b"tc_oversample", 4.0)
         lib.fmgp_tune_set(b"tc_fused_select", 1.0)
+        lib.fmgp_tune_set(b"block_persistent", -1.0)

@@ -106,8 +106,8 @@ def test_autotuner_choices_keep_results(cuda):
     t = fb.fmgp_autotune_knn(X, 50)
     w = fb.fmgp_autotune_precompute(X, Y, nbr0, 50, gk, fb.PREC_MIXED, sample_rows=5000)
     assert t > 0 and w >= 1
-    cw, panel = fb.autotune_choice(50, 2, 1, fb.PREC_MIXED)
-    assert cw == w and panel in (4, 8)
+    cw, panel, pers = fb.autotune_choice(50, 2, 1, fb.PREC_MIXED)
+    assert cw == w and panel in (4, 8) and pers in (0, 1)
     nbr1, d1 = fb.fmgp_build_knn(X, 50, with_dist=True)
     C1, _ = fb.fmgp_precompute(X, Y, nbr1, 50, gk, fb.PREC_MIXED)
     assert torch.equal(nbr0, nbr1) and torch.equal(d0, d1)
@@ -138,3 +138,36 @@ def test_every_panel_width_gives_the_same_predictions(cuda, panel):
         y, _ = fb.fmgp_predict(X, nbr, C, k, gk, Z, fb.PREC_MIXED)
         rel = float(torch.linalg.norm(y - y64) / torch.linalg.norm(y64))
         assert rel < 1e-7, rel
+
+
+@pytest.mark.parametrize("prec", [fb.PREC_MIXED, fb.PREC_FP64])
+@pytest.mark.parametrize("k", [50, 120])
+def test_persistent_and_multiwave_launches_agree(cuda, prec, k):
+    """The neighbourhood kernels give bit-identical coefficients, LOOCV
+    residuals and MuyGPs predictions whether they run persistent (one wave of
+    CTAs claiming neighbourhoods from a device counter) or as eight waves of
+    grid-stride CTAs: a neighbourhood's arithmetic does not depend on the warp
+    or CTA that runs it.  k = 50 runs the one-warp kernels, k = 120 the
+    CTA-per-neighbourhood ones."""
+    W = wl.spatial(n=12_000, m=700, nu=1.5, b=900)
+    _, gk = kern_pair(W.kernel)
+    X, Y, Z, B = dev(W.X), dev(W.Y), dev(W.Z), dev(W.batch)
+    nbr, _ = fb.fmgp_build_knn(X, k - 1)
+    nbr_l, _ = fb.fmgp_build_knn(X, k)
+    out = {}
+    for p in (1, 0):
+        fb.tune_set("block_persistent", p)
+        try:
+            assert fb.tune_get("block_persistent") == p
+            C, st = fb.fmgp_precompute(X, Y, nbr, k, gk, prec)
+            Q, res = fb.fmgp_loocv_objective(X, Y, nbr_l, k, B, gk, prec)
+            yh, _ = fb.fmgp_muygps_predict(X, Y, Z, k, gk, prec)
+        finally:
+            fb.tune_set("block_persistent", -1)
+        torch.cuda.synchronize()
+        assert int((st != 0).sum()) == 0
+        out[p] = (C, Q, res, yh)
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    assert torch.equal(out[0][2], out[1][2])
+    assert torch.equal(out[0][3], out[1][3])
