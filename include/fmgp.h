@@ -268,19 +268,27 @@ int fmgp_predict_rows(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, con
  * ---------------------------------------------------------------------- */
 typedef struct fmgp_model fmgp_model;
 
+/* How fmgp_model_create holds the caller's X, nbr and C. */
+enum { FMGP_MODEL_BORROW = 0, FMGP_MODEL_COPY = 1 };
+
 /*
  * fmgp_model_create -- register a fitted model for repeated prediction.
- * X, nbr and C (as produced by fmgp_build_knn / fmgp_precompute with the same
- * k, kernel and precision) are BORROWED: they must stay valid and unchanged
- * until fmgp_model_destroy.  The model builds and OWNS the nearest-point
- * search grid (d <= 3), an FP32 copy of an FP64 X for the nearest-point scan
- * (4 <= d <= 15) and, for FMGP_PREC_MIXED, a double-float copy of X.
- * Synchronises `stream` before returning.  *out receives the handle.
+ * X, nbr and C are as produced by fmgp_build_knn / fmgp_precompute with the
+ * same k, kernel and precision.  flags = FMGP_MODEL_BORROW: they are
+ * BORROWED and must stay valid and unchanged until fmgp_model_destroy.
+ * flags = FMGP_MODEL_COPY: the model copies them into device memory of its
+ * own (charged to the bound context, if any, like its other buffers), and the
+ * caller may free or reuse them as soon as the call returns.  Any other flags
+ * value returns FMGP_EINVAL.  Either way the model builds and OWNS the
+ * nearest-point search grid (d <= 3), an FP32 copy of an FP64 X for the
+ * nearest-point scan (4 <= d <= 15), the packed training side of the
+ * tensor-core search (d >= 16) and, for FMGP_PREC_MIXED, a double-float copy
+ * of X.  Synchronises `stream` before returning.  *out receives the handle.
  */
 int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
                       int32_t nbr_ld, const void* C, int32_t k, int32_t r,
-                      const fmgp_kernel* kernel, fmgp_precision precision, fmgp_model** out,
-                      void* stream);
+                      const fmgp_kernel* kernel, fmgp_precision precision, int32_t flags,
+                      fmgp_model** out, void* stream);
 
 /* fmgp_predict through a model (Eq. 7): same results, no index rebuild.
  * Z (m x d device, the model's dtype), Yhat_out (m x r FP64 device),

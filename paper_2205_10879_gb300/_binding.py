@@ -128,7 +128,7 @@ def load(build_if_missing=True):
     lib.fmgp_autotune_knn.argtypes = [P, I32, I64, I32, I32, ctypes.POINTER(ctypes.c_double), P]
     lib.fmgp_autotune_knn.restype = I32
     lib.fmgp_autotune_reset.restype = I32
-    lib.fmgp_model_create.argtypes = [P, I32, I64, I32, P, I32, P, I32, I32, KP, I32,
+    lib.fmgp_model_create.argtypes = [P, I32, I64, I32, P, I32, P, I32, I32, KP, I32, I32,
                                       ctypes.POINTER(ctypes.c_void_p), P]
     lib.fmgp_model_predict.argtypes = [P, P, I64, P, P, P]
     lib.fmgp_model_destroy.argtypes = [P]
@@ -409,20 +409,27 @@ def kernel_launches():
     return int(load().fmgp_kernel_launches())
 
 
-class FmgpModel:
-    """fmgp_model_create / fmgp_model_predict / fmgp_model_destroy.  Keeps
-    references to the borrowed tensors X, nbr and C for its lifetime."""
+MODEL_BORROW, MODEL_COPY = 0, 1
 
-    def __init__(self, X, nbr, C, k, kernel, precision=PREC_FP64, stream=None):
+
+class FmgpModel:
+    """fmgp_model_create / fmgp_model_predict / fmgp_model_destroy.  A
+    borrowing model keeps references to the tensors X, nbr and C for its
+    lifetime; with copy=True the library keeps copies of its own and the
+    tensors may be freed or reused after construction."""
+
+    def __init__(self, X, nbr, C, k, kernel, precision=PREC_FP64, stream=None, copy=False):
         _dev(X, "X"); _dev(nbr, "nbr"); _dev(C, "C")
-        self.X, self.nbr, self.C, self.k, self.kernel, self.precision = X, nbr, C, k, kernel, precision
+        self.k, self.kernel, self.precision = k, kernel, precision
+        self.X, self.nbr, self.C = (None, None, None) if copy else (X, nbr, C)
         self.n, self.d = X.shape
         self.r = C.shape[2]
         self.dtype = X.dtype
         h = ctypes.c_void_p()
         _check(load().fmgp_model_create(_ptr(X), _dtype_code(X), self.n, self.d, _ptr(nbr),
                                         nbr.shape[1], _ptr(C), int(k), self.r,
-                                        ctypes.byref(kernel), int(precision), ctypes.byref(h),
+                                        ctypes.byref(kernel), int(precision),
+                                        MODEL_COPY if copy else MODEL_BORROW, ctypes.byref(h),
                                         _stream(stream)))
         self.handle = h
 

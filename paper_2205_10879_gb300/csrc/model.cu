@@ -1,5 +1,6 @@
 // Resident fitted models: a model borrows the caller's X, neighbour table and
-// coefficients and owns what prediction would otherwise rebuild per call (the
+// coefficients (or keeps copies of its own) and owns what prediction would
+// otherwise rebuild per call (the
 // search grid over X for d <= 3, an FP32 copy of an FP64 X for the
 // nearest-point scan at 4 <= d <= 15, the packed training side of the
 // tensor-core search at d >= 16, the double-float copy of X for the mixed
@@ -27,7 +28,7 @@ namespace fmgp {
 int model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
                  int32_t nbr_ld, const void* C, int32_t k, int32_t r, const fmgp_kernel* kernel,
                  fmgp_precision precision, fmgp_model** out, cudaStream_t s, void* const* owned,
-                 int nowned) {
+                 int nowned, bool copy) {
   auto release = [&]() {
     for (int i = 0; i < nowned; ++i) cudaFree(owned[i]);
   };
@@ -64,7 +65,27 @@ int model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const in
   m->k = k; m->r = r; m->kern = *kernel; m->prec = precision;
   Workspace ws(s);
   int rc = FMGP_OK;
-  if (d <= kGridMaxD) {
+  if (copy) {
+    // the model's own copies of X, the neighbour table and C
+    const size_t xb = (size_t)n * d * (dtype == FMGP_F64 ? 8 : 4);
+    const size_t nb = k > 1 ? (size_t)n * nbr_ld * 4 : 0;
+    const size_t cb = (size_t)n * k * r * 8;
+    void* Xc = ws.alloc(xb);
+    void* Cc = ws.alloc(cb);
+    void* Nc = nb ? ws.alloc(nb) : nullptr;
+    if (!Xc || !Cc || (nb && !Nc)) {
+      rc = FMGP_ENOMEM;
+    } else {
+      cudaError_t e = cudaMemcpyAsync(Xc, X, xb, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(Cc, C, cb, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess && nb) e = cudaMemcpyAsync(Nc, nbr, nb, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync (model copy)");
+      m->X = X = Xc;
+      m->C = Cc;
+      if (nb) m->nbr = (const int32_t*)Nc;
+    }
+  }
+  if (!rc && d <= kGridMaxD) {
     rc = build_grid(X, dtype, n, d, tune_params().grid_target, ws, s, &m->grid);
     m->has_grid = (rc == FMGP_OK);
   }
@@ -101,10 +122,15 @@ int model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const in
 extern "C" int fmgp_model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d,
                                  const int32_t* nbr, int32_t nbr_ld, const void* C, int32_t k,
                                  int32_t r, const fmgp_kernel* kernel, fmgp_precision precision,
-                                 fmgp_model** out, void* stream) {
+                                 int32_t flags, fmgp_model** out, void* stream) {
   clear_error();
+  if (flags != FMGP_MODEL_BORROW && flags != FMGP_MODEL_COPY) {
+    if (out) *out = nullptr;
+    set_error("flags = %d: FMGP_MODEL_BORROW (0) or FMGP_MODEL_COPY (1)", flags);
+    return FMGP_EINVAL;
+  }
   return model_create(X, dtype, n, d, nbr, nbr_ld, C, k, r, kernel, precision, out,
-                      (cudaStream_t)stream, nullptr, 0);
+                      (cudaStream_t)stream, nullptr, 0, flags == FMGP_MODEL_COPY);
 }
 
 extern "C" int fmgp_model_predict(fmgp_model* model, const void* Z, int64_t m, double* Yhat_out,

@@ -35,10 +35,11 @@ int model_predict(const Model& md, const void* Z, int64_t m, double* Yhat, int32
                   cudaStream_t s);
 
 // fmgp_model_create with the device buffers owned[0..nowned) handed to the
-// model (freed with it, or at once if creation fails).
+// model (freed with it, or at once if creation fails); with copy, X, nbr and
+// C are first copied into the model's own workspace.
 int model_create(const void* X, fmgp_dtype dtype, int64_t n, int32_t d, const int32_t* nbr,
                  int32_t nbr_ld, const void* C, int32_t k, int32_t r, const fmgp_kernel* kernel,
                  fmgp_precision precision, fmgp_model** out, cudaStream_t s, void* const* owned,
-                 int nowned);
+                 int nowned, bool copy = false);
 
 }  // namespace fmgp

@@ -83,6 +83,11 @@ def test_argument_errors_are_caught_on_the_host():
     assert lib.fmgp_predict(fake, b.F64, 100, 2, fake, 29, fake, 30, 1, ctypes.byref(k),
                             b.PREC_FP64, fake, -1, fake, None, None) == b.FMGP_EINVAL
     assert b"m = -1" in lib.fmgp_last_error()
+    # model: flags other than borrow (0) / copy (1)
+    h = ctypes.c_void_p(16)
+    assert lib.fmgp_model_create(fake, b.F64, 100, 2, fake, 29, fake, 30, 1, ctypes.byref(k),
+                                 b.PREC_FP64, 2, ctypes.byref(h), None) == b.FMGP_EINVAL
+    assert h.value is None and b"flags = 2" in lib.fmgp_last_error()
 
 
 def test_tuning_keys_are_host_only_and_range_checked():

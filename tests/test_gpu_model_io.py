@@ -86,3 +86,45 @@ def test_damaged_or_truncated_file_is_refused(cuda, tmp_path):
     with pytest.raises(fb.FmgpError) as e:
         fb.FmgpModel.load(tmp_path / "hdr.fmgp")
     assert e.value.code == fb.FMGP_EIO
+
+
+@pytest.mark.parametrize("d,dtype,prec", [(2, np.float64, fb.PREC_MIXED),
+                                          (8, np.float32, fb.PREC_FP64)])
+def test_copying_model_outlives_the_callers_arrays(cuda, d, dtype, prec):
+    """FMGP_MODEL_COPY: the model keeps X, the neighbour table and C in device
+    memory of its own.  It predicts bit-identically to a borrowing model, also
+    after the caller has overwritten and freed its arrays, and the copies are
+    charged to the context bound when the model was created (released with
+    the model)."""
+    rng = np.random.default_rng(40 + d)
+    n, k = 5000, 20
+    X = rng.random((n, d)).astype(dtype)
+    Y = np.stack([np.sin(4 * X[:, 0]), np.cos(3 * X[:, -1])], axis=1).astype(np.float64)
+    kern = fb.make_kernel("matern", 1.5, 0.3 * np.sqrt(d), 1.3, 1e-3)
+    Xd, Yd = dev(X), dev(Y)
+    nbr, _ = fb.fmgp_build_knn(Xd, k - 1)
+    C, _ = fb.fmgp_precompute(Xd, Yd, nbr, k, kern, prec)
+    Z = dev(rng.random((600, d)).astype(dtype))
+    borrowed = fb.FmgpModel(Xd, nbr, C, k, kern, prec)
+    y0, j0 = borrowed.predict(Z)
+    torch.cuda.synchronize()
+    borrowed.close()
+    own = sum(t.numel() * t.element_size() for t in (Xd, nbr, C))
+    ctx = fb.Context(64 << 20)
+    try:
+        with ctx:
+            copied = fb.FmgpModel(Xd, nbr, C, k, kern, prec, copy=True)
+        assert ctx.bytes_in_use() >= own
+        Xd.fill_(7.0)
+        nbr.fill_(0)
+        C.fill_(float("nan"))
+        del Xd, nbr, C
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        y1, j1 = copied.predict(Z)
+        torch.cuda.synchronize()
+        assert torch.equal(y0, y1) and torch.equal(j0, j1)
+        copied.close()
+        assert ctx.bytes_in_use() == 0
+    finally:
+        ctx.close()
