@@ -883,7 +883,11 @@ def serving_bench(a, dev):
         lat, pts, wall, sz = serving.run_poisson(srv, models, frac * req_rate, a.serving_requests,
                                                  12 + int(frac * 100))
         out[f"load_{int(frac * 100)}"] = serving.latency_summary(lat, pts, wall, sz)
-    out["server"] = srv.stats()
+    st = srv.stats()
+    # batches hold pieces of one model up to piece_points points; a piece of a
+    # large request fills one alone, small requests share one
+    st["mean_batch_points"] = st["points"] / st["batches"] if st["batches"] else 0.0
+    out["server"] = st
     srv.close()
     for m in models:
         m.close()
