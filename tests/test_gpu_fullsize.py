@@ -211,3 +211,32 @@ def test_borehole_mcmc_full_size(cuda):
     # near-zero margins (|margin| < 1e-2, about 1 % of decisions here) may go
     # either way; every other decision must match
     assert checked > 0.45 * chains * steps and skipped < 0.05 * chains * steps
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_grid_prefix_sum_paths_give_one_table(cuda, d):
+    """The grid's cell offsets come from the count kernel's last CTA up to
+    32,768 cells and from the multi-CTA prefix sum above.  On 400,000 points,
+    64 points per cell (about 6,000 cells) takes the first path and 4 points
+    per cell (about 100,000 cells) the second: the kNN tables (indices and
+    keys) are identical, and sampled rows equal the oracle's."""
+    rng = np.random.default_rng(70 + d)
+    n, kq = 400_000, 20
+    X = rng.random((n, d))
+    Xd = dev(X)
+    fb.autotune_reset()  # the occupancy set below is the one used
+    tabs = []
+    for target in (64.0, 4.0):
+        fb.tune_set("grid_target", target)
+        try:
+            nbr, dist = fb.fmgp_build_knn(Xd, kq, with_dist=True)
+        finally:
+            fb.tune_set("grid_target", 12.0)
+        torch.cuda.synchronize()
+        tabs.append((nbr.cpu().numpy(), dist.cpu().numpy()))
+    np.testing.assert_array_equal(tabs[0][0], tabs[1][0])
+    np.testing.assert_array_equal(tabs[0][1], tabs[1][1])
+    rows = np.sort(rng.choice(n, 200, replace=False))
+    ref_i, ref_k = oracle.knn(X, X[rows], kq, rows)
+    np.testing.assert_array_equal(tabs[0][0][rows], ref_i)
+    np.testing.assert_array_equal(tabs[0][1][rows], ref_k)
