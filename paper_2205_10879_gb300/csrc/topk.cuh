@@ -57,7 +57,7 @@ struct WarpTopK {
       if (s == ts) { mk = k[s]; mi = i[s]; }
     tk = __shfl_sync(kFull, mk, tl);
     ti = __shfl_sync(kFull, mi, tl);
-    t_up = key_bits_to_float_up(tk);
+    // t_up is refreshed by the caller (offer) once its inserts are done
   }
 
   // Into an empty list (just after init), put the one candidate per lane
@@ -97,9 +97,12 @@ struct WarpTopK {
   }
 
   // Offer one candidate per lane (ck = ~0 for none); inserts every candidate
-  // that belongs in the list, lowest lane first.
+  // that belongs in the list, lowest lane first.  The inserts keep (tk, ti)
+  // current for the admission test; the FP32 bound t_up, which only the
+  // search's pruning reads, is formed once afterwards.
   __device__ __forceinline__ void offer(unsigned long long ck, int ci, int lane) {
     unsigned hits = __ballot_sync(kFull, admits(ck, ci));
+    if (!hits) return;
     while (hits) {
       const int src = __ffs(hits) - 1;
       const unsigned long long bk = __shfl_sync(kFull, ck, src);
@@ -108,6 +111,7 @@ struct WarpTopK {
       hits &= ~(1u << src);
       hits &= __ballot_sync(kFull, admits(ck, ci));
     }
+    t_up = key_bits_to_float_up(tk);
   }
 
   __device__ __forceinline__ void store(int kq, int lane, int32_t* idx_row, double* key_row) const {
