@@ -118,9 +118,12 @@ __device__ __forceinline__ void grid_knn_search(const GridView& gv, const GridGe
 }
 
 // A1: queries are the training points themselves, in cell order (warp w takes
-// sorted point w), each excluded from its own list.
+// sorted point w), each excluded from its own list.  At D = 3 the launch
+// bound keeps four 256-thread CTAs per SM (64 registers, a 4-byte spill)
+// where the compiler would otherwise take 80 registers and three CTAs (the
+// 10^7-point table: 99 -> 87 ms); at D <= 2 its own choice is kept.
 template <int D, int L>
-__global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
+__global__ void __launch_bounds__(256, D == 3 ? 4 : 0) knn_grid_self_kernel(GridView gv, int kq,
                                                             int32_t* nbr_out, double* dist_out) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(256) knn_grid_self_kernel(GridView gv, int kq,
 
 // kq nearest training points of external query points (MuyGPs prediction).
 template <int D, int L, typename T>
-__global__ void __launch_bounds__(256) knn_grid_query_kernel(GridView gv, const T* Q, int64_t m,
+__global__ void __launch_bounds__(256, D == 3 ? 4 : 0) knn_grid_query_kernel(GridView gv, const T* Q, int64_t m,
                                                              int kq, int32_t* idx_out,
                                                              double* key_out) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
